@@ -1,0 +1,530 @@
+"""Benchmark of the spherical-index neighborhood queries on B300.
+
+Default (N=1): the all-agents fixed-radius query at 1M points on a 128^3
+fully cyclic lattice, r = 1.5 cell sides, with both seeded distributions
+(uniform and 64-component Gaussian mixture).  One step = one pass of the hot
+path over both point clouds: bin (key, histogram, scan, scatter) and query
+(count, scan, write, per-list id sort).  Other workloads: --workload
+knn_4m | batched | walk_1m | tiny | radius_1m_cube.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle (FP64
+brute force) on bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "all-agent radius queries/s and HBM-roofline % at 1M pts, batched/fused vs plain, exact sets"
+L2_BYTES = 126 * 2 ** 20
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def src_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_cs_0608108_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    from the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    cur = src_hash()
+    for line in open(p):
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel and f[1] == workload:
+            return float(f[2]) if f[3] == cur else None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.out = ""
+
+    def summary(self):
+        rows = []
+        for line in (getattr(self, "out", "") or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 6:
+                try:
+                    rows.append((float(f[0]), float(f[1]), f[2:6]))
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# workloads (GPU arm)
+# ---------------------------------------------------------------------------
+class RadiusWork:
+    """Bin + all-agents radius query for a list of scenes."""
+
+    def __init__(self, scenes, method="sphere"):
+        import torch
+        from paper_cs_0608108_b300 import Grid
+        self.scenes = scenes
+        self.method = method
+        self.pos = [torch.from_numpy(s.pos).cuda() for s in scenes]
+        self.grids = [Grid.for_scene(s) for s in scenes]
+        self.off, self.ids, self.totals = [], [], []
+        for g, p, s in zip(self.grids, self.pos, scenes):
+            g.build(p)
+            off, ids = g.query_radius(s.r, method=method)
+            g.sync()
+            self.totals.append(int(off[-1].item()))
+            self.off.append(off)
+            self.ids.append(torch.empty(max(self.totals[-1], 1), dtype=torch.int32, device="cuda"))
+        self.queries = sum(s.n for s in scenes)
+
+    def step(self):
+        for g, p, s, off, ids in zip(self.grids, self.pos, self.scenes, self.off, self.ids):
+            g.build(p)
+            g.query_radius(s.r, method=self.method, out_offsets=off, out_ids=ids, sync_total=False)
+
+    def check(self):
+        for g in self.grids:
+            g.sync()
+
+    def algorithmic_bytes(self):
+        """Per-kernel minimum DRAM bytes of one launch, per scene (averaged)."""
+        out = {}
+        for s, tot in zip(self.scenes, self.totals):
+            n, C = s.n, (1 << sum(s.log2_cells)) + 1
+            per = {
+                "k_bin_key": 16 * n + 8 * n + 8 * C,
+                "k_bin_scatter": 8 * n + 16 * n + 4 * C + 16 * n + 4 * n,
+                "k_radius_count": 16 * n + 4 * n + 4 * C + 8 * n,
+                "k_radius_write": 16 * n + 4 * n + 4 * C + 8 * n + 4 * tot,
+                "k_radius_count_cube": 16 * n + 4 * n + 4 * C + 8 * n,
+                "k_radius_write_cube": 16 * n + 4 * n + 4 * C + 8 * n + 4 * tot,
+            }
+            for k, v in per.items():
+                out.setdefault(k, []).append(v)
+        return {k: float(np.mean(v)) for k, v in out.items()}
+
+    def step_bytes(self):
+        tot = 0
+        for s, t in zip(self.scenes, self.totals):
+            n, C = s.n, (1 << sum(s.log2_cells)) + 1
+            tot += (16 + 20) * n + 4 * C + (16 + 4) * n + 4 * C + 8 * n + 4 * t
+        return tot
+
+
+def e2e_radius(work, steps, warmup):
+    """Same metric through the public API with host buffers: pinned H2D of the
+    points, bin + query, D2H of the CSR result, every step."""
+    import torch
+    hpos = [torch.from_numpy(s.pos).pin_memory() for s in work.scenes]
+    hoff = [torch.empty(s.n + 1, dtype=torch.int64).pin_memory() for s in work.scenes]
+    hids = [torch.empty(max(t, 1), dtype=torch.int32).pin_memory() for t in work.totals]
+    dpos = [torch.empty_like(p, device="cuda") for p in hpos]
+    st = torch.cuda.current_stream()
+
+    def one():
+        for k, (g, s) in enumerate(zip(work.grids, work.scenes)):
+            dpos[k].copy_(hpos[k], non_blocking=True)
+            g.build(dpos[k])
+            g.query_radius(s.r, out_offsets=work.off[k], out_ids=work.ids[k], sync_total=False)
+            hoff[k].copy_(work.off[k], non_blocking=True)
+            hids[k][: work.totals[k]].copy_(work.ids[k][: work.totals[k]], non_blocking=True)
+    for _ in range(warmup):
+        one()
+    st.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(steps):
+        one()
+    b.record(st)
+    b.synchronize()
+    ms = a.elapsed_time(b) / steps
+    bi = sum(16 * s.n for s in work.scenes)
+    bo = sum(8 * (s.n + 1) + 4 * t for s, t in zip(work.scenes, work.totals))
+    return ms, bi, bo
+
+
+class KnnWork:
+    def __init__(self, scene, ks=(16, 64)):
+        import torch
+        from paper_cs_0608108_b300 import Grid
+        self.scene = scene
+        self.ks = ks
+        self.pos = torch.from_numpy(scene.pos).cuda()
+        self.grid = Grid.for_scene(scene)
+        self.out = {k: (torch.empty((scene.n, k), dtype=torch.int32, device="cuda"),
+                        torch.empty((scene.n, k), dtype=torch.float32, device="cuda"),
+                        torch.empty(scene.n, dtype=torch.int32, device="cuda")) for k in ks}
+        self.queries = scene.n * len(ks)
+
+    def step(self):
+        self.grid.build(self.pos)
+        for k in self.ks:
+            self.grid.query_knn(k, r_max=self.scene.r, out=self.out[k])
+
+    def check(self):
+        self.grid.sync()
+
+    def algorithmic_bytes(self):
+        n, C = self.scene.n, (1 << sum(self.scene.log2_cells)) + 1
+        kb = float(np.mean([16 * n + 4 * n + 4 * C + 8 * k * n + 4 * n for k in self.ks]))
+        return {"k_knn": kb, "k_bin_key": 24 * n + 8 * C, "k_bin_scatter": 48 * n + 4 * C}
+
+    def step_bytes(self):
+        n, C = self.scene.n, (1 << sum(self.scene.log2_cells)) + 1
+        return 36 * n + 4 * C + sum(20 * n + 4 * C + 8 * k * n + 4 * n for k in self.ks)
+
+
+class WalkWork:
+    """Random-walk timestep: rebin, energy kernel, adjoint kernel (autograd)."""
+
+    def __init__(self, scene, n_pos=4):
+        import torch
+        from paper_cs_0608108_b300 import Grid
+        self.scene = scene
+        s = scene.cell_size
+        pos = scene.pos
+        self.frames = []
+        for t in range(n_pos):
+            pos = __import__("paper_cs_0608108_b300.synth", fromlist=["x"]).random_walk_step(
+                pos, 0x5A1, t, 0.1 * s)
+            self.frames.append(torch.from_numpy(pos).cuda())
+        self.grid = Grid.for_scene(scene)
+        self.t = 0
+        self.queries = scene.n
+
+    def step(self):
+        from paper_cs_0608108_b300 import neighbor_energy
+        x = self.frames[self.t % len(self.frames)].detach().requires_grad_(True)
+        self.t += 1
+        E = neighbor_energy(x, self.grid, self.scene.r)
+        E.backward()
+
+    def check(self):
+        self.grid.sync()
+
+    def algorithmic_bytes(self):
+        n, C = self.scene.n, (1 << sum(self.scene.log2_cells)) + 1
+        return {"k_reduce": 16 * n + 4 * n + 4 * C + 16 * n, "k_bin_key": 24 * n + 8 * C,
+                "k_bin_scatter": 48 * n + 4 * C}
+
+    def step_bytes(self):
+        n, C = self.scene.n, (1 << sum(self.scene.log2_cells)) + 1
+        return 36 * n + 4 * C + 2 * (20 * n + 4 * C) + 16 * n
+
+
+class BatchWork:
+    def __init__(self, scenes, graph=True):
+        import torch
+        from paper_cs_0608108_b300 import Batch
+        self.scenes = scenes
+        self.pos = [torch.from_numpy(s.pos).cuda() for s in scenes]
+        self.offs = [torch.empty(s.n + 1, dtype=torch.int64, device="cuda") for s in scenes]
+        # first pass with generous capacity to learn the totals
+        self.ids = [torch.empty(max(48 * s.n, 64), dtype=torch.int32, device="cuda") for s in scenes]
+        b = Batch(list(zip(scenes, self.pos)), self.offs, self.ids)
+        b.run(False)
+        self.totals = b.sync()
+        b.close()
+        self.ids = [torch.empty(max(t, 1), dtype=torch.int32, device="cuda") for t in self.totals]
+        self.batch = Batch(list(zip(scenes, self.pos)), self.offs, self.ids)
+        self.graph = graph
+        self.queries = sum(s.n for s in scenes)
+
+    def step(self):
+        self.batch.run(self.graph)
+
+    def check(self):
+        self.batch.sync()
+
+    def algorithmic_bytes(self):
+        return {"batch_graph": float(self.step_bytes())}
+
+    def step_bytes(self):
+        tot = 0
+        for s, t in zip(self.scenes, self.totals):
+            n, C = s.n, (1 << sum(s.log2_cells)) + 1
+            tot += 36 * n + 4 * C + 20 * n + 4 * C + 8 * n + 4 * t
+        return tot
+
+
+class LoopWork(RadiusWork):
+    """The plain single-scene path looped over the batch's scenes."""
+
+
+def make_work(name):
+    from paper_cs_0608108_b300 import synth
+    if name == "radius_1m":
+        return RadiusWork([synth.uniform_1m_scene(), synth.mixture_1m_scene()]), \
+            "1M-point all-agents radius, 128^3 cyclic, r=1.5 cells, uniform + Gaussian mixture"
+    if name == "radius_1m_cube":
+        return RadiusWork([synth.uniform_1m_scene(), synth.mixture_1m_scene()], "cube"), \
+            "same, GPU bin-lattice cube scan"
+    if name == "knn_4m":
+        return KnnWork(synth.knn_4m_scene()), "4M-point K-nearest (K=16 and 64), 256^3, cyclic x,y, r_max=4 cells"
+    if name == "walk_1m":
+        return WalkWork(synth.uniform_1m_scene()), \
+            "1M-point random walk step: rebin + energy + adjoint, 128^3 cyclic, r=1.5 cells"
+    if name == "batched":
+        return BatchWork(synth.batched_scenes()), "256 uneven scenes (log-uniform 1k-200k points), one graph replay"
+    if name == "batched_loop":
+        return LoopWork(synth.batched_scenes()), "256 uneven scenes, plain path looped per scene"
+    if name == "tiny":
+        return RadiusWork([synth.tiny_scene()]), "20k-point radius, 32^3 non-cyclic, r=0.96 cells"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def time_steps(work, steps, warmup, flush):
+    import torch
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        work.step()
+    work.check()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for a, b in evs:
+        flush.zero_()                        # evict L2 between timed steps
+        a.record(st)
+        work.step()
+        b.record(st)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def kernel_report(lib):
+    buf = ctypes.create_string_buffer(1 << 16)
+    lib.si_kernel_timing_report(buf, len(buf))
+    rows = {}
+    for line in buf.value.decode().splitlines():
+        f = line.rsplit(" ", 2)
+        if len(f) == 3:
+            rows[f[0]] = (int(f[1]), float(f[2]))
+    return rows
+
+
+def _oracle_scene(name):
+    from paper_cs_0608108_b300 import synth
+    if name in ("radius_1m", "radius_1m_cube", "walk_1m"):
+        return synth.uniform_1m_scene()
+    if name == "knn_4m":
+        return synth.knn_4m_scene()
+    if name == "tiny":
+        return synth.tiny_scene()
+    return synth.batched_scenes()[0]
+
+
+class OracleRunner:
+    """The oracle (FP64 brute force over all points) as it stands, on bounded
+    samples of the workload's query points, with every host thread."""
+
+    def __init__(self, name):
+        import oracle
+        self.oracle = oracle
+        self.name = name
+        self.sc = _oracle_scene(name)
+        self.threads = oracle.max_threads()
+        self.rng = np.random.default_rng(0)
+
+    def run(self, m):
+        sc, o = self.sc, self.oracle
+        q = self.rng.choice(sc.n, m, replace=False)
+        t = time.perf_counter()
+        if self.name == "knn_4m":
+            o.knn(sc.pos, sc.pos[q], sc.box, sc.cyclic_mask, 16, sc.r, q)
+        elif self.name == "walk_1m":
+            o.reduce(sc.pos, q, sc.box, sc.cyclic_mask, sc.r)
+        else:
+            o.radius(sc.pos, sc.pos[q], sc.box, sc.cyclic_mask, sc.r, q)
+        return time.perf_counter() - t
+
+    def calibrate(self, seconds):
+        m = max(64, self.threads * 32)   # the oracle hands out queries in chunks of 16
+        self.run(m)                       # warm the thread pool
+        dt = self.run(m)
+        return int(min(self.sc.n, max(m, m * seconds / max(dt, 1e-4))))
+
+    def describe(self, m, total_s, steps):
+        return (f"{steps} x {m} random query points of the {self.sc.n}-point workload, "
+                f"FP64 brute force over all points, {self.threads} threads, {total_s:.1f} s")
+
+
+def cpu_baseline(name, budget_s=15.0):
+    r = OracleRunner(name)
+    m = r.calibrate(budget_s)
+    dt = r.run(m)
+    return {"value": m / dt, "unit": "queries/s", "cores": r.threads, "kind": "oracle",
+            "sample": r.describe(m, dt, 1)}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="radius_1m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_setup()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        r = OracleRunner(args.workload)
+        m = r.calibrate(min(4.0, 90.0 / max(args.steps + args.warmup, 1)))
+        for _ in range(args.warmup):
+            r.run(max(1, m // 4))
+        total = sum(r.run(m) for _ in range(args.steps))
+        v = m * args.steps / total
+        cb = {"value": v, "unit": "queries/s", "cores": r.threads, "kind": "oracle",
+              "sample": r.describe(m, total, args.steps)}
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": args.workload}, "cpu_baseline": cb,
+                "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_cs_0608108_b300 import _native, launch_count
+    lib = _native.lib()
+    work, desc = make_work(args.workload)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    # whole-step timing (no per-kernel events)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = launch_count()
+    with ClockSampler(local) as clk:
+        ms = time_steps(work, args.steps, args.warmup, flush)
+    launches = (launch_count() - l0) // (args.steps + args.warmup)
+    work.check()
+    ms_step = float(np.mean(ms))
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = work.queries * world / (ms_step * 1e-3)
+    # per-kernel timing pass (CUDA events around each launch, same stream)
+    lib.si_kernel_timing_enable(1)
+    kernel_report(lib)
+    time_steps(work, args.steps, 1, flush)
+    rows = kernel_report(lib)
+    lib.si_kernel_timing_enable(0)
+    alg = work.algorithmic_bytes()
+    peak, peak_kind = peaks()
+    dom = max(rows.items(), key=lambda kv: kv[1][1])[0] if rows else None
+    roof = None
+    if dom is not None:
+        cnt, tot = rows[dom]
+        avg_ms = tot / max(cnt, 1)
+        a_bytes = alg.get(dom)
+        achieved = (a_bytes / (avg_ms * 1e-3) / 1e9) if a_bytes else None
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+                "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": a_bytes,
+                "traffic": ncu_traffic(dom, args.workload),
+                "kernel_share": {k: round(v[1] / sum(x[1] for x in rows.values()), 4)
+                                 for k, v in sorted(rows.items(), key=lambda kv: -kv[1][1])}}
+    step_gbs = work.step_bytes() / (ms_step * 1e-3) / 1e9
+    e2e = None
+    if not args.no_e2e and isinstance(work, RadiusWork):
+        e_ms, bi, bo = e2e_radius(work, max(3, args.steps // 2), 2)
+        e2e = {"value": work.queries * world / (e_ms * 1e-3), "unit": "queries/s",
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e_ms}
+    line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "l2": "flushed between steps",
+                       "queries_per_step": work.queries, "parallelism": f"replicas x{world}"},
+            "step_algorithmic_gbs": step_gbs, "step_hbm_frac": step_gbs / peak,
+            "roofline": roof, "gpu_launches": int(launches), "clocks": clk.summary(), "e2e": e2e,
+            "ms_samples": {"median": float(np.median(ms)), "min": float(np.min(ms)),
+                           "max": float(np.max(ms))}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * si.h -- C ABI of the B300 spherical-index neighborhood queries.
+ *
+ * Method: N. Brodu, "Spherical Indexing for Neighborhood Queries".
+ *   Problem statement (Sec. I, Sec. II.A): a query center C, a radius d, the
+ *   objects X with |X - C| <= d; optionally only the K nearest (Sec. II.A,
+ *   last paragraph; Sec. IV.B).  Space is a power-of-two lattice of cubic
+ *   cells (Sec. II.B) whose axes are each cyclic or not (Sec. II.B,
+ *   Appendix), with one extra cell for every object outside the region.
+ *
+ * Conventions shared by every call
+ *   - Points are float32 quadruples (x, y, z, unused): an array of n * 4
+ *     floats, 16-byte aligned.  The fourth lane is never read.
+ *   - "d_" pointers are device pointers, "h_" pointers host pointers.  The
+ *     caller owns every buffer it passes and the stream; the library owns
+ *     only the opaque objects it returns (si_grid, si_batch).
+ *   - Every call is ordered on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) and returns without synchronising unless stated.
+ *   - Errors are returned as si_status; no call aborts or throws.
+ *     si_last_error() gives a one-line message for the calling host thread.
+ *   - Distances follow one canonical predicate, identical on every path:
+ *       a_k = |x_jk - x_ik| in FP64; on a cyclic axis a_k = min(a_k, L_k - a_k);
+ *       D2  = (a_x^2 + a_y^2) + a_z^2 in FP64 (round to nearest, no FMA);
+ *       neighbor  <=>  D2 <= (double)r * (double)r.
+ *     The kernels filter in FP32 and re-test in FP64 every pair whose FP32
+ *     value lies inside a guard band around r^2, so the sets are exact.
+ *   - Neighbor ids are indices into the point array given to si_grid_build.
+ */
+#ifndef SI_H
+#define SI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SI_OK = 0,
+  SI_ERR_INVALID = 1,   /* bad argument, descriptor, or input value        */
+  SI_ERR_OOM = 2,       /* device or host allocation failed                */
+  SI_ERR_CUDA = 3,      /* a CUDA runtime call failed (see si_last_error)  */
+  SI_ERR_CAPACITY = 4,  /* output buffer too small; required size reported */
+  SI_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up              */
+  SI_ERR_INTERNAL = 6   /* a device-side consistency check failed          */
+} si_status;
+
+/* Query flags */
+#define SI_METHOD_SPHERE   0u  /* spherical index walk (Sec. II-III)            */
+#define SI_METHOD_CUBE     1u  /* bin-lattice cube scan (Sec. I, Sec. IV.A)     */
+#define SI_INCLUDE_SELF    2u  /* all-agents mode: keep the querying point      */
+#define SI_NO_SORT         4u  /* radius lists left in walk order (not by id)   */
+
+/* Region, lattice and table extent (Sec. II.B).  The box side on axis a is
+ * L_a = cell_size * 2^log2_cells[a] (exact in float32).  A cyclic axis wraps
+ * at L_a; positions on it must lie in [origin_a, origin_a + L_a).  On a
+ * non-cyclic axis points may lie anywhere (finite); those outside the region
+ * go to the single outside cell.
+ * r_max bounds every radius queried on the grid (it sizes the offset tables).
+ * r_max = +inf (or <= 0) means "the whole region" and is accepted only when
+ * no axis is cyclic.  On a cyclic axis the tables must not wrap onto
+ * themselves: 2 * (floor(r_max / cell_size) + 1) + 1 <= 2^log2_cells[a].
+ * Constraints: 2 <= log2_cells[a] <= 10, sum <= 27. */
+typedef struct {
+  float origin[3];
+  float cell_size;
+  uint8_t log2_cells[3];
+  uint8_t reserved;
+  uint32_t cyclic_mask;   /* bit 0 = x, bit 1 = y, bit 2 = z */
+  float r_max;
+} si_grid_desc;
+
+typedef struct si_grid si_grid;
+
+/* Grid state that tests and tools may read (all device pointers are owned by
+ * the grid and valid until the next build or destroy). */
+typedef struct {
+  int64_t n;               /* points in the last build                       */
+  int64_t n_cells;         /* 2^W + 1 (the last one is the outside cell)     */
+  const int32_t *d_cell_start; /* n_cells + 1 entries: cell c holds sorted
+                                  points cell_start[c] .. cell_start[c+1]-1  */
+  const float *d_sorted_pos;   /* n float4, points in cell order            */
+  const int32_t *d_perm;       /* n: sorted slot -> input index             */
+  int64_t table_entries;   /* offsets in the sorted table                    */
+  int32_t table_n_max;     /* largest floor(d^2) the table covers            */
+  int32_t spec_shells;     /* shells with specialized tables (0..spec_shells-1) */
+} si_grid_info;
+
+/* Create a grid for up to n_capacity points: validates the descriptor,
+ * builds the sorted offset table (Sec. II.A), its index by floor(d^2) and the
+ * 64 specialized tables (Sec. III.A, Eq. 1-2) on the host, and allocates and
+ * uploads every device array.  This is the only call that allocates. */
+si_status si_grid_create(const si_grid_desc *desc, int64_t n_capacity, si_grid **out);
+
+/* Bin n points (n <= capacity) into the lattice: cell key by mask and shift
+ * (Sec. II.B), histogram, exclusive scan, scatter into cell order.  Re-binning
+ * moved points (Sec. I: objects move freely) reuses the grid's memory.
+ * d_pos: n * 4 floats, device, 16-byte aligned.  A cyclic-axis coordinate
+ * outside its box or a non-finite coordinate makes the build fail with
+ * SI_ERR_INVALID; this is detected on the device and reported by the next
+ * call that synchronises (si_grid_sync). */
+si_status si_grid_build(si_grid *g, const float *d_pos, int64_t n, void *stream);
+
+/* Convenience: si_grid_create(desc, n) followed by si_grid_build. */
+si_status si_build_grid(const si_grid_desc *desc, const float *d_pos, int64_t n,
+                        void *stream, si_grid **out);
+
+/* Wait for the grid's work on `stream` and return any device-side status
+ * recorded since the last call (SI_ERR_INVALID from a build, SI_ERR_CAPACITY
+ * from an asynchronous radius query, SI_ERR_INTERNAL).  Clears it. */
+si_status si_grid_sync(si_grid *g, void *stream);
+
+si_status si_grid_get_info(const si_grid *g, si_grid_info *info);
+si_status si_grid_destroy(si_grid *g);
+
+/* All-agents fixed-radius query (Sec. I: every agent queries its
+ * neighborhood; Sec. II.A: x <= d).  Query k is point k of the last build;
+ * its own index is excluded unless SI_INCLUDE_SELF.
+ * d_centers must be NULL (all agents) and m must equal the grid's n.
+ * Output: CSR in input order, d_offsets[m + 1] (int64, device) and d_ids
+ * (int32, device, capacity ids_capacity); ids ascending per query unless
+ * SI_NO_SORT.  r must satisfy 0 <= r <= r_max.
+ * h_total (nullable, host): when given, the call synchronises after counting,
+ * stores the total there and returns SI_ERR_CAPACITY without writing ids if
+ * total > ids_capacity.  When NULL the call stays asynchronous; an overflow
+ * then writes only the ids that fit and is reported by si_grid_sync. */
+si_status si_query_radius(si_grid *g, const float *d_centers, int64_t m, float r,
+                          uint32_t flags, int64_t *d_offsets, int32_t *d_ids,
+                          int64_t ids_capacity, int64_t *h_total, void *stream);
+
+/* All-agents K-nearest query (Sec. II.A, last paragraph: once K neighbors are
+ * found the search radius shrinks to the K-th distance; Sec. IV.B).
+ * Up to k (1 <= k <= 64) nearest points within r_max_query (inclusive), ordered
+ * by (canonical D2, index); d_ids[m * k] int32 padded with -1, d_d2[m * k]
+ * float (nullable; FP32 rounding of the canonical D2, +inf padding), and
+ * d_counts[m] int32 (number found).  r_max_query <= the grid's r_max
+ * (+inf allowed when the grid's r_max is +inf). */
+si_status si_query_knn(si_grid *g, const float *d_centers, int64_t m, int k,
+                       float r_max_query, uint32_t flags, int32_t *d_ids, float *d_d2,
+                       int32_t *d_counts, void *stream);
+
+/* Smooth neighbor reduction: the "functor applied to each neighbor" of
+ * Sec. IV.A made concrete.  kernel 0 (SI_KERNEL_POLY6_CUBED):
+ *   E = sum_i sum_{j != i, D_ij < r} (1 - D_ij^2 / r^2)^3
+ *   dE/dx_i = -(12 / r^2) sum_{j != i, D_ij < r} (1 - D_ij^2 / r^2)^2 (x_i - x_j)
+ * (shortest displacement on cyclic axes).  d_energy: one double (device,
+ * nullable).  d_grad: n * 4 floats in input order (device, nullable; the
+ * fourth lane is written 0), multiplied by *d_grad_scale when that device
+ * pointer is given.  FP32 arithmetic, FP64 accumulation of E. */
+#define SI_KERNEL_POLY6_CUBED 0
+si_status si_neighbor_reduce(si_grid *g, float r, int kernel, double *d_energy,
+                             float *d_grad, const float *d_grad_scale, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched scenes: many independent grids served together.
+ * Each scene has its own lattice, cyclic mask, radius and points; all scenes
+ * are binned and queried by a fixed, small number of launches (one persistent
+ * query kernel pulls (scene, query tile) items from a device work queue), so
+ * that the whole batch can be captured once in a CUDA graph and replayed.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  si_grid_desc desc;       /* r_max is ignored; the scene's r sizes its tables */
+  const float *d_pos;      /* n * 4 floats, device                            */
+  int64_t n;
+  float r;                 /* all-agents radius of this scene                 */
+  int64_t *d_offsets;      /* n + 1, device                                   */
+  int32_t *d_ids;          /* ids_capacity, device                            */
+  int64_t ids_capacity;
+} si_scene;
+
+typedef struct si_batch si_batch;
+
+/* Plan a batch: validates every scene, builds each scene's tables and
+ * allocates the batch's device memory (cell arrays of all scenes, sorted
+ * points, work queue).  Scene pointers are captured: later runs read the
+ * scenes' current point data and write their outputs. */
+si_status si_batch_create(const si_scene *scenes, int n_scenes, uint32_t flags, si_batch **out);
+
+/* Run the batch on `stream`: bin all scenes, count, scan, write, sort.
+ * Asynchronous; capacity overflow is reported by si_batch_sync.
+ * use_graph != 0: the first call captures the launches into a CUDA graph
+ * and every call replays it. */
+si_status si_batch_run(si_batch *b, int use_graph, void *stream);
+
+/* Wait, then report the per-scene totals (h_totals[n_scenes], host,
+ * nullable) and any device-side status. */
+si_status si_batch_sync(si_batch *b, int64_t *h_totals, void *stream);
+si_status si_batch_destroy(si_batch *b);
+
+/* Number of kernel launches issued by this library (all calls, this process):
+ * lets a benchmark count the launches inside its timed region. */
+int64_t si_launch_count(void);
+
+/* Per-kernel device timing, for benchmarks.  While enabled, every kernel
+ * launch of the library (and every batch graph replay) is bracketed by two
+ * CUDA events recorded on its own stream; launches made during a stream
+ * capture are not timed.  Not thread-safe with concurrent library calls. */
+si_status si_kernel_timing_enable(int enable);
+
+/* Synchronise the device, aggregate the launches timed since the last report
+ * and write one line per kernel, "name launches total_ms\n", into buf (host,
+ * cap bytes, always NUL-terminated).  Clears the records. */
+si_status si_kernel_timing_report(char *buf, size_t cap);
+
+const char *si_status_string(si_status s);
+const char *si_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SI_H */

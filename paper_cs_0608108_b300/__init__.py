@@ -1,0 +1,244 @@
+"""B300 spherical-index neighborhood queries (Brodu, "Spherical Indexing for
+Neighborhood Queries").
+
+Thin Python layer over the C ABI of include/si.h: it only marshals torch
+device tensors and the current CUDA stream into the library's calls.  Every
+step of binning, querying, sorting and reducing runs in the library's CUDA
+kernels; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _native as N
+
+__all__ = ["Grid", "NeighborEnergy", "neighbor_energy", "Batch", "launch_count"]
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr() if t is not None else 0)
+
+
+def _check_points(pos: torch.Tensor) -> torch.Tensor:
+    if not (pos.is_cuda and pos.dtype == torch.float32 and pos.dim() == 2 and pos.shape[1] == 4):
+        raise ValueError("points must be a CUDA float32 tensor of shape (n, 4)")
+    return pos.contiguous()
+
+
+class _CudaArray:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), True), "version": 2}
+
+
+def _device_view(ptr, shape, typestr) -> torch.Tensor:
+    """Zero-copy torch view of library-owned device memory."""
+    if int(torch.Size(shape).numel()) == 0:
+        return torch.empty(shape, dtype={"<i4": torch.int32, "<f4": torch.float32}[typestr], device="cuda")
+    return torch.as_tensor(_CudaArray(ptr, shape, typestr), device="cuda")
+
+
+def launch_count() -> int:
+    """Kernel launches issued by the library so far in this process."""
+    return int(N.lib().si_launch_count())
+
+
+def make_desc(origin, cell_size, log2_cells, cyclic_mask, r_max) -> N.GridDesc:
+    d = N.GridDesc()
+    for a in range(3):
+        d.origin[a] = float(origin[a])
+        d.log2_cells[a] = int(log2_cells[a])
+    d.cell_size = float(cell_size)
+    d.cyclic_mask = int(cyclic_mask)
+    d.r_max = float("inf") if r_max is None else float(r_max)
+    return d
+
+
+class Grid:
+    """A power-of-two cubic-cell lattice with its offset tables (Sec. II) and
+    the binned points of the last `build`."""
+
+    def __init__(self, origin, cell_size, log2_cells, cyclic_mask, r_max, capacity: int):
+        self._lib = N.lib()
+        self.desc = make_desc(origin, cell_size, log2_cells, cyclic_mask, r_max)
+        h = ctypes.c_void_p()
+        N.check(self._lib.si_grid_create(ctypes.byref(self.desc), int(capacity), ctypes.byref(h)),
+                "si_grid_create")
+        self._h = h
+        self.capacity = int(capacity)
+        self.n = 0
+        self._pos = None
+        self._ids_cap = 0
+        self.build_id = 0
+
+    @classmethod
+    def for_scene(cls, scene, r_max=None, capacity=None):
+        return cls(scene.origin, scene.cell_size, scene.log2_cells, scene.cyclic_mask,
+                   scene.r if r_max is None else r_max, scene.n if capacity is None else capacity)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.si_grid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build(self, pos: torch.Tensor) -> "Grid":
+        pos = _check_points(pos)
+        N.check(self._lib.si_grid_build(self._h, _ptr(pos), pos.shape[0], _stream()), "si_grid_build")
+        self._pos = pos          # keep the input alive while the grid refers to it
+        self.n = pos.shape[0]
+        self.build_id += 1
+        return self
+
+    def sync(self) -> None:
+        N.check(self._lib.si_grid_sync(self._h, _stream()), "si_grid_sync")
+
+    def info(self) -> dict:
+        inf = N.GridInfo()
+        N.check(self._lib.si_grid_get_info(self._h, ctypes.byref(inf)), "si_grid_get_info")
+        return {k: getattr(inf, k) for k, _ in N.GridInfo._fields_}
+
+    def cell_arrays(self):
+        """(cell_start int32[n_cells+1], sorted points float32[n,4], perm int32[n]):
+        copies of the grid's device arrays, for tests and tools."""
+        inf = self.info()
+        start = _device_view(inf["d_cell_start"], (inf["n_cells"] + 1,), "<i4").clone()
+        spos = _device_view(inf["d_sorted_pos"], (inf["n"], 4), "<f4").clone()
+        perm = _device_view(inf["d_perm"], (inf["n"],), "<i4").clone()
+        return start, spos, perm
+
+    # -- queries -------------------------------------------------------------
+    def query_radius(self, r: float, include_self: bool = False, method: str = "sphere",
+                     sort: bool = True, out_offsets=None, out_ids=None, sync_total: bool = True):
+        """All-agents radius query.  Returns (offsets int64[n+1], ids int32[total])."""
+        flags = (N.SI_INCLUDE_SELF if include_self else 0) | \
+                (N.SI_METHOD_CUBE if method == "cube" else 0) | (0 if sort else N.SI_NO_SORT)
+        dev = self._pos.device
+        off = out_offsets if out_offsets is not None else torch.empty(self.n + 1, dtype=torch.int64, device=dev)
+        ids = out_ids
+        if ids is None:
+            cap = self._ids_cap or max(16 * self.n, 1024)
+            ids = torch.empty(cap, dtype=torch.int32, device=dev)
+        total = ctypes.c_int64(0)
+        st = self._lib.si_query_radius(self._h, None, self.n, float(r), flags, _ptr(off), _ptr(ids),
+                                       ids.numel(), ctypes.byref(total) if sync_total else None,
+                                       _stream())
+        if st == N.SI_ERR_CAPACITY and out_ids is None:
+            ids = torch.empty(max(int(total.value), 1), dtype=torch.int32, device=dev)
+            st = self._lib.si_query_radius(self._h, None, self.n, float(r), flags, _ptr(off),
+                                           _ptr(ids), ids.numel(), ctypes.byref(total), _stream())
+        N.check(st, "si_query_radius")
+        if sync_total:
+            self._ids_cap = max(self._ids_cap, int(total.value))
+            return off, ids[: int(total.value)]
+        return off, ids
+
+    def query_knn(self, k: int, r_max=None, include_self: bool = False, with_d2: bool = True,
+                  out=None):
+        """All-agents K nearest within r_max (None = grid's whole region).
+        Returns (ids int32[n,k] padded -1, d2 float32[n,k] or None, counts int32[n])."""
+        dev = self._pos.device
+        if out is None:
+            ids = torch.empty((self.n, k), dtype=torch.int32, device=dev)
+            d2 = torch.empty((self.n, k), dtype=torch.float32, device=dev) if with_d2 else None
+            cnt = torch.empty(self.n, dtype=torch.int32, device=dev)
+        else:
+            ids, d2, cnt = out
+        rm = float("inf") if r_max is None else float(r_max)
+        flags = N.SI_INCLUDE_SELF if include_self else 0
+        N.check(self._lib.si_query_knn(self._h, None, self.n, int(k), rm, flags, _ptr(ids), _ptr(d2),
+                                       _ptr(cnt), _stream()), "si_query_knn")
+        return ids, d2, cnt
+
+    def neighbor_reduce(self, r: float, energy=None, grad=None, grad_scale=None):
+        """Fused smooth-kernel sum over radius neighbors: energy (float64[1]) and,
+        when `grad` is given (float32[n,4]), dE/dx in input order."""
+        N.check(self._lib.si_neighbor_reduce(self._h, float(r), N.SI_KERNEL_POLY6_CUBED, _ptr(energy),
+                                             _ptr(grad), _ptr(grad_scale), _stream()),
+                "si_neighbor_reduce")
+        return energy, grad
+
+
+class NeighborEnergy(torch.autograd.Function):
+    """E(x) = sum_i sum_{j != i, |x_i - x_j| < r} (1 - |x_i - x_j|^2 / r^2)^3.
+
+    forward bins the points and runs the energy kernel; backward runs the
+    hand-written adjoint kernel, which walks the same neighborhoods and writes
+    grad_output * dE/dx directly (the scale is read on the device)."""
+
+    @staticmethod
+    def forward(ctx, pos, grid: Grid, r: float):
+        grid.build(pos.detach())
+        energy = torch.empty(1, dtype=torch.float64, device=pos.device)
+        grid.neighbor_reduce(r, energy=energy)
+        ctx.grid, ctx.r, ctx.build_id = grid, r, grid.build_id
+        return energy[0]
+
+    @staticmethod
+    def backward(ctx, g_out):
+        if g_out is None or not ctx.needs_input_grad[0]:
+            return None, None, None
+        if ctx.grid.build_id != ctx.build_id:
+            raise RuntimeError("the grid was rebuilt between forward and backward")
+        scale = g_out.detach().to(torch.float32).reshape(1).contiguous()
+        out = torch.empty((ctx.grid.n, 4), dtype=torch.float32, device=scale.device)
+        ctx.grid.neighbor_reduce(ctx.r, energy=None, grad=out, grad_scale=scale)
+        return out, None, None
+
+
+def neighbor_energy(pos: torch.Tensor, grid: Grid, r: float) -> torch.Tensor:
+    return NeighborEnergy.apply(pos, grid, r)
+
+
+class Batch:
+    """Many independent scenes served by one fixed set of launches."""
+
+    def __init__(self, scenes, offsets, ids, flags: int = 0):
+        self._lib = N.lib()
+        arr = (N.SceneDesc * len(scenes))()
+        self._keep = []
+        for k, (sc, pos) in enumerate(scenes):
+            pos = _check_points(pos)
+            self._keep.append(pos)
+            arr[k].desc = make_desc(sc.origin, sc.cell_size, sc.log2_cells, sc.cyclic_mask, sc.r)
+            arr[k].d_pos = pos.data_ptr()
+            arr[k].n = pos.shape[0]
+            arr[k].r = float(sc.r)
+            arr[k].d_offsets = offsets[k].data_ptr()
+            arr[k].d_ids = ids[k].data_ptr()
+            arr[k].ids_capacity = ids[k].numel()
+        self._keep += list(offsets) + list(ids)
+        self.n_scenes = len(scenes)
+        h = ctypes.c_void_p()
+        N.check(self._lib.si_batch_create(arr, len(scenes), int(flags), ctypes.byref(h)), "si_batch_create")
+        self._h = h
+
+    def run(self, use_graph: bool = False):
+        N.check(self._lib.si_batch_run(self._h, int(use_graph), _stream()), "si_batch_run")
+
+    def sync(self):
+        tot = (ctypes.c_int64 * self.n_scenes)()
+        N.check(self._lib.si_batch_sync(self._h, tot, _stream()), "si_batch_sync")
+        return list(tot)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.si_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

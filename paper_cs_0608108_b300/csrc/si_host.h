@@ -1,0 +1,132 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "si.h"
+#include "si_internal.cuh"
+
+namespace si {
+
+// Record a message for si_last_error() (per host thread) and return `s`.
+si_status fail(si_status s, const std::string &msg);
+si_status cuda_fail(cudaError_t e, const char *what);
+void count_launch(int k = 1);
+
+#define SI_CUDA_TRY(expr)                                   \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return ::si::cuda_fail(_e, #expr); \
+  } while (0)
+
+#define SI_LAUNCH_CHECK(name)                               \
+  do {                                                      \
+    ::si::count_launch();                                   \
+    cudaError_t _e = cudaGetLastError();                    \
+    if (_e != cudaSuccess) return ::si::cuda_fail(_e, name); \
+  } while (0)
+
+// Optional per-kernel event timing (si_kernel_timing_enable).
+void prof_begin(cudaStream_t st);
+void prof_end(cudaStream_t st, const char *name);
+
+// Launch a kernel with error check and optional timing:
+//   SI_KLAUNCH("name", stream, kernel<<<grid, block, smem, stream>>>(args));
+#define SI_KLAUNCH(name, st, ...)  \
+  do {                             \
+    ::si::prof_begin(st);          \
+    __VA_ARGS__;                   \
+    SI_LAUNCH_CHECK(name);         \
+    ::si::prof_end(st, name);      \
+  } while (0)
+
+// Host copy of the offset tables of one lattice / cyclic mask / extent.
+struct HostTables {
+  std::vector<TabEntry> tab;
+  std::vector<int> tab_end;        // n_max + 1
+  std::vector<TabEntry> spec;
+  std::vector<int> spec_begin;     // spec_shells * 64
+  std::vector<int> spec_end;       // 64 * spec_shells^2
+  int n_max = 0;
+  int spec_shells = 0;
+};
+
+// Largest shell with specialized tables: 64 copies of a shell cost memory
+// (64 x its entries); beyond this the run-time cell test does the same job.
+constexpr int kSpecShellsMax = 8;
+
+// Build the sorted table for b2 <= n_max (Sec. II.A) and the specialized
+// tables (Sec. III.A, Eq. 2).  Fails (returns false) if a cyclic axis would
+// wrap onto itself.
+bool build_tables(const int w[3], unsigned cyc, int n_max, HostTables &out, std::string &err);
+
+// Device copies of the tables.
+struct DevTables {
+  TabEntry *tab = nullptr;
+  int *tab_end = nullptr;
+  TabEntry *spec = nullptr;
+  int *spec_begin = nullptr;
+  int *spec_end = nullptr;
+  int n_max = 0, spec_shells = 0;
+  int64_t entries = 0;
+};
+si_status upload_tables(const HostTables &h, DevTables &d);
+void free_tables(DevTables &d);
+
+// Geometry derived from a descriptor.
+struct Lattice {
+  int w[3];
+  int W;
+  unsigned cyc;
+  float origin[3];
+  float s, inv_s;
+  float L[3];
+  double eps;          // cell-unit margin for conservative culling
+  int n_max;           // table extent
+  bool unbounded;
+};
+si_status make_lattice(const si_grid_desc &d, double r_for_tables, Lattice &lat);
+void fill_griddev(const Lattice &lat, const DevTables &t, GridDev &g);
+
+// Inclusive prefix sum of n values, in place allowed (in == out).
+// Scratch must hold scan_scratch_elems(n) values.
+int64_t scan_scratch_elems(int64_t n);
+si_status scan_inclusive_i32(const int *in, int *out, int64_t n, int *scratch, cudaStream_t st);
+si_status scan_inclusive_i64(const long long *in, long long *out, int64_t n, long long *scratch,
+                             cudaStream_t st);
+
+// FP32 guard band around r^2 for a lattice (see si_grid.cu for the bound).
+Band make_band(const Lattice &lat, float r);
+// Band coefficients for comparing two FP32 squared distances (KNN order).
+struct PairBand {
+  float c2, c1;        // |d2f - D2| <= c2 * d2 + c1 * sqrt(d2)
+};
+PairBand make_pair_band(const Lattice &lat);
+
+}  // namespace si
+
+struct si_grid {
+  si_grid_desc desc;
+  si::Lattice lat;
+  int64_t cap = 0, n = 0;
+  int64_t n_cells = 0;
+  si::DevTables tables;
+  // device arrays
+  uint2 *key_slot = nullptr;     // cap: (cell, rank in cell)
+  int *cell_count = nullptr;     // n_cells
+  int *cell_start = nullptr;     // n_cells + 1
+  float4 *spos = nullptr;        // cap
+  int *perm = nullptr;           // cap
+  int *scan_i32 = nullptr;       // scan scratch for cells
+  long long *scan_i64 = nullptr; // scan scratch for offsets
+  int *status = nullptr;         // device status word
+  int *longq = nullptr;          // cap + 1: [0] = count, then query ids of long lists
+  double *partial = nullptr;     // reduce partial sums
+  int64_t partial_len = 0;
+  long long *h_pinned = nullptr; // pinned host scratch (2 values)
+  si::GridDev dev() const;
+};

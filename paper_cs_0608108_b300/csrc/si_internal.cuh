@@ -1,0 +1,226 @@
+// Internal definitions shared by the CUDA translation units of the library.
+// Method: Brodu, "Spherical Indexing for Neighborhood Queries" (Sec. II-III).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "si.h"
+
+namespace si {
+
+// ---------------------------------------------------------------------------
+// Offset table entry (Sec. II.A, Sec. II.B): one cell offset of the sorted
+// center-to-edge array.  16 bytes so a warp reads whole sectors.
+//   unp   offset in the unpacked layout (Y field above Z and X, see below),
+//         each field in (w+1)-bit two's complement: after the SWAR add the
+//         field's bit w is set exactly when that coordinate left [0, G).
+//   ox..  the offset itself (cell units), for the exact cell test (Eq. 1)
+//   dirs  6 direction bits: bit 2a for +axis a, bit 2a+1 for -axis a
+//   b2    minimum-bound squared distance sum_a max(|o_a|-1, 0)^2 (Fig. 2)
+// ---------------------------------------------------------------------------
+struct __align__(16) TabEntry {
+  unsigned long long unp;
+  signed char ox, oy, oz;
+  unsigned char dirs;
+  int b2;
+};
+static_assert(sizeof(TabEntry) == 16, "table entry must be 16 bytes");
+
+// Everything a query kernel needs, passed by value (kernel parameter space).
+struct GridDev {
+  const float4 *spos;        // sorted positions (cell order)
+  const int *perm;           // sorted slot -> input index
+  const int *cell_start;     // n_cells + 1
+  int n;
+  float ox, oy, oz;          // region origin
+  float inv_s;               // 1 / cell side (float32)
+  float Lx, Ly, Lz;          // box sides (float32, exact: s * 2^w)
+  int wx, wy, wz, W;
+  unsigned cyc;              // cyclic mask
+  unsigned outside;          // 1 << W, the outside cell
+  unsigned long long valid;  // bits of the three fields in unpacked form
+  unsigned long long gx, gy, gz;   // guard bit of each field
+  unsigned long long guard_non;    // guard bits of the non-cyclic fields
+  const TabEntry *tab;       // main sorted table
+  const int *tab_end;        // tab_end[n] = entries with b2 <= n, n = 0..n_max
+  int n_max;
+  const TabEntry *spec;      // specialized tables, concatenated
+  const int *spec_begin;     // [shell * 64 + mask]
+  const int *spec_end;       // [64 * shell^2 + mask * (2 shell + 1) + (n - shell^2)]
+  int spec_shells;           // shells 0 .. spec_shells-1 have specialized tables
+  float eps;                 // conservative margin in cell units
+  int *status;               // device status word (bit flags below)
+};
+
+enum : int { ST_INVALID = 1, ST_CAPACITY = 2, ST_INTERNAL = 4, ST_TIMEOUT = 8 };
+
+// ---------------------------------------------------------------------------
+// Cell of one coordinate (Sec. II.B: power-of-two lattice; Sec. II.B last
+// paragraph: one outside cell for objects out of the region).  The same
+// function bins points and locates query centers, so both agree bit for bit.
+// rel * inv_s is >= 0 here, so truncation is floor; the clamp to G-1 keeps a
+// coordinate that rounds up to G (rel just below L) in the last cell.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int axis_cell(float x, float o, float L, float inv_s, int w,
+                                         bool cyclic, bool &outside, bool &bad) {
+  const float rel = x - o;
+  if (!(rel >= 0.f && rel < L)) {          // false for NaN too
+    if (cyclic || !(fabsf(x) <= 3.0e38f)) bad = true;
+    outside = true;
+    return 0;
+  }
+  const int c = (int)(rel * inv_s);
+  return min(c, (1 << w) - 1);
+}
+
+// Packed location: bits z | y | x (Sec. II.B), also the cell's memory index.
+__device__ __forceinline__ unsigned pack3(int cx, int cy, int cz, const GridDev &g) {
+  return ((unsigned)cz << (g.wx + g.wy)) | ((unsigned)cy << g.wx) | (unsigned)cx;
+}
+
+// Unpacked location: Y moved up by the packed width W, leaving carry gaps.
+__device__ __forceinline__ unsigned long long unpack3(int cx, int cy, int cz, const GridDev &g) {
+  return ((unsigned long long)cy << (g.W + g.wx)) |
+         ((unsigned long long)cz << (g.wx + g.wy)) | (unsigned long long)cx;
+}
+
+// Pack a masked unpacked location: shift Y back down and OR the low part.
+__device__ __forceinline__ unsigned repack(unsigned long long u, const GridDev &g) {
+  return (unsigned)(u >> g.W) | (unsigned)(u & ((1ull << g.W) - 1ull));
+}
+
+// ---------------------------------------------------------------------------
+// Canonical FP64 predicate value (identical definition on every path):
+//   a = |xj - xi|, cyclic: min(a, L - a);  D2 = (ax*ax + ay*ay) + az*az,
+// each operation rounded to nearest, no fused multiply-add.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double canon_gap(float a, float b, float L, bool cyclic) {
+  double d = fabs((double)b - (double)a);
+  if (cyclic) {
+    const double w = (double)L - d;
+    if (w < d) d = w;
+  }
+  return d;
+}
+
+__device__ __forceinline__ double canon_d2(const float4 &q, const float4 &p, const GridDev &g) {
+  const double ax = canon_gap(q.x, p.x, g.Lx, g.cyc & 1u);
+  const double ay = canon_gap(q.y, p.y, g.Ly, (g.cyc >> 1) & 1u);
+  const double az = canon_gap(q.z, p.z, g.Lz, (g.cyc >> 2) & 1u);
+  double s = __dmul_rn(ax, ax);
+  s = __dadd_rn(s, __dmul_rn(ay, ay));
+  s = __dadd_rn(s, __dmul_rn(az, az));
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Query geometry: the center's cell, its unpacked location and the distances
+// zeta from the center to its own cell faces (Sec. III.A, Fig. 3), in cell
+// units, shrunk by the margin eps so every cell rejection stays conservative
+// under float32 binning (a point may sit a few ulps outside its cell).
+// ---------------------------------------------------------------------------
+struct QueryGeom {
+  float4 q;                  // query position
+  float u[3];                // query position in cell units (relative to origin)
+  int c[3];                  // query cell (valid when !outside)
+  float phi[3];              // sub-cell position in [0, 1] (cell units)
+  float zp[3], zn[3];        // zeta toward +axis and -axis, shrunk by eps
+  unsigned long long cu;     // unpacked center cell
+  bool outside;              // query center outside the region
+};
+
+__device__ __forceinline__ QueryGeom make_geom(const float4 &q, const GridDev &g) {
+  QueryGeom Q;
+  Q.q = q;
+  bool out = false, bad = false;
+  Q.c[0] = axis_cell(q.x, g.ox, g.Lx, g.inv_s, g.wx, g.cyc & 1u, out, bad);
+  Q.c[1] = axis_cell(q.y, g.oy, g.Ly, g.inv_s, g.wy, (g.cyc >> 1) & 1u, out, bad);
+  Q.c[2] = axis_cell(q.z, g.oz, g.Lz, g.inv_s, g.wz, (g.cyc >> 2) & 1u, out, bad);
+  Q.outside = out;
+  Q.u[0] = (q.x - g.ox) * g.inv_s;
+  Q.u[1] = (q.y - g.oy) * g.inv_s;
+  Q.u[2] = (q.z - g.oz) * g.inv_s;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float phi = fminf(fmaxf(Q.u[a] - (float)Q.c[a], 0.f), 1.f);
+    Q.phi[a] = phi;
+    Q.zp[a] = fmaxf(1.f - phi - g.eps, 0.f);
+    Q.zn[a] = fmaxf(phi - g.eps, 0.f);
+  }
+  Q.cu = unpack3(Q.c[0], Q.c[1], Q.c[2], g);
+  return Q;
+}
+
+// Exact minimum squared distance (cell units) from the query center to the
+// cell at offset o (Sec. III.A, Eq. 1 left side): sum over non-zero offset
+// axes of (b_a + zeta_a)^2.  With zeta shrunk by eps this never exceeds the
+// true value.
+__device__ __forceinline__ float cell_t2(const TabEntry &e, const QueryGeom &Q) {
+  float t2 = 0.f;
+  const int o[3] = {e.ox, e.oy, e.oz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float gap = 0.f;
+    if (o[a] > 0) gap = (float)(o[a] - 1) + Q.zp[a];
+    else if (o[a] < 0) gap = (float)(-o[a] - 1) + Q.zn[a];
+    t2 = fmaf(gap, gap, t2);
+  }
+  return t2;
+}
+
+// Farthest squared distance (cell units) from the query to any point of the
+// cell at offset o, grown by eps: a cell below this bound lies wholly inside
+// the sphere (Sec. III.A, unconditional inclusion, exact-corner reading).
+__device__ __forceinline__ float cell_far2(const TabEntry &e, const QueryGeom &Q, float eps) {
+  float f2 = 0.f;
+  const int o[3] = {e.ox, e.oy, e.oz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float lo = fabsf((float)o[a] - Q.phi[a]), hi = fabsf((float)(o[a] + 1) - Q.phi[a]);
+    const float far = fmaxf(lo, hi) + eps;
+    f2 = fmaf(far, far, f2);
+  }
+  return f2;
+}
+
+// Result of translating a table entry to the query's cell (Sec. II.B): the
+// packed cell key, or the outside cell, and the image shift of each cyclic
+// axis whose coordinate wrapped (-1, 0, +1 box lengths).
+struct Target {
+  unsigned key;
+  bool outside;
+  bool wrapped;
+  float qx, qy, qz;          // query position moved by the image shift
+};
+
+__device__ __forceinline__ Target translate(const TabEntry &e, const QueryGeom &Q, const GridDev &g) {
+  Target t;
+  const unsigned long long s = Q.cu + e.unp;          // SWAR add of all fields
+  t.outside = (s & g.guard_non) != 0ull;
+  t.key = t.outside ? g.outside : repack(s & g.valid, g);
+  const bool wx = (s & g.gx) != 0ull, wy = (s & g.gy) != 0ull, wz = (s & g.gz) != 0ull;
+  t.wrapped = !t.outside && (wx | wy | wz);
+  // wrapped on +a: the candidate's near image is x + L, so compare against q - L
+  t.qx = Q.q.x - (wx ? (e.ox > 0 ? g.Lx : -g.Lx) : 0.f);
+  t.qy = Q.q.y - (wy ? (e.oy > 0 ? g.Ly : -g.Ly) : 0.f);
+  t.qz = Q.q.z - (wz ? (e.oz > 0 ? g.Lz : -g.Lz) : 0.f);
+  return t;
+}
+
+__device__ __forceinline__ int isqrt_small(int n) {
+  int r = (int)sqrtf((float)n);
+  while (r * r > n) --r;
+  while ((r + 1) * (r + 1) <= n) ++r;
+  return r;
+}
+
+// FP32 guard band around r^2 (absolute, world units squared): pairs with an
+// FP32 squared distance inside [lo, hi] are re-tested with canon_d2.
+struct Band {
+  float lo, hi;        // pairs not crossing a cyclic boundary
+  float lo_w, hi_w;    // pairs compared through a wrapped image
+  double r2;           // canonical (double)r * (double)r
+};
+
+}  // namespace si

@@ -1,0 +1,133 @@
+// The cell walks of one query, as device templates shared by the radius,
+// reduction and batched kernels.
+#pragma once
+
+#include "si_internal.cuh"
+
+namespace si {
+
+// Per-call culling parameters (cell units).
+struct WalkParams {
+  float dg;        // query distance d = r / s, grown by the margin eps
+  int rt_b2;       // run-time exact cell test for entries with b2 >= rt_b2
+  int incl_b2;     // unconditional-inclusion test for entries with b2 <= incl_b2 (-1: off)
+  float incl_d2;   // (d - eps)^2: far corner below this => whole cell inside
+};
+
+// Spherical-index walk (Sec. II.A, Sec. III.A).  The main table is read from
+// the center up to the shell floor(d); the rest comes from the specialized
+// table chosen by the 6 direction bits f < zeta (Eq. 2); a cell whose b2 is
+// at or above rt_b2 gets the exact test t^2 > d^2 (Eq. 1).  Offsets that
+// leave the region on a non-cyclic axis all map to the one outside cell,
+// which is visited at most once.  visit(Target, bool whole_cell_inside).
+template <class V>
+__device__ __forceinline__ void walk_sphere(const GridDev &g, const QueryGeom &Q, const WalkParams &P,
+                                            V &visit) {
+  const float dg2 = P.dg * P.dg;
+  const int n = min((int)dg2, g.n_max);
+  const int fl = isqrt_small(n);
+  const float f = P.dg - (float)fl;
+  unsigned mask = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    mask |= (f < Q.zp[a]) ? (1u << (2 * a)) : 0u;
+    mask |= (f < Q.zn[a]) ? (1u << (2 * a + 1)) : 0u;
+  }
+  bool out_seen = false;
+  auto entry = [&](const TabEntry &e) {
+    if (e.b2 >= P.rt_b2 && cell_t2(e, Q) > dg2) return;
+    const Target t = translate(e, Q, g);
+    if (t.outside) {
+      if (out_seen) return;
+      out_seen = true;
+    }
+    const bool full = !t.outside && e.b2 <= P.incl_b2 && cell_far2(e, Q, g.eps) <= P.incl_d2;
+    visit(t, full);
+  };
+  const int main_end = fl > 0 ? __ldg(g.tab_end + fl * fl - 1) : 0;
+  for (int i = 0; i < main_end; ++i) entry(g.tab[i]);
+  if (fl < g.spec_shells) {
+    const int sb = __ldg(g.spec_begin + fl * 64 + (int)mask);
+    const int se = __ldg(g.spec_end + 64 * fl * fl + (int)mask * (2 * fl + 1) + (n - fl * fl));
+    for (int i = sb; i < se; ++i) entry(g.spec[i]);
+  } else {
+    const int te = __ldg(g.tab_end + n);
+    for (int i = main_end; i < te; ++i) entry(g.tab[i]);
+  }
+}
+
+// Bin-lattice walk (Sec. I; Sec. III.C parallelepiped): every cell of the
+// sphere's bounding cube, clipped to the region on non-cyclic axes (the
+// outside cell visited once if the cube leaves the region), wrapped with an
+// image shift on cyclic axes.  Also serves query centers outside the region.
+template <class V>
+__device__ __forceinline__ void walk_cube(const GridDev &g, const QueryGeom &Q, float dg, V &visit) {
+  int lo[3], hi[3];
+  bool leaves = false;
+  const int w[3] = {g.wx, g.wy, g.wz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int G = 1 << w[a];
+    float fl = floorf(Q.u[a] - dg), fh = floorf(Q.u[a] + dg);
+    fl = fmaxf(fminf(fl, 4096.f), -4096.f);
+    fh = fmaxf(fminf(fh, 4096.f), -4096.f);
+    lo[a] = (int)fl;
+    hi[a] = (int)fh;
+    if (!((g.cyc >> a) & 1u)) {
+      if (lo[a] < 0 || hi[a] >= G) leaves = true;
+      lo[a] = max(lo[a], 0);
+      hi[a] = min(hi[a], G - 1);
+    }
+  }
+  const float Ls[3] = {g.Lx, g.Ly, g.Lz};
+  for (int tz = lo[2]; tz <= hi[2]; ++tz) {
+    const int Gz = 1 << g.wz;
+    const int cz = tz & (Gz - 1);
+    const float sz = tz < 0 ? -Ls[2] : (tz >= Gz ? Ls[2] : 0.f);
+    for (int ty = lo[1]; ty <= hi[1]; ++ty) {
+      const int Gy = 1 << g.wy;
+      const int cy = ty & (Gy - 1);
+      const float sy = ty < 0 ? -Ls[1] : (ty >= Gy ? Ls[1] : 0.f);
+      for (int tx = lo[0]; tx <= hi[0]; ++tx) {
+        const int Gx = 1 << g.wx;
+        const int cx = tx & (Gx - 1);
+        const float sx = tx < 0 ? -Ls[0] : (tx >= Gx ? Ls[0] : 0.f);
+        Target t;
+        t.key = pack3(cx, cy, cz, g);
+        t.outside = false;
+        t.wrapped = (sx != 0.f) | (sy != 0.f) | (sz != 0.f);
+        t.qx = Q.q.x - sx;
+        t.qy = Q.q.y - sy;
+        t.qz = Q.q.z - sz;
+        visit(t, false);
+      }
+    }
+  }
+  if (leaves) {
+    Target t;
+    t.key = g.outside;
+    t.outside = true;
+    t.wrapped = false;
+    t.qx = Q.q.x;
+    t.qy = Q.q.y;
+    t.qz = Q.q.z;
+    visit(t, false);
+  }
+}
+
+// FP32 candidate test with FP64 recheck inside the guard band.  The outside
+// cell holds arbitrary positions (any image may be nearest), so its
+// candidates always take the FP64 path.
+__device__ __forceinline__ bool pair_hit(const GridDev &g, const QueryGeom &Q, const Target &t,
+                                         const Band &B, const float4 &p) {
+  if (t.outside) return canon_d2(Q.q, p, g) <= B.r2;
+  const float dx = p.x - t.qx, dy = p.y - t.qy, dz = p.z - t.qz;
+  const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  const float lo = t.wrapped ? B.lo_w : B.lo;
+  const float hi = t.wrapped ? B.hi_w : B.hi;
+  if (d2 <= lo) return true;
+  if (d2 > hi) return false;
+  return canon_d2(Q.q, p, g) <= B.r2;
+}
+
+}  // namespace si

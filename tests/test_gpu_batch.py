@@ -1,0 +1,63 @@
+"""Parity of the batched persistent path (all scenes in one set of launches,
+optionally replayed from a CUDA graph) with the FP64 oracle, scene by scene."""
+import numpy as np
+import pytest
+import torch
+
+from paper_cs_0608108_b300 import Batch, _native, synth
+
+from gpu_helpers import assert_csr_equal, gpu_radius, oracle_radius, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def make_batch(scenes, caps=None):
+    pos = [to_dev(s.pos) for s in scenes]
+    offs = [torch.empty(s.n + 1, dtype=torch.int64, device="cuda") for s in scenes]
+    ids = [torch.empty(max(int(c), 1), dtype=torch.int32, device="cuda")
+           for c in (caps or [64 * s.n + 64 for s in scenes])]
+    return Batch(list(zip(scenes, pos)), offs, ids), offs, ids
+
+
+def test_small_uneven_batch_matches_oracle_and_graph_replays():
+    scenes = synth.batched_scenes(24, seed=123, n_lo=10, n_hi=20_000)
+    scenes[3].pos = scenes[3].pos[:0]          # an empty scene
+    b, offs, ids = make_batch(scenes)
+    b.run(use_graph=False)
+    totals = b.sync()
+    ref = []
+    for k, sc in enumerate(scenes):
+        off_o, ids_o = oracle_radius(sc)
+        o = offs[k].cpu().numpy()
+        assert totals[k] == off_o[-1]
+        assert_csr_equal(o, ids[k].cpu().numpy()[: o[-1]], off_o, ids_o)
+        ref.append((off_o, ids_o))
+    for _ in range(2):
+        for t in ids:
+            t.fill_(-7)
+        b.run(use_graph=True)
+        b.sync()
+        for k, (off_o, ids_o) in enumerate(ref):
+            o = offs[k].cpu().numpy()
+            assert_csr_equal(o, ids[k].cpu().numpy()[: o[-1]], off_o, ids_o)
+
+
+def test_batch_equals_looped_plain_path_on_seeded_scenes():
+    scenes = synth.batched_scenes(16, seed=7, n_lo=1000, n_hi=60_000)
+    b, offs, ids = make_batch(scenes)
+    b.run(use_graph=True)
+    b.sync()
+    for k, sc in enumerate(scenes):
+        off_p, ids_p = gpu_radius(sc)
+        o = offs[k].cpu().numpy()
+        assert np.array_equal(o, off_p)
+        assert np.array_equal(ids[k].cpu().numpy()[: o[-1]], ids_p)
+
+
+def test_batch_capacity_overflow_is_reported():
+    scenes = synth.batched_scenes(4, seed=9, n_lo=2000, n_hi=3000)
+    b, offs, ids = make_batch(scenes, caps=[1, 10 ** 6, 10 ** 6, 10 ** 6])
+    b.run()
+    with pytest.raises(_native.SIError) as ei:
+        b.sync()
+    assert ei.value.status == _native.SI_ERR_CAPACITY

@@ -1,0 +1,78 @@
+"""Parity of the CUDA K-nearest query with the FP64 oracle: ids (ordered by
+(D2, index)) and counts bit-exact; the FP32 distances within their bound."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_cs_0608108_b300 import Grid, synth
+
+from gpu_helpers import gpu_grid, to_dev
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -24
+
+
+def run_knn(scene, k, r_max, grid_r_max=None):
+    g = gpu_grid(scene, r_max=grid_r_max if grid_r_max is not None else r_max)
+    ids, d2, cnt = g.query_knn(k, r_max=r_max)
+    g.sync()
+    return ids.cpu().numpy(), d2.cpu().numpy(), cnt.cpu().numpy()
+
+
+def check(scene, k, r_max, ids, d2, cnt, queries):
+    oi, od, oc = oracle.knn(scene.pos, scene.pos[queries], scene.box, scene.cyclic_mask, k, r_max,
+                            queries)
+    assert np.array_equal(cnt[queries], oc)
+    assert np.array_equal(ids[queries], oi)
+    fin = np.isfinite(od)
+    got = d2[queries].astype(np.float64)
+    assert np.all(np.isinf(got[~fin]))
+    L = max(scene.box)
+    assert np.all(np.abs(got[fin] - od[fin]) <= 12 * U * od[fin] + 16 * U * L * np.sqrt(od[fin]) + 1e-30)
+
+
+def test_tiny_config_k8_unbounded_exact():
+    scene = synth.tiny_scene()
+    ids, d2, cnt = run_knn(scene, 8, None)
+    check(scene, 8, None, ids, d2, cnt, np.arange(scene.n))
+    assert np.all(cnt == 8)
+
+
+@pytest.mark.parametrize("mask", [7, 3, 0, 4])
+@pytest.mark.parametrize("k", [1, 5, 16, 64])
+def test_masks_and_k_within_r_max(mask, k):
+    pos = synth.uniform_points(30_000, 40 + mask)
+    scene = synth.Scene(pos, (0, 0, 0), 1 / 32, (5, 5, 5), mask, 4 / 32)
+    ids, d2, cnt = run_knn(scene, k, scene.r)
+    check(scene, k, scene.r, ids, d2, cnt, np.arange(0, scene.n, 3))
+
+
+def test_ties_on_a_coarse_lattice_broken_by_index():
+    rng = np.random.default_rng(2)
+    pos = np.zeros((20_000, 4), np.float32)
+    pos[:, :3] = rng.integers(0, 64, size=(20_000, 3)) / 64.0
+    scene = synth.Scene(pos, (0, 0, 0), 1 / 16, (4, 4, 4), 7, 3 / 16)
+    ids, d2, cnt = run_knn(scene, 12, scene.r)
+    check(scene, 12, scene.r, ids, d2, cnt, np.arange(scene.n))
+
+
+def test_duplicates_and_points_outside_region():
+    pos = synth.uniform_points(8000, 8)
+    pos[100:140] = pos[7]                  # 40 copies of point 7: distance-0 ties
+    pos[:20, 2] = np.float32(1.3)          # outside on a non-cyclic z
+    scene = synth.Scene(pos, (0, 0, 0), 1 / 16, (4, 4, 4), 3, 2 / 16)
+    ids, d2, cnt = run_knn(scene, 16, scene.r)
+    check(scene, 16, scene.r, ids, d2, cnt, np.arange(scene.n))
+
+
+@pytest.mark.parametrize("k", [16, 64])
+def test_full_size_4m_config_sampled(k):
+    scene = synth.knn_4m_scene()
+    ids, d2, cnt = run_knn(scene, k, scene.r)
+    q = np.random.default_rng(k).choice(scene.n, 600, replace=False)
+    check(scene, k, scene.r, ids, d2, cnt, q)
+    if k == 64:
+        # about half the points have fewer than 64 neighbors within 4 cells
+        assert 0.3 < (cnt < 64).mean() < 0.7
