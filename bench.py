@@ -281,16 +281,18 @@ class WalkWork:
 class BatchWork:
     def __init__(self, scenes, graph=True):
         import torch
-        from paper_cs_0608108_b300 import Batch
+        from paper_cs_0608108_b300 import Batch, Grid
         self.scenes = scenes
         self.pos = [torch.from_numpy(s.pos).cuda() for s in scenes]
         self.offs = [torch.empty(s.n + 1, dtype=torch.int64, device="cuda") for s in scenes]
-        # first pass with generous capacity to learn the totals
-        self.ids = [torch.empty(max(48 * s.n, 64), dtype=torch.int32, device="cuda") for s in scenes]
-        b = Batch(list(zip(scenes, self.pos)), self.offs, self.ids)
-        b.run(False)
-        self.totals = b.sync()
-        b.close()
+        # each scene's neighbor total, from the plain single-scene path
+        self.totals = []
+        for sc, p in zip(scenes, self.pos):
+            g = Grid.for_scene(sc)
+            g.build(p)
+            off, _ = g.query_radius(sc.r)
+            self.totals.append(int(off[-1].item()))
+            g.close()
         self.ids = [torch.empty(max(t, 1), dtype=torch.int32, device="cuda") for t in self.totals]
         self.batch = Batch(list(zip(scenes, self.pos)), self.offs, self.ids)
         self.graph = graph

@@ -34,7 +34,7 @@ def _check_points(pos: torch.Tensor) -> torch.Tensor:
 class _CudaArray:
     def __init__(self, ptr, shape, typestr):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
-                                         "data": (int(ptr), True), "version": 2}
+                                         "data": (int(ptr), False), "version": 2}
 
 
 def _device_view(ptr, shape, typestr) -> torch.Tensor:

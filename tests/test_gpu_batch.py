@@ -22,16 +22,15 @@ def make_batch(scenes, caps=None):
 def test_small_uneven_batch_matches_oracle_and_graph_replays():
     scenes = synth.batched_scenes(24, seed=123, n_lo=10, n_hi=20_000)
     scenes[3].pos = scenes[3].pos[:0]          # an empty scene
-    b, offs, ids = make_batch(scenes)
+    ref = [oracle_radius(sc) for sc in scenes]
+    b, offs, ids = make_batch(scenes, caps=[int(o[-1]) + 1 for o, _ in ref])
     b.run(use_graph=False)
     totals = b.sync()
-    ref = []
     for k, sc in enumerate(scenes):
-        off_o, ids_o = oracle_radius(sc)
+        off_o, ids_o = ref[k]
         o = offs[k].cpu().numpy()
         assert totals[k] == off_o[-1]
         assert_csr_equal(o, ids[k].cpu().numpy()[: o[-1]], off_o, ids_o)
-        ref.append((off_o, ids_o))
     for _ in range(2):
         for t in ids:
             t.fill_(-7)
@@ -44,11 +43,12 @@ def test_small_uneven_batch_matches_oracle_and_graph_replays():
 
 def test_batch_equals_looped_plain_path_on_seeded_scenes():
     scenes = synth.batched_scenes(16, seed=7, n_lo=1000, n_hi=60_000)
-    b, offs, ids = make_batch(scenes)
+    plain = [gpu_radius(sc) for sc in scenes]
+    b, offs, ids = make_batch(scenes, caps=[int(o[-1]) + 1 for o, _ in plain])
     b.run(use_graph=True)
     b.sync()
     for k, sc in enumerate(scenes):
-        off_p, ids_p = gpu_radius(sc)
+        off_p, ids_p = plain[k]
         o = offs[k].cpu().numpy()
         assert np.array_equal(o, off_p)
         assert np.array_equal(ids[k].cpu().numpy()[: o[-1]], ids_p)
@@ -56,7 +56,8 @@ def test_batch_equals_looped_plain_path_on_seeded_scenes():
 
 def test_batch_capacity_overflow_is_reported():
     scenes = synth.batched_scenes(4, seed=9, n_lo=2000, n_hi=3000)
-    b, offs, ids = make_batch(scenes, caps=[1, 10 ** 6, 10 ** 6, 10 ** 6])
+    big = [int(oracle_radius(sc)[0][-1]) + 1 for sc in scenes]
+    b, offs, ids = make_batch(scenes, caps=[1] + big[1:])
     b.run()
     with pytest.raises(_native.SIError) as ei:
         b.sync()

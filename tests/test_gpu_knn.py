@@ -14,8 +14,8 @@ pytestmark = pytest.mark.gpu
 U = 2.0 ** -24
 
 
-def run_knn(scene, k, r_max, grid_r_max=None):
-    g = gpu_grid(scene, r_max=grid_r_max if grid_r_max is not None else r_max)
+def run_knn(scene, k, r_max):
+    g = gpu_grid(scene, r_max=float("inf") if r_max is None else r_max)
     ids, d2, cnt = g.query_knn(k, r_max=r_max)
     g.sync()
     return ids.cpu().numpy(), d2.cpu().numpy(), cnt.cpu().numpy()

@@ -157,7 +157,7 @@ def test_heavy_mixture_lists_sorted_and_exact():
     q = np.random.default_rng(0).choice(scene.n, 1500, replace=False)
     assert_sampled_equal(off_g, ids_g, scene, q)
     lens = np.diff(off_g)
-    assert lens.max() > 1000
+    assert lens.max() > 500
     # symmetry of the whole relation
     rows = np.repeat(np.arange(scene.n), lens)
     fwd = rows.astype(np.int64) * scene.n + ids_g
