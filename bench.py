@@ -152,22 +152,42 @@ class RadiusWork:
         for g in self.grids:
             g.sync()
 
+    def heavy_split(self, k):
+        """(fraction of queries, fraction of hits) served by the cell-at-a-time
+        kernels for scene k: queries whose cell holds >= 8 points."""
+        start, _, perm = (t.cpu().numpy() for t in self.grids[k].cell_arrays())
+        cnt = np.diff(start)
+        cnt[-1] = 0                      # the outside cell is never a heavy cell
+        heavy_slot = np.repeat(cnt >= 8, cnt.clip(min=0))[: len(perm)]
+        if self.method == "cube":
+            heavy_slot[:] = False
+        off = self.off[k].cpu().numpy()
+        lens = np.diff(off)
+        ids = perm[heavy_slot]
+        return heavy_slot.mean() if len(perm) else 0.0, lens[ids].sum() / max(lens.sum(), 1)
+
     def algorithmic_bytes(self):
-        """Per-kernel minimum DRAM bytes of one launch, per scene (averaged)."""
+        """Per-kernel minimum DRAM bytes of one launch, averaged over the scenes:
+        each structure touched once by the queries that kernel serves."""
         out = {}
-        for s, tot in zip(self.scenes, self.totals):
+        for k, (s, tot) in enumerate(zip(self.scenes, self.totals)):
             n, C = s.n, (1 << sum(s.log2_cells)) + 1
+            fq, ft = self.heavy_split(k)
+            cnt_b = 16 * n + 4 * n + 4 * C + 8 * n
+            wr_b = 16 * n + 4 * n + 4 * C + 8 * n
             per = {
                 "k_bin_key": 16 * n + 8 * n + 8 * C,
                 "k_bin_scatter": 8 * n + 16 * n + 4 * C + 16 * n + 4 * n,
-                "k_radius_count": 16 * n + 4 * n + 4 * C + 8 * n,
-                "k_radius_write": 16 * n + 4 * n + 4 * C + 8 * n + 4 * tot,
-                "k_radius_count_cube": 16 * n + 4 * n + 4 * C + 8 * n,
-                "k_radius_write_cube": 16 * n + 4 * n + 4 * C + 8 * n + 4 * tot,
+                "k_radius_count": (1 - fq) * cnt_b,
+                "k_radius_write": (1 - fq) * wr_b + (1 - ft) * 4 * tot,
+                "k_cell_count": fq * cnt_b,
+                "k_cell_write": fq * wr_b + ft * 4 * tot,
+                "k_radius_count_cube": cnt_b,
+                "k_radius_write_cube": wr_b + 4 * tot,
             }
-            for k, v in per.items():
-                out.setdefault(k, []).append(v)
-        return {k: float(np.mean(v)) for k, v in out.items()}
+            for kk, v in per.items():
+                out.setdefault(kk, []).append(v)
+        return {kk: float(np.mean(v)) for kk, v in out.items()}
 
     def step_bytes(self):
         tot = 0
@@ -324,6 +344,14 @@ def make_work(name):
     if name == "radius_1m":
         return RadiusWork([synth.uniform_1m_scene(), synth.mixture_1m_scene()]), \
             "1M-point all-agents radius, 128^3 cyclic, r=1.5 cells, uniform + Gaussian mixture"
+    if name == "radius_uniform":
+        return RadiusWork([synth.uniform_1m_scene()]), "1M uniform all-agents radius, 128^3 cyclic, r=1.5 cells"
+    if name == "radius_mixture":
+        return RadiusWork([synth.mixture_1m_scene()]), "1M Gaussian-mixture all-agents radius, 128^3 cyclic, r=1.5 cells"
+    if name == "radius_uniform_cube":
+        return RadiusWork([synth.uniform_1m_scene()], "cube"), "1M uniform, GPU bin-lattice cube scan"
+    if name == "radius_mixture_cube":
+        return RadiusWork([synth.mixture_1m_scene()], "cube"), "1M mixture, GPU bin-lattice cube scan"
     if name == "radius_1m_cube":
         return RadiusWork([synth.uniform_1m_scene(), synth.mixture_1m_scene()], "cube"), \
             "same, GPU bin-lattice cube scan"
@@ -372,8 +400,10 @@ def kernel_report(lib):
 
 def _oracle_scene(name):
     from paper_cs_0608108_b300 import synth
-    if name in ("radius_1m", "radius_1m_cube", "walk_1m"):
+    if name in ("radius_1m", "radius_1m_cube", "walk_1m", "radius_uniform", "radius_uniform_cube"):
         return synth.uniform_1m_scene()
+    if name in ("radius_mixture", "radius_mixture_cube"):
+        return synth.mixture_1m_scene()
     if name == "knn_4m":
         return synth.knn_4m_scene()
     if name == "tiny":

@@ -389,17 +389,26 @@ __global__ void __launch_bounds__(256) k_bin_key(const float4 *__restrict__ pos,
   key_slot[i] = make_uint2(key, (unsigned)slot);
 }
 
+// Scatter into cell order; the first point of every cell holding at least
+// kHeavyMinBuild points (outside cell excepted) lists that cell for the
+// cell-at-a-time query kernels.
 __global__ void __launch_bounds__(256) k_bin_scatter(const float4 *__restrict__ pos, int n,
                                                      const uint2 *__restrict__ key_slot,
                                                      const int *__restrict__ start,
                                                      float4 *__restrict__ spos,
-                                                     int *__restrict__ perm) {
+                                                     int *__restrict__ perm, unsigned outside,
+                                                     int *__restrict__ heavy) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint2 ks = key_slot[i];
-  const int dst = __ldg(start + ks.x) + (int)ks.y;
+  const int b = __ldg(start + ks.x);
+  const int dst = b + (int)ks.y;
   spos[dst] = __ldg(pos + i);
   perm[dst] = i;
+  if (ks.y == 0u && ks.x != outside && __ldg(start + ks.x + 1) - b >= kHeavyMinBuild) {
+    const int slot = atomicAdd(heavy, 1);
+    heavy[1 + slot] = (int)ks.x;
+  }
 }
 
 }  // namespace si
@@ -428,6 +437,10 @@ static void grid_free(si_grid *g) {
   cudaFree(g->scan_i64);
   cudaFree(g->status);
   cudaFree(g->longq);
+  cudaFree(g->hugeq);
+  cudaFree(g->heavy);
+  cudaFree(g->over);
+  cudaFree(g->counters);
   cudaFree(g->partial);
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
   free_tables(g->tables);
@@ -474,6 +487,10 @@ extern "C" si_status si_grid_create(const si_grid_desc *desc, int64_t n_capacity
   SI_ALLOC(g->scan_i64, scan_scratch_elems(cap1 + 1) * sizeof(long long));
   SI_ALLOC(g->status, sizeof(int));
   SI_ALLOC(g->longq, (cap1 + 1) * sizeof(int));
+  SI_ALLOC(g->hugeq, (cap1 + 1) * sizeof(int));
+  SI_ALLOC(g->heavy, (cap1 / kHeavyMinBuild + 2) * sizeof(int));
+  SI_ALLOC(g->over, (cap1 / kHeavyMinBuild + 2) * sizeof(int));
+  SI_ALLOC(g->counters, kCounterInts * sizeof(int));
   g->partial_len = (cap1 + 127) / 128 + 1;
   SI_ALLOC(g->partial, g->partial_len * sizeof(double));
 #undef SI_ALLOC
@@ -486,7 +503,10 @@ extern "C" si_status si_grid_create(const si_grid_desc *desc, int64_t n_capacity
     grid_free(g);
     return s;
   }
+  g->tab_end_host = ht.tab_end;
   e = cudaMemset(g->status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g->heavy, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g->over, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(g->cell_start, 0, (g->n_cells + 1) * sizeof(int));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -512,11 +532,13 @@ extern "C" si_status si_grid_build(si_grid *g, const float *d_pos, int64_t n, vo
   }
   // cell_start[0] = 0; cell_start[c + 1] = sum of counts of cells 0..c
   SI_CUDA_TRY(cudaMemsetAsync(g->cell_start, 0, sizeof(int), st));
+  SI_CUDA_TRY(cudaMemsetAsync(g->heavy, 0, sizeof(int), st));
   si_status s = scan_inclusive_i32(g->cell_count, g->cell_start + 1, g->n_cells, g->scan_i32, st);
   if (s != SI_OK) return s;
   if (n > 0) {
     SI_KLAUNCH("k_bin_scatter", st, k_bin_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-        (const float4 *)d_pos, (int)n, g->key_slot, g->cell_start, g->spos, g->perm));
+        (const float4 *)d_pos, (int)n, g->key_slot, g->cell_start, g->spos, g->perm, 1u << g->lat.W,
+        g->heavy));
   }
   return SI_OK;
 }

@@ -12,6 +12,9 @@
 
 namespace si {
 
+constexpr int kCounterInts = 8;
+constexpr int kHeavyMinBuild = 8;   // must equal kHeavyMin of the radius kernels
+
 // Record a message for si_last_error() (per host thread) and return `s`.
 si_status fail(si_status s, const std::string &msg);
 si_status cuda_fail(cudaError_t e, const char *what);
@@ -125,6 +128,11 @@ struct si_grid {
   long long *scan_i64 = nullptr; // scan scratch for offsets
   int *status = nullptr;         // device status word
   int *longq = nullptr;          // cap + 1: [0] = count, then query ids of long lists
+  int *hugeq = nullptr;          // cap + 1: lists too long for a warp sort
+  int *heavy = nullptr;          // [0] = count, then cells with >= kHeavyMin points (set by build)
+  int *over = nullptr;           // [0] = count, then heavy cells that did not fit the cell kernel
+  int *counters = nullptr;       // kCounterInts work counters
+  std::vector<int> tab_end_host; // host copy of the table's end[] index
   double *partial = nullptr;     // reduce partial sums
   int64_t partial_len = 0;
   long long *h_pinned = nullptr; // pinned host scratch (2 values)

@@ -1,18 +1,18 @@
 // All-agents fixed-radius query (Sec. I, Sec. II.A): count pass, prefix sum,
-// write pass, per-list id sort.  One thread per query point, queries taken in
-// cell order so that neighbouring threads walk neighbouring cells (their
-// candidate cells are shared through L1/L2).
+// write pass, ids ascending per list.
+//
+// Queries in lightly loaded cells: one thread per query point, queries in cell
+// order so that neighbouring threads walk neighbouring cells (their candidate
+// cells are shared through L1/L2); lists of up to 32 ids are sorted while
+// written, longer ones are queued for a warp (or block) bitonic sort.
+// Queries in cells holding at least kHeavyMin points: one block per cell
+// (si_cell.cu), lists written already sorted.
 #include <cmath>
 
 #include "si_host.h"
-#include "si_walk.cuh"
+#include "si_radius.cuh"
 
 namespace si {
-
-constexpr int kQueryThreads = 128;
-constexpr int kInlineSort = 32;      // lists up to this length are sorted while written
-constexpr int kSortThreads = 512;
-constexpr int kSortSmem = 8192;      // longer lists are sorted in global memory
 
 struct CountVisitor {
   const GridDev &g;
@@ -67,57 +67,82 @@ struct WriteVisitor {
   }
 };
 
-template <bool CUBE>
-__global__ void __launch_bounds__(kQueryThreads) k_radius_count(GridDev g, WalkParams P, Band B,
-                                                                unsigned flags,
-                                                                long long *__restrict__ counts) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= g.n) return;
+// One query by one thread.  heavy_min > 0: queries whose cell holds at least
+// heavy_min points are left to the cell kernel.
+template <bool WRITE, bool CUBE>
+__device__ __forceinline__ void radius_one(const GridDev &g, const WalkParams &P, const Band &B,
+                                           unsigned flags, int s, int heavy_min, long long *counts,
+                                           const long long *offsets, int *ids, long long cap,
+                                           int *longq) {
   const QueryGeom Q = make_geom(g.spos[s], g);
-  CountVisitor v{g, Q, B, (flags & SI_INCLUDE_SELF) ? -1 : s, 0};
-  if (CUBE || Q.outside) walk_cube(g, Q, P.dg, v);
-  else walk_sphere(g, Q, P, v);
-  counts[__ldg(g.perm + s)] = v.count;
-}
-
-template <bool CUBE>
-__global__ void __launch_bounds__(kQueryThreads) k_radius_write(GridDev g, WalkParams P, Band B,
-                                                                unsigned flags,
-                                                                const long long *__restrict__ offsets,
-                                                                int *__restrict__ ids, long long cap,
-                                                                int *__restrict__ longq) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= g.n) return;
+  if (heavy_min > 0 && !Q.outside) {
+    const unsigned key = pack3(Q.c[0], Q.c[1], Q.c[2], g);
+    if (__ldg(g.cell_start + key + 1) - __ldg(g.cell_start + key) >= heavy_min) return;
+  }
+  const int self = (flags & SI_INCLUDE_SELF) ? -1 : s;
   const int orig = __ldg(g.perm + s);
-  const long long base = offsets[orig];
-  const int len = (int)(offsets[orig + 1] - base);
-  if (len == 0) return;
-  if (base + len > cap) {
-    atomicOr(g.status, ST_CAPACITY);
-    return;
-  }
-  const bool sort_all = !(flags & SI_NO_SORT);
-  const QueryGeom Q = make_geom(g.spos[s], g);
-  WriteVisitor v{g, Q, B, (flags & SI_INCLUDE_SELF) ? -1 : s, ids + base, len, 0,
-                 sort_all && len <= kInlineSort};
-  if (CUBE || Q.outside) walk_cube(g, Q, P.dg, v);
-  else walk_sphere(g, Q, P, v);
-  if (v.k != len) atomicOr(g.status, ST_INTERNAL);
-  if (sort_all && len > kInlineSort) {
-    const int slot = atomicAdd(longq, 1);
-    longq[1 + slot] = orig;
+  if (!WRITE) {
+    CountVisitor v{g, Q, B, self, 0};
+    if (CUBE || Q.outside) walk_cube(g, Q, P.dg, v);
+    else walk_sphere(g, Q, P, v);
+    counts[orig] = v.count;
+  } else {
+    const long long base = offsets[orig];
+    const int len = (int)(offsets[orig + 1] - base);
+    if (len == 0) return;
+    if (base + len > cap) {
+      atomicOr(g.status, ST_CAPACITY);
+      return;
+    }
+    const bool sort_all = !(flags & SI_NO_SORT);
+    WriteVisitor v{g, Q, B, self, ids + base, len, 0, sort_all && len <= kInlineSort};
+    if (CUBE || Q.outside) walk_cube(g, Q, P.dg, v);
+    else walk_sphere(g, Q, P, v);
+    if (v.k != len) atomicOr(g.status, ST_INTERNAL);
+    if (sort_all && len > kInlineSort) {
+      const int slot = atomicAdd(longq, 1);
+      longq[1 + slot] = orig;
+    }
   }
 }
 
-// Ascending bitonic sort of a[0..n) by one block, with virtual +inf padding
-// up to the next power of two.  Every compare-exchange puts the smaller value
-// at the lower index (first step of each merge compares mirrored pairs), so a
-// pair whose upper index is past n never moves anything.
-__device__ void block_bitonic(int *a, int n) {
+template <bool WRITE, bool CUBE>
+__global__ void __launch_bounds__(kQueryThreads) k_radius(GridDev g, WalkParams P, Band B, unsigned flags,
+                                                          int heavy_min, long long *counts,
+                                                          const long long *offsets, int *ids,
+                                                          long long cap, int *longq) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.n) return;
+  radius_one<WRITE, CUBE>(g, P, B, flags, s, heavy_min, counts, offsets, ids, cap, longq);
+}
+
+// Queries of the heavy cells that did not fit the cell kernel: per query.
+template <bool WRITE>
+__global__ void __launch_bounds__(kQueryThreads) k_radius_over(GridDev g, WalkParams P, Band B,
+                                                               unsigned flags, const int *over,
+                                                               long long *counts,
+                                                               const long long *offsets, int *ids,
+                                                               long long cap, int *longq) {
+  const int nover = over[0];
+  for (int item = blockIdx.x; item < nover; item += gridDim.x) {
+    const unsigned key = (unsigned)over[1 + item];
+    const int qs = __ldg(g.cell_start + key), qe = __ldg(g.cell_start + key + 1);
+    for (int s = qs + threadIdx.x; s < qe; s += blockDim.x)
+      radius_one<WRITE, false>(g, P, B, flags, s, 0, counts, offsets, ids, cap, longq);
+  }
+}
+
+// Ascending bitonic sort of a[0..n) with +inf padding up to the next power
+// of two, by `lanes` cooperating threads (rank = thread's index among them);
+// sync() separates the stages.  Every compare-exchange puts the smaller value
+// at the lower index (first step of each merge compares mirrored pairs), so
+// a pair whose upper index is past n never moves anything.
+template <class Sync>
+__device__ __forceinline__ void bitonic_padded(int *a, int n, int rank, int lanes, Sync sync) {
   int P = 1;
   while (P < n) P <<= 1;
   for (int k = 2; k <= P; k <<= 1) {
-    for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+    for (int i = rank; i < P / 2; i += lanes) {
       const int lo = (i / (k / 2)) * k + (i % (k / 2));
       const int hi = (lo / k) * k + (k - 1 - (lo % k));
       if (hi < n && a[hi] < a[lo]) {
@@ -126,9 +151,9 @@ __device__ void block_bitonic(int *a, int n) {
         a[hi] = t;
       }
     }
-    __syncthreads();
+    sync();
     for (int h = k / 4; h >= 1; h >>= 1) {
-      for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+      for (int i = rank; i < P / 2; i += lanes) {
         const int lo = (i / h) * 2 * h + (i % h);
         const int hi = lo + h;
         if (hi < n && a[hi] < a[lo]) {
@@ -137,27 +162,64 @@ __device__ void block_bitonic(int *a, int n) {
           a[hi] = t;
         }
       }
-      __syncthreads();
+      sync();
     }
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_long(const long long *__restrict__ offsets,
-                                                           int *ids, const int *__restrict__ longq) {
-  __shared__ int buf[kSortSmem];
+struct WarpSync {
+  __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+struct BlockSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// One warp per queued list (up to kSortWarpCap ids, in shared memory); longer
+// lists are passed on to the block sort.
+__global__ void __launch_bounds__(kSortWarps * 32) k_sort_warp(const long long *__restrict__ offsets,
+                                                              int *ids, const int *__restrict__ longq,
+                                                              int *hugeq) {
+  extern __shared__ int sbuf[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int *buf = sbuf + w * kSortWarpCap;
   const int nq = longq[0];
-  for (int item = blockIdx.x; item < nq; item += gridDim.x) {
+  const int gw = blockIdx.x * kSortWarps + w, nwarps = gridDim.x * kSortWarps;
+  for (int item = gw; item < nq; item += nwarps) {
     const int q = longq[1 + item];
     const long long base = offsets[q];
     const int len = (int)(offsets[q + 1] - base);
     int *list = ids + base;
-    if (len <= kSortSmem) {
-      for (int i = threadIdx.x; i < len; i += blockDim.x) buf[i] = list[i];
+    if (len > kSortWarpCap) {
+      if (lane == 0) {
+        const int slot = atomicAdd(hugeq, 1);
+        hugeq[1 + slot] = q;
+      }
+      continue;
+    }
+    for (int i = lane; i < len; i += 32) buf[i] = list[i];
+    __syncwarp();
+    bitonic_padded(buf, len, lane, 32, WarpSync());
+    for (int i = lane; i < len; i += 32) list[i] = buf[i];
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(512) k_sort_block(const long long *__restrict__ offsets, int *ids,
+                                                   const int *__restrict__ hugeq) {
+  extern __shared__ int sbuf[];
+  const int nq = hugeq[0];
+  for (int item = blockIdx.x; item < nq; item += gridDim.x) {
+    const int q = hugeq[1 + item];
+    const long long base = offsets[q];
+    const int len = (int)(offsets[q + 1] - base);
+    int *list = ids + base;
+    if (len <= kSortBlockCap) {
+      for (int i = threadIdx.x; i < len; i += blockDim.x) sbuf[i] = list[i];
       __syncthreads();
-      block_bitonic(buf, len);
-      for (int i = threadIdx.x; i < len; i += blockDim.x) list[i] = buf[i];
+      bitonic_padded(sbuf, len, threadIdx.x, blockDim.x, BlockSync());
+      for (int i = threadIdx.x; i < len; i += blockDim.x) list[i] = sbuf[i];
     } else {
-      block_bitonic(list, len);
+      bitonic_padded(list, len, threadIdx.x, blockDim.x, BlockSync());
     }
     __syncthreads();
   }
@@ -188,6 +250,21 @@ static WalkParams walk_params(const Lattice &lat, float r, bool inclusion) {
   return P;
 }
 
+template <bool WRITE>
+static si_status launch_light(bool cube, const GridDev &dv, const WalkParams &P, const Band &B,
+                              unsigned flags, int heavy_min, long long *counts, const long long *off,
+                              int *ids, long long cap, int *longq, unsigned blocks, cudaStream_t st) {
+  if (cube)
+    SI_KLAUNCH(WRITE ? "k_radius_write_cube" : "k_radius_count_cube", st,
+               k_radius<WRITE, true><<<blocks, kQueryThreads, 0, st>>>(dv, P, B, flags, 0, counts, off,
+                                                                       ids, cap, longq));
+  else
+    SI_KLAUNCH(WRITE ? "k_radius_write" : "k_radius_count", st,
+               k_radius<WRITE, false><<<blocks, kQueryThreads, 0, st>>>(dv, P, B, flags, heavy_min,
+                                                                        counts, off, ids, cap, longq));
+  return SI_OK;
+}
+
 extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t m, float r,
                                      uint32_t flags, int64_t *d_offsets, int32_t *d_ids,
                                      int64_t ids_capacity, int64_t *h_total, void *stream) {
@@ -207,18 +284,31 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   const WalkParams P = walk_params(g->lat, r, load >= 4.0);
   const Band B = make_band(g->lat, r);
   const GridDev dv = g->dev();
+  // the cell path holds the whole cell-level sphere (entries with b^2 <= n)
+  const int n_tab = std::min((int)std::floor((double)P.dg * (double)P.dg), g->tables.n_max);
+  const bool heavy = !cube && n_tab >= 0 && g->tab_end_host[n_tab] <= kCellTCap;
+  const int heavy_min = heavy ? kHeavyMin : 0;
   long long *off = (long long *)d_offsets;
   SI_CUDA_TRY(cudaMemsetAsync(off, 0, sizeof(long long), st));
+  SI_CUDA_TRY(cudaMemsetAsync(g->counters, 0, kCounterInts * sizeof(int), st));
+  SI_CUDA_TRY(cudaMemsetAsync(g->over, 0, sizeof(int), st));
   const unsigned blocks = (unsigned)((m + kQueryThreads - 1) / kQueryThreads);
+  int *work_c = g->counters, *work_w = g->counters + 1;
+  si_status s;
   if (m > 0) {
-    if (cube)
-      SI_KLAUNCH("k_radius_count_cube", st,
-                 k_radius_count<true><<<blocks, kQueryThreads, 0, st>>>(dv, P, B, flags, off + 1));
-    else
-      SI_KLAUNCH("k_radius_count", st,
-                 k_radius_count<false><<<blocks, kQueryThreads, 0, st>>>(dv, P, B, flags, off + 1));
-    si_status s = scan_inclusive_i64(off + 1, off + 1, m, g->scan_i64, st);
-    if (s != SI_OK) return s;
+    if ((s = launch_light<false>(cube, dv, P, B, flags, heavy_min, off + 1, nullptr, nullptr, 0,
+                                 nullptr, blocks, st)) != SI_OK)
+      return s;
+    if (heavy) {
+      if ((s = launch_cell_pass(false, dv, P, B, flags, g->heavy, work_c, g->over, off + 1, nullptr,
+                                nullptr, 0, st)) != SI_OK)
+        return s;
+      SI_KLAUNCH("k_radius_over_count", st,
+                 k_radius_over<false><<<148 * 4, kQueryThreads, 0, st>>>(dv, P, B, flags, g->over,
+                                                                         off + 1, nullptr, nullptr, 0,
+                                                                         nullptr));
+    }
+    if ((s = scan_inclusive_i64(off + 1, off + 1, m, g->scan_i64, st)) != SI_OK) return s;
   }
   if (h_total) {
     SI_CUDA_TRY(cudaMemcpyAsync(g->h_pinned, off + m, sizeof(long long), cudaMemcpyDeviceToHost, st));
@@ -228,16 +318,27 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   }
   if (m == 0) return SI_OK;
   SI_CUDA_TRY(cudaMemsetAsync(g->longq, 0, sizeof(int), st));
-  if (cube)
-    SI_KLAUNCH("k_radius_write_cube", st,
-               k_radius_write<true><<<blocks, kQueryThreads, 0, st>>>(dv, P, B, flags, off, d_ids,
-                                                                      ids_capacity, g->longq));
-  else
-    SI_KLAUNCH("k_radius_write", st,
-               k_radius_write<false><<<blocks, kQueryThreads, 0, st>>>(dv, P, B, flags, off, d_ids,
-                                                                       ids_capacity, g->longq));
+  SI_CUDA_TRY(cudaMemsetAsync(g->hugeq, 0, sizeof(int), st));
+  if ((s = launch_light<true>(cube, dv, P, B, flags, heavy_min, nullptr, off, d_ids, ids_capacity,
+                              g->longq, blocks, st)) != SI_OK)
+    return s;
+  if (heavy) {
+    if ((s = launch_cell_pass(true, dv, P, B, flags, g->heavy, work_w, g->over, nullptr, off, d_ids,
+                              ids_capacity, st)) != SI_OK)
+      return s;
+    SI_KLAUNCH("k_radius_over_write", st,
+               k_radius_over<true><<<148 * 4, kQueryThreads, 0, st>>>(dv, P, B, flags, g->over, nullptr,
+                                                                      off, d_ids, ids_capacity,
+                                                                      g->longq));
+  }
   if (!(flags & SI_NO_SORT)) {
-    SI_KLAUNCH("k_sort_long", st, k_sort_long<<<2 * 148, kSortThreads, 0, st>>>(off, d_ids, g->longq));
+    const size_t wsm = (size_t)kSortWarps * kSortWarpCap * sizeof(int);
+    SI_CUDA_TRY(cudaFuncSetAttribute(k_sort_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
+    SI_KLAUNCH("k_sort_warp", st,
+               k_sort_warp<<<148 * 2, kSortWarps * 32, wsm, st>>>(off, d_ids, g->longq, g->hugeq));
+    const size_t bsm = (size_t)kSortBlockCap * sizeof(int);
+    SI_CUDA_TRY(cudaFuncSetAttribute(k_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+    SI_KLAUNCH("k_sort_block", st, k_sort_block<<<148, 512, bsm, st>>>(off, d_ids, g->hugeq));
   }
   return SI_OK;
 }

@@ -1,0 +1,27 @@
+// Shared constants and launchers of the radius-query kernels.
+#pragma once
+
+#include "si_host.h"
+#include "si_internal.cuh"
+#include "si_walk.cuh"
+
+namespace si {
+
+constexpr int kQueryThreads = 128;   // per-query kernels
+constexpr int kInlineSort = 32;      // lists up to this length are sorted while written
+constexpr int kHeavyMin = kHeavyMinBuild;   // cells with this many points take the cell path
+constexpr int kCellThreads = 256;
+constexpr int kCellCap = 3072;       // staged candidates per query cell
+constexpr int kCellKeyCap = 4096;    // power of two >= kCellCap (sort keys)
+constexpr int kCellMaxQ = 512;       // queries of one cell in one block
+constexpr int kCellTCap = 512;       // target cells of the cell-level sphere
+constexpr int kSortWarps = 8;
+constexpr int kSortWarpCap = 2048;   // lists a warp sorts in shared memory
+constexpr int kSortBlockCap = 16384; // lists a block sorts in shared memory
+
+size_t cell_smem_bytes();
+si_status launch_cell_pass(bool write, const GridDev &g, const WalkParams &P, const Band &B,
+                           unsigned flags, const int *heavy, int *work, int *over, long long *counts,
+                           const long long *offsets, int *ids, long long cap, cudaStream_t st);
+
+}  // namespace si
