@@ -152,6 +152,30 @@ si_status si_query_knn(si_grid *g, const float *d_centers, int64_t m, int k,
 si_status si_neighbor_reduce(si_grid *g, float r, int kernel, double *d_energy,
                              float *d_grad, const float *d_grad_scale, void *stream);
 
+/* Smooth-kernel energy E (as si_neighbor_reduce, kernel SI_KERNEL_POLY6_CUBED)
+ * of n points, for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this entry point exists because some callers cannot call
+ * cudaMalloc where they need the energy -- code running under a framework
+ * that owns every device allocation, plug-ins with a fixed device-memory
+ * budget, a real-time step that must never touch the allocator -- and cannot
+ * create a grid.  It allocates nothing: its scratch (about 2.5 MB: cell keys,
+ * counts and starts, points in cell order, partial sums, a status word) is one
+ * static device array that every GPU loading the library holds until the
+ * process exits.  Limits: n <= 65536 points and at most 2^16 cells
+ * (sum of log2_cells <= 16); larger inputs return SI_ERR_INVALID.
+ * desc: lattice as for si_grid_create (r_max ignored; r validated the same
+ * way).  d_pos: n * 4 floats, device, 16-byte aligned.  d_energy: one double,
+ * device; NaN when a point lies outside a cyclic axis' box or is not finite.
+ * Neighbors come from the bin-lattice walk (no tables needed), so the result
+ * equals si_neighbor_reduce's up to FP32 summation order.
+ * The first call on a device looks up the scratch array's device address
+ * (with that device current); make that first call before any stream
+ * capture.  Every call shares the scratch and leaves its contents there; the
+ * call clears what must start at zero, and calls whose work overlaps on the
+ * GPU (other streams, other host threads) race on it. */
+si_status si_neighbor_energy_noalloc(const si_grid_desc *desc, const float *d_pos, int64_t n,
+                                     float r, double *d_energy, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Batched scenes: many independent grids served together.
  * Each scene has its own lattice, cyclic mask, radius and points; all scenes
