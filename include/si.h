@@ -51,6 +51,9 @@ typedef enum {
 #define SI_METHOD_CUBE     1u  /* bin-lattice cube scan (Sec. I, Sec. IV.A)     */
 #define SI_INCLUDE_SELF    2u  /* all-agents mode: keep the querying point      */
 #define SI_NO_SORT         4u  /* radius lists left in walk order (not by id)   */
+#define SI_WALK_PAPER      8u  /* radius: walk the 64 direction-bit tables of
+                                  Sec. III.A with the run-time test (Eq. 1)
+                                  instead of the sub-cell class tables         */
 
 /* Region, lattice and table extent (Sec. II.B).  The box side on axis a is
  * L_a = cell_size * 2^log2_cells[a] (exact in float32).  A cyclic axis wraps

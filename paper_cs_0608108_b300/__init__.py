@@ -120,10 +120,14 @@ class Grid:
 
     # -- queries -------------------------------------------------------------
     def query_radius(self, r: float, include_self: bool = False, method: str = "sphere",
-                     sort: bool = True, out_offsets=None, out_ids=None, sync_total: bool = True):
-        """All-agents radius query.  Returns (offsets int64[n+1], ids int32[total])."""
+                     sort: bool = True, out_offsets=None, out_ids=None, sync_total: bool = True,
+                     walk: str = "classes"):
+        """All-agents radius query.  Returns (offsets int64[n+1], ids int32[total]).
+        method "sphere" (spherical index) or "cube" (bin-lattice scan); walk
+        "classes" (sub-cell class tables) or "paper" (Sec. III.A 64 tables)."""
         flags = (N.SI_INCLUDE_SELF if include_self else 0) | \
-                (N.SI_METHOD_CUBE if method == "cube" else 0) | (0 if sort else N.SI_NO_SORT)
+                (N.SI_METHOD_CUBE if method == "cube" else 0) | (0 if sort else N.SI_NO_SORT) | \
+                (N.SI_WALK_PAPER if walk == "paper" else 0)
         dev = self._pos.device
         off = out_offsets if out_offsets is not None else torch.empty(self.n + 1, dtype=torch.int64, device=dev)
         ids = out_ids

@@ -311,6 +311,9 @@ void fill_griddev(const Lattice &lat, const DevTables &t, GridDev &g) {
   g.spec_end = t.spec_end;
   g.spec_shells = t.spec_shells;
   g.eps = (float)lat.eps;
+  g.cls = nullptr;
+  g.cls_begin = nullptr;
+  g.cls_q = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -423,6 +426,9 @@ si::GridDev si_grid::dev() const {
   g.cell_start = cell_start;
   g.n = (int)n;
   g.status = status;
+  g.cls = cls;
+  g.cls_begin = cls_begin;
+  g.cls_q = cls_q;
   return g;
 }
 
@@ -442,6 +448,8 @@ static void grid_free(si_grid *g) {
   cudaFree(g->over);
   cudaFree(g->counters);
   cudaFree(g->partial);
+  cudaFree(g->cls);
+  cudaFree(g->cls_begin);
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
   free_tables(g->tables);
   delete g;
@@ -504,6 +512,16 @@ extern "C" si_status si_grid_create(const si_grid_desc *desc, int64_t n_capacity
     return s;
   }
   g->tab_end_host = ht.tab_end;
+  g->cls_cap = class_capacity(g->lat, (int64_t)ht.tab.size());
+  if (g->cls_cap > 0) {
+    const int q = class_q_for(std::sqrt((double)g->lat.n_max + 1.0));
+    e = cudaMalloc((void **)&g->cls, g->cls_cap * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&g->cls_begin, ((size_t)q * q * q + 1) * sizeof(int));
+    if (e != cudaSuccess) {
+      grid_free(g);
+      return cuda_fail(e, "cudaMalloc (class tables)");
+    }
+  }
   e = cudaMemset(g->status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(g->heavy, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(g->over, 0, sizeof(int));

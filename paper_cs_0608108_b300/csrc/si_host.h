@@ -13,6 +13,8 @@
 namespace si {
 
 constexpr int kCounterInts = 8;
+constexpr long long kClassCapMax = 1ll << 22;   // class-table entries a grid may hold
+constexpr size_t kClassSmemMax = 48 * 1024;      // class tables staged in shared memory up to this
 constexpr int kHeavyMinBuild = 8;   // must equal kHeavyMin of the radius kernels
 
 // Record a message for si_last_error() (per host thread) and return `s`.
@@ -110,6 +112,12 @@ struct PairBand {
 };
 PairBand make_pair_band(const Lattice &lat);
 
+// Sub-cell class tables (si_class.cu).
+int class_q_for(double dmax);
+int64_t class_capacity(const Lattice &lat, int64_t table_entries);
+void build_class_tables(const Lattice &lat, double dg, int q, std::vector<unsigned long long> &ent,
+                        std::vector<int> &begin);
+
 }  // namespace si
 
 struct si_grid {
@@ -133,6 +141,16 @@ struct si_grid {
   int *over = nullptr;           // [0] = count, then heavy cells that did not fit the cell kernel
   int *counters = nullptr;       // kCounterInts work counters
   std::vector<int> tab_end_host; // host copy of the table's end[] index
+  // sub-cell class tables for the current radius (see si_class.cu)
+  unsigned long long *cls = nullptr;
+  int *cls_begin = nullptr;
+  int64_t cls_cap = 0;
+  float cls_dg = -1.f;
+  int cls_q = 0;
+  size_t cls_smem_bytes = 0;     // > 0: the current tables fit a block's shared memory
+  std::vector<unsigned long long> cls_host;
+  std::vector<int> cls_begin_host;
+  bool ensure_classes(float dg, cudaStream_t st);
   double *partial = nullptr;     // reduce partial sums
   int64_t partial_len = 0;
   long long *h_pinned = nullptr; // pinned host scratch (2 values)

@@ -51,6 +51,12 @@ struct GridDev {
   int spec_shells;           // shells 0 .. spec_shells-1 have specialized tables
   float eps;                 // conservative margin in cell units
   int *status;               // device status word (bit flags below)
+  // sub-cell class tables (refinement of the specialized tables): class
+  // c = (k q + j) q + i of the query's sub-cell position lists, center to
+  // edge, every offset whose cell lies within d of the class's sub-box
+  const unsigned long long *cls;   // entries: unpacked offset | bit 63 = whole cell inside
+  const int *cls_begin;            // q^3 + 1
+  int cls_q;                       // 0: no class tables
 };
 
 enum : int { ST_INVALID = 1, ST_CAPACITY = 2, ST_INTERNAL = 4, ST_TIMEOUT = 8 };
@@ -205,6 +211,21 @@ __device__ __forceinline__ Target translate(const TabEntry &e, const QueryGeom &
   t.qx = Q.q.x - (wx ? (e.ox > 0 ? g.Lx : -g.Lx) : 0.f);
   t.qy = Q.q.y - (wy ? (e.oy > 0 ? g.Ly : -g.Ly) : 0.f);
   t.qz = Q.q.z - (wz ? (e.oz > 0 ? g.Lz : -g.Lz) : 0.f);
+  return t;
+}
+
+// Translation of a class-table entry: the same SWAR add as translate(); the
+// sign of a wrapped coordinate's offset is the top bit of its (w+1)-bit field.
+__device__ __forceinline__ Target translate_raw(unsigned long long e, const QueryGeom &Q, const GridDev &g) {
+  Target t;
+  const unsigned long long s = Q.cu + e;
+  t.outside = (s & g.guard_non) != 0ull;
+  t.key = t.outside ? g.outside : repack(s & g.valid, g);
+  const bool wx = (s & g.gx) != 0ull, wy = (s & g.gy) != 0ull, wz = (s & g.gz) != 0ull;
+  t.wrapped = !t.outside && (wx | wy | wz);
+  t.qx = Q.q.x - (wx ? ((e & g.gx) ? -g.Lx : g.Lx) : 0.f);
+  t.qy = Q.q.y - (wy ? ((e & g.gy) ? -g.Ly : g.Ly) : 0.f);
+  t.qz = Q.q.z - (wz ? ((e & g.gz) ? -g.Lz : g.Lz) : 0.f);
   return t;
 }
 

@@ -7,6 +7,7 @@
 // written, longer ones are queued for a warp (or block) bitonic sort.
 // Queries in cells holding at least kHeavyMin points: one block per cell
 // (si_cell.cu), lists written already sorted.
+#include <algorithm>
 #include <cmath>
 
 #include "si_host.h"
@@ -67,9 +68,19 @@ struct WriteVisitor {
   }
 };
 
+// Cell walks of the per-query kernels.
+enum Walk : int { kWalkPaper = 0, kWalkClasses = 1, kWalkCube = 2 };
+
+template <int WALK, class V>
+__device__ __forceinline__ void walk_one(const GridDev &g, const QueryGeom &Q, const WalkParams &P, V &v) {
+  if (WALK == kWalkCube || Q.outside) walk_cube(g, Q, P.dg, v);
+  else if (WALK == kWalkClasses) walk_classes_in(g, Q, g.cls, g.cls_begin, g.cls_q, v);
+  else walk_sphere(g, Q, P, v);
+}
+
 // One query by one thread.  heavy_min > 0: queries whose cell holds at least
 // heavy_min points are left to the cell kernel.
-template <bool WRITE, bool CUBE>
+template <bool WRITE, int WALK>
 __device__ __forceinline__ void radius_one(const GridDev &g, const WalkParams &P, const Band &B,
                                            unsigned flags, int s, int heavy_min, long long *counts,
                                            const long long *offsets, int *ids, long long cap,
@@ -83,8 +94,7 @@ __device__ __forceinline__ void radius_one(const GridDev &g, const WalkParams &P
   const int orig = __ldg(g.perm + s);
   if (!WRITE) {
     CountVisitor v{g, Q, B, self, 0};
-    if (CUBE || Q.outside) walk_cube(g, Q, P.dg, v);
-    else walk_sphere(g, Q, P, v);
+    walk_one<WALK>(g, Q, P, v);
     counts[orig] = v.count;
   } else {
     const long long base = offsets[orig];
@@ -96,8 +106,7 @@ __device__ __forceinline__ void radius_one(const GridDev &g, const WalkParams &P
     }
     const bool sort_all = !(flags & SI_NO_SORT);
     WriteVisitor v{g, Q, B, self, ids + base, len, 0, sort_all && len <= kInlineSort};
-    if (CUBE || Q.outside) walk_cube(g, Q, P.dg, v);
-    else walk_sphere(g, Q, P, v);
+    walk_one<WALK>(g, Q, P, v);
     if (v.k != len) atomicOr(g.status, ST_INTERNAL);
     if (sort_all && len > kInlineSort) {
       const int slot = atomicAdd(longq, 1);
@@ -106,14 +115,37 @@ __device__ __forceinline__ void radius_one(const GridDev &g, const WalkParams &P
   }
 }
 
-template <bool WRITE, bool CUBE>
+template <bool WRITE, int WALK>
 __global__ void __launch_bounds__(kQueryThreads) k_radius(GridDev g, WalkParams P, Band B, unsigned flags,
                                                           int heavy_min, long long *counts,
                                                           const long long *offsets, int *ids,
                                                           long long cap, int *longq) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.n) return;
-  radius_one<WRITE, CUBE>(g, P, B, flags, s, heavy_min, counts, offsets, ids, cap, longq);
+  radius_one<WRITE, WALK>(g, P, B, flags, s, heavy_min, counts, offsets, ids, cap, longq);
+}
+
+// Per-query kernel with the class tables staged in shared memory: a
+// persistent grid, each block copies the tables once and then walks queries
+// in cell order (grid-stride), so the divergent per-lane table reads hit
+// shared memory instead of L2.
+template <bool WRITE>
+__global__ void __launch_bounds__(kClassThreads) k_radius_cls(GridDev g, WalkParams P, Band B,
+                                                              unsigned flags, int heavy_min,
+                                                              int n_entries, long long *counts,
+                                                              const long long *offsets, int *ids,
+                                                              long long cap, int *longq) {
+  extern __shared__ __align__(16) unsigned long long cls_smem[];
+  const int nbeg = g.cls_q * g.cls_q * g.cls_q + 1;
+  int *beg_smem = reinterpret_cast<int *>(cls_smem + n_entries);
+  for (int i = threadIdx.x; i < n_entries; i += blockDim.x) cls_smem[i] = __ldg(g.cls + i);
+  for (int i = threadIdx.x; i < nbeg; i += blockDim.x) beg_smem[i] = __ldg(g.cls_begin + i);
+  __syncthreads();
+  GridDev gs = g;
+  gs.cls = cls_smem;
+  gs.cls_begin = beg_smem;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.n; s += gridDim.x * blockDim.x)
+    radius_one<WRITE, kWalkClasses>(gs, P, B, flags, s, heavy_min, counts, offsets, ids, cap, longq);
 }
 
 // Queries of the heavy cells that did not fit the cell kernel: per query.
@@ -128,7 +160,7 @@ __global__ void __launch_bounds__(kQueryThreads) k_radius_over(GridDev g, WalkPa
     const unsigned key = (unsigned)over[1 + item];
     const int qs = __ldg(g.cell_start + key), qe = __ldg(g.cell_start + key + 1);
     for (int s = qs + threadIdx.x; s < qe; s += blockDim.x)
-      radius_one<WRITE, false>(g, P, B, flags, s, 0, counts, offsets, ids, cap, longq);
+      radius_one<WRITE, kWalkPaper>(g, P, B, flags, s, 0, counts, offsets, ids, cap, longq);
   }
 }
 
@@ -251,17 +283,34 @@ static WalkParams walk_params(const Lattice &lat, float r, bool inclusion) {
 }
 
 template <bool WRITE>
-static si_status launch_light(bool cube, const GridDev &dv, const WalkParams &P, const Band &B,
-                              unsigned flags, int heavy_min, long long *counts, const long long *off,
-                              int *ids, long long cap, int *longq, unsigned blocks, cudaStream_t st) {
-  if (cube)
+static si_status launch_light(int walk, const si_grid *gr, const GridDev &dv, const WalkParams &P,
+                              const Band &B, unsigned flags, int heavy_min, long long *counts,
+                              const long long *off, int *ids, long long cap, int *longq,
+                              unsigned blocks, cudaStream_t st) {
+  if (walk == kWalkCube) {
     SI_KLAUNCH(WRITE ? "k_radius_write_cube" : "k_radius_count_cube", st,
-               k_radius<WRITE, true><<<blocks, kQueryThreads, 0, st>>>(dv, P, B, flags, 0, counts, off,
-                                                                       ids, cap, longq));
-  else
+               k_radius<WRITE, kWalkCube><<<blocks, kQueryThreads, 0, st>>>(dv, P, B, flags, 0, counts,
+                                                                            off, ids, cap, longq));
+  } else if (walk == kWalkClasses && gr->cls_smem_bytes > 0) {
+    const size_t smem = gr->cls_smem_bytes;
+    SI_CUDA_TRY(cudaFuncSetAttribute(k_radius_cls<WRITE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    int per_sm = 0;
+    SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radius_cls<WRITE>,
+                                                              kClassThreads, smem));
+    const unsigned grid = (unsigned)std::max(1, std::min<int>(per_sm, 8) * 148);
     SI_KLAUNCH(WRITE ? "k_radius_write" : "k_radius_count", st,
-               k_radius<WRITE, false><<<blocks, kQueryThreads, 0, st>>>(dv, P, B, flags, heavy_min,
-                                                                        counts, off, ids, cap, longq));
+               k_radius_cls<WRITE><<<grid, kClassThreads, smem, st>>>(
+                   dv, P, B, flags, heavy_min, (int)gr->cls_host.size(), counts, off, ids, cap, longq));
+  } else if (walk == kWalkClasses) {
+    SI_KLAUNCH(WRITE ? "k_radius_write_cls_l2" : "k_radius_count_cls_l2", st,
+               k_radius<WRITE, kWalkClasses><<<blocks, kQueryThreads, 0, st>>>(
+                   dv, P, B, flags, heavy_min, counts, off, ids, cap, longq));
+  } else {
+    SI_KLAUNCH(WRITE ? "k_radius_write_eq2" : "k_radius_count_eq2", st,
+               k_radius<WRITE, kWalkPaper><<<blocks, kQueryThreads, 0, st>>>(
+                   dv, P, B, flags, heavy_min, counts, off, ids, cap, longq));
+  }
   return SI_OK;
 }
 
@@ -276,13 +325,16 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
     return fail(SI_ERR_INVALID, "radius exceeds the grid's r_max");
   if (!d_offsets) return fail(SI_ERR_INVALID, "null offsets");
   if (ids_capacity < 0 || (ids_capacity > 0 && !d_ids)) return fail(SI_ERR_INVALID, "bad ids buffer");
-  if (flags & ~(SI_METHOD_CUBE | SI_INCLUDE_SELF | SI_NO_SORT))
+  if (flags & ~(SI_METHOD_CUBE | SI_INCLUDE_SELF | SI_NO_SORT | SI_WALK_PAPER))
     return fail(SI_ERR_INVALID, "unknown flags");
   cudaStream_t st = (cudaStream_t)stream;
   const bool cube = flags & SI_METHOD_CUBE;
   const double load = g->n_cells > 1 ? (double)g->n / (double)(g->n_cells - 1) : 0.0;
   const WalkParams P = walk_params(g->lat, r, load >= 4.0);
   const Band B = make_band(g->lat, r);
+  const int walk = cube ? kWalkCube
+                        : ((!(flags & SI_WALK_PAPER) && g->ensure_classes(P.dg, st)) ? kWalkClasses
+                                                                                    : kWalkPaper);
   const GridDev dv = g->dev();
   // the cell path holds the whole cell-level sphere (entries with b^2 <= n)
   const int n_tab = std::min((int)std::floor((double)P.dg * (double)P.dg), g->tables.n_max);
@@ -296,7 +348,7 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   int *work_c = g->counters, *work_w = g->counters + 1;
   si_status s;
   if (m > 0) {
-    if ((s = launch_light<false>(cube, dv, P, B, flags, heavy_min, off + 1, nullptr, nullptr, 0,
+    if ((s = launch_light<false>(walk, g, dv, P, B, flags, heavy_min, off + 1, nullptr, nullptr, 0,
                                  nullptr, blocks, st)) != SI_OK)
       return s;
     if (heavy) {
@@ -319,7 +371,7 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   if (m == 0) return SI_OK;
   SI_CUDA_TRY(cudaMemsetAsync(g->longq, 0, sizeof(int), st));
   SI_CUDA_TRY(cudaMemsetAsync(g->hugeq, 0, sizeof(int), st));
-  if ((s = launch_light<true>(cube, dv, P, B, flags, heavy_min, nullptr, off, d_ids, ids_capacity,
+  if ((s = launch_light<true>(walk, g, dv, P, B, flags, heavy_min, nullptr, off, d_ids, ids_capacity,
                               g->longq, blocks, st)) != SI_OK)
     return s;
   if (heavy) {

@@ -8,13 +8,15 @@
 namespace si {
 
 constexpr int kQueryThreads = 128;   // per-query kernels
+constexpr int kClassThreads = 256;   // per-query kernel with shared-memory class tables
 constexpr int kInlineSort = 32;      // lists up to this length are sorted while written
 constexpr int kHeavyMin = kHeavyMinBuild;   // cells with this many points take the cell path
-constexpr int kCellThreads = 256;
+constexpr int kCellThreads = 512;
 constexpr int kCellCap = 3072;       // staged candidates per query cell
 constexpr int kCellKeyCap = 4096;    // power of two >= kCellCap (sort keys)
 constexpr int kCellMaxQ = 512;       // queries of one cell in one block
 constexpr int kCellTCap = 512;       // target cells of the cell-level sphere
+constexpr int kCellMaskCap = 4096;   // (query, 32-candidate) ballots kept per query batch
 constexpr int kSortWarps = 8;
 constexpr int kSortWarpCap = 2048;   // lists a warp sorts in shared memory
 constexpr int kSortBlockCap = 16384; // lists a block sorts in shared memory

@@ -6,6 +6,7 @@
 //   dE/dx_i = -(12 / r^2) sum_{j != i, D_ij < r} (1 - D_ij^2 / r^2)^2 (x_i - x_j)
 // (every unordered pair appears twice in E, hence 2 * 3 * 2 = 12).  One walk
 // computes both; no neighbor list is materialised.
+#include <algorithm>
 #include <cmath>
 
 #include "si_host.h"
@@ -56,24 +57,36 @@ struct ReduceVisitor {
   }
 };
 
-template <bool GRAD>
+// One query per thread.  CLASSES: the sub-cell class tables are staged in
+// shared memory once per block and the grid is persistent (grid-stride over
+// the queries); otherwise the walk of Sec. III.A reads the global tables.
+template <bool GRAD, bool CLASSES>
 __global__ void __launch_bounds__(kReduceThreads) k_reduce(GridDev g, WalkParams P, float r2,
-                                                           float inv_r2,
+                                                           float inv_r2, int n_entries,
                                                            const float *__restrict__ scale,
                                                            float4 *__restrict__ grad,
                                                            double *__restrict__ partial) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ __align__(16) unsigned long long cls_smem[];
+  if (CLASSES) {
+    const int nbeg = g.cls_q * g.cls_q * g.cls_q + 1;
+    int *beg_smem = reinterpret_cast<int *>(cls_smem + n_entries);
+    for (int i = threadIdx.x; i < n_entries; i += blockDim.x) cls_smem[i] = __ldg(g.cls + i);
+    for (int i = threadIdx.x; i < nbeg; i += blockDim.x) beg_smem[i] = __ldg(g.cls_begin + i);
+    __syncthreads();
+    g.cls = cls_smem;
+    g.cls_begin = beg_smem;
+  }
   double e = 0.0;
-  if (s < g.n) {
+  const float c = -12.f * inv_r2 * ((GRAD && scale) ? __ldg(scale) : 1.f);
+  const int stride = CLASSES ? gridDim.x * blockDim.x : g.n;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.n; s += stride) {
     const QueryGeom Q = make_geom(g.spos[s], g);
     ReduceVisitor v{g, Q, r2, inv_r2, s, GRAD, 0.f, 0.f, 0.f, 0.f};
     if (Q.outside) walk_cube(g, Q, P.dg, v);
+    else if (CLASSES) walk_classes_in(g, Q, g.cls, g.cls_begin, g.cls_q, v);
     else walk_sphere(g, Q, P, v);
-    e = (double)v.e;
-    if (GRAD) {
-      const float c = -12.f * inv_r2 * (scale ? __ldg(scale) : 1.f);
-      grad[__ldg(g.perm + s)] = make_float4(c * v.gx, c * v.gy, c * v.gz, 0.f);
-    }
+    e += (double)v.e;
+    if (GRAD) grad[__ldg(g.perm + s)] = make_float4(c * v.gx, c * v.gy, c * v.gz, 0.f);
   }
   // block sum of the energy in FP64, one partial per block (deterministic)
 #pragma unroll
@@ -132,14 +145,35 @@ extern "C" si_status si_neighbor_reduce(si_grid *g, float r, int kernel, double 
   P.incl_d2 = 0.f;
   const float r2 = r * r;
   const float inv_r2 = 1.f / r2;
-  const unsigned blocks = (unsigned)((n + kReduceThreads - 1) / kReduceThreads);
+  const bool classes = g->ensure_classes(P.dg, st) && g->cls_smem_bytes > 0;
+  const GridDev dv = g->dev();
+  unsigned blocks = (unsigned)((n + kReduceThreads - 1) / kReduceThreads);
+  const size_t smem = classes ? g->cls_smem_bytes : 0;
+  const int n_entries = classes ? (int)g->cls_host.size() : 0;
+  if (classes) {
+    auto kern = d_grad ? k_reduce<true, true> : k_reduce<false, true>;
+    SI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kReduceThreads, smem));
+    blocks = std::min<unsigned>(blocks, (unsigned)std::max(1, std::min(per_sm, 16)) * 148u);
+  }
   if ((int64_t)blocks > g->partial_len) return fail(SI_ERR_INTERNAL, "partial buffer too small");
-  if (d_grad)
-    k_reduce<true><<<blocks, kReduceThreads, 0, st>>>(g->dev(), P, r2, inv_r2, d_grad_scale,
-                                                      (float4 *)d_grad, g->partial);
+  if (d_grad && classes)
+    SI_KLAUNCH("k_reduce_grad", st,
+               k_reduce<true, true><<<blocks, kReduceThreads, smem, st>>>(
+                   dv, P, r2, inv_r2, n_entries, d_grad_scale, (float4 *)d_grad, g->partial));
+  else if (d_grad)
+    SI_KLAUNCH("k_reduce_grad_eq2", st,
+               k_reduce<true, false><<<blocks, kReduceThreads, 0, st>>>(
+                   dv, P, r2, inv_r2, 0, d_grad_scale, (float4 *)d_grad, g->partial));
+  else if (classes)
+    SI_KLAUNCH("k_reduce", st,
+               k_reduce<false, true><<<blocks, kReduceThreads, smem, st>>>(dv, P, r2, inv_r2, n_entries,
+                                                                          nullptr, nullptr, g->partial));
   else
-    SI_KLAUNCH("k_reduce", st, k_reduce<false><<<blocks, kReduceThreads, 0, st>>>(g->dev(), P, r2, inv_r2, nullptr, nullptr,
-                                                       g->partial));
+    SI_KLAUNCH("k_reduce_eq2", st,
+               k_reduce<false, false><<<blocks, kReduceThreads, 0, st>>>(dv, P, r2, inv_r2, 0, nullptr,
+                                                                        nullptr, g->partial));
   if (d_energy) {
     SI_KLAUNCH("k_reduce_final", st, k_reduce_final<<<1, 1024, 0, st>>>(g->partial, (int)blocks, d_energy));
   }

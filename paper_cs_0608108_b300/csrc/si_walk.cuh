@@ -56,6 +56,37 @@ __device__ __forceinline__ void walk_sphere(const GridDev &g, const QueryGeom &Q
   }
 }
 
+// Sub-cell class walk: the query's sub-cell position selects one of q^3
+// precomputed lists holding exactly the cells within d of that sub-cell box,
+// center to edge; no run-time cell test is needed.  This refines the 64
+// direction-bit tables of Sec. III.A (which select by f < zeta only).
+// cls / begin may point to global or to shared memory (plain loads).
+template <class V>
+__device__ __forceinline__ void walk_classes_in(const GridDev &g, const QueryGeom &Q,
+                                                const unsigned long long *cls, const int *begin, int q,
+                                                V &visit) {
+  const int i = min((int)(Q.phi[0] * (float)q), q - 1);
+  const int j = min((int)(Q.phi[1] * (float)q), q - 1);
+  const int k = min((int)(Q.phi[2] * (float)q), q - 1);
+  const int c = (k * q + j) * q + i;
+  const int b = begin[c], e = begin[c + 1];
+  bool out_seen = false;
+  for (int t = b; t < e; ++t) {
+    const unsigned long long E = cls[t];
+    const Target tg = translate_raw(E & ~(1ull << 63), Q, g);
+    if (tg.outside) {
+      if (out_seen) continue;
+      out_seen = true;
+    }
+    visit(tg, (E >> 63) != 0ull && !tg.outside);
+  }
+}
+
+template <class V>
+__device__ __forceinline__ void walk_classes(const GridDev &g, const QueryGeom &Q, V &visit) {
+  walk_classes_in(g, Q, g.cls, g.cls_begin, g.cls_q, visit);
+}
+
 // Bin-lattice walk (Sec. I; Sec. III.C parallelepiped): every cell of the
 // sphere's bounding cube, clipped to the region on non-cyclic axes (the
 // outside cell visited once if the cube leaves the region), wrapped with an

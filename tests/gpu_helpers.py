@@ -19,10 +19,11 @@ def gpu_grid(scene: synth.Scene, r_max=None, capacity=None) -> Grid:
     return g.build(to_dev(scene.pos))
 
 
-def gpu_radius(scene, r=None, method="sphere", include_self=False, sort=True, grid=None):
+def gpu_radius(scene, r=None, method="sphere", include_self=False, sort=True, grid=None,
+               walk="classes"):
     g = grid or gpu_grid(scene)
     off, ids = g.query_radius(scene.r if r is None else r, include_self=include_self,
-                              method=method, sort=sort)
+                              method=method, sort=sort, walk=walk)
     g.sync()
     return off.cpu().numpy(), ids.cpu().numpy()
 

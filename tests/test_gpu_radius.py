@@ -35,12 +35,15 @@ def test_binning_is_a_cell_ordered_permutation():
     assert set(perm[~inside].tolist()) == set(range(7))
 
 
+WALKS = [("sphere", "classes"), ("sphere", "paper"), ("cube", "classes")]
+
+
 def test_tiny_config_sphere_and_cube_bit_exact():
     # N=20k uniform, 32^3 non-cyclic, r = 0.03 (0.96 cells)
     scene = synth.tiny_scene()
     off_o, ids_o = oracle_radius(scene)
-    for method in ("sphere", "cube"):
-        off_g, ids_g = gpu_radius(scene, method=method)
+    for method, walk in WALKS:
+        off_g, ids_g = gpu_radius(scene, method=method, walk=walk)
         assert_csr_equal(off_g, ids_g, off_o, ids_o)
 
 
@@ -54,8 +57,8 @@ def test_every_cyclic_mask_and_radius(mask, r_cells):
             pos[a * 5:(a + 1) * 5, a] = np.float32(1.07 if a % 2 else -0.03)
     scene = synth.Scene(pos, (0, 0, 0), 1 / 16, (4, 4, 4), mask, r_cells / 16)
     off_o, ids_o = oracle_radius(scene)
-    for method in ("sphere", "cube"):
-        off_g, ids_g = gpu_radius(scene, method=method)
+    for method, walk in WALKS:
+        off_g, ids_g = gpu_radius(scene, method=method, walk=walk)
         assert_csr_equal(off_g, ids_g, off_o, ids_o)
 
 
@@ -66,8 +69,9 @@ def test_non_power_of_two_box_and_offset_origin():
     for mask in (7, 0, 5):
         scene = synth.Scene(base.copy(), (-2.0, 1.0, 3.0), 0.37, (4, 4, 4), mask, 0.37 * 1.7)
         off_o, ids_o = oracle_radius(scene)
-        off_g, ids_g = gpu_radius(scene)
-        assert_csr_equal(off_g, ids_g, off_o, ids_o)
+        for method, walk in WALKS:
+            off_g, ids_g = gpu_radius(scene, method=method, walk=walk)
+            assert_csr_equal(off_g, ids_g, off_o, ids_o)
 
 
 def test_guard_band_pairs_at_the_radius():
@@ -87,8 +91,9 @@ def test_guard_band_pairs_at_the_radius():
     for mask in (7, 0):
         scene = synth.Scene(pos, (0, 0, 0), 1 / 64, (6, 6, 6), mask, float(r))
         off_o, ids_o = oracle_radius(scene)
-        off_g, ids_g = gpu_radius(scene)
-        assert_csr_equal(off_g, ids_g, off_o, ids_o)
+        for method, walk in WALKS:
+            off_g, ids_g = gpu_radius(scene, method=method, walk=walk)
+            assert_csr_equal(off_g, ids_g, off_o, ids_o)
         assert 0 < off_o[-1] < 2 * m
 
 
@@ -108,8 +113,9 @@ def test_wrapped_pairs_near_the_radius():
     pos[:, :3] = np.where(pos[:, :3] >= 1.0, np.float32(0), pos[:, :3])
     scene = synth.Scene(pos, (0, 0, 0), 1 / 128, (7, 7, 7), 7, r)
     off_o, ids_o = oracle_radius(scene)
-    off_g, ids_g = gpu_radius(scene)
-    assert_csr_equal(off_g, ids_g, off_o, ids_o)
+    for method, walk in WALKS:
+        off_g, ids_g = gpu_radius(scene, method=method, walk=walk)
+        assert_csr_equal(off_g, ids_g, off_o, ids_o)
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 31, 33, 257])
@@ -132,8 +138,8 @@ def test_all_points_in_one_cell_and_duplicates():
     pos[100:200] = pos[50]                       # exact duplicates of point 50
     scene = synth.Scene(pos, (0, 0, 0), 1 / 32, (5, 5, 5), 0, 0.03)
     off_o, ids_o = oracle_radius(scene)
-    for method in ("sphere", "cube"):
-        off_g, ids_g = gpu_radius(scene, method=method)
+    for method, walk in WALKS:
+        off_g, ids_g = gpu_radius(scene, method=method, walk=walk)
         assert_csr_equal(off_g, ids_g, off_o, ids_o)
     assert np.diff(off_o).max() == 8999
 
@@ -169,11 +175,11 @@ def test_heavy_mixture_lists_sorted_and_exact():
 def test_full_size_1m_configs_sampled(name):
     scene = synth.uniform_1m_scene() if name == "uniform_1m" else synth.mixture_1m_scene()
     g = gpu_grid(scene)
-    for method in ("sphere", "cube"):
-        off, ids = g.query_radius(scene.r, method=method)
+    for method, walk in WALKS:
+        off, ids = g.query_radius(scene.r, method=method, walk=walk)
         g.sync()
         off_g, ids_g = off.cpu().numpy(), ids.cpu().numpy()
-        if method == "sphere":
+        if (method, walk) == WALKS[0]:
             q = np.random.default_rng(1).choice(scene.n, 1500, replace=False)
             assert_sampled_equal(off_g, ids_g, scene, q)
             ref = (off_g, ids_g)
