@@ -180,8 +180,10 @@ class RadiusWork:
                 "k_bin_scatter": 8 * n + 16 * n + 4 * C + 16 * n + 4 * n,
                 "k_radius_count": (1 - fq) * cnt_b,
                 "k_radius_write": (1 - fq) * wr_b + (1 - ft) * 4 * tot,
-                "k_cell_count": fq * cnt_b,
-                "k_cell_write": fq * wr_b + ft * 4 * tot,
+                # heavy cells: one pass reads their queries' inputs and writes
+                # their lists (to scratch); the copy reads and writes them again
+                "k_cell": fq * cnt_b + ft * 4 * tot,
+                "k_cell_copy": ft * 8 * tot,
                 "k_radius_count_cube": cnt_b,
                 "k_radius_write_cube": wr_b + 4 * tot,
             }

@@ -1,22 +1,26 @@
 // Radius query for heavily loaded cells (Sec. I: with many objects per cell
 // the cost of processing cells dominates, so it pays to share that work).
 //
-// One block per query cell holding at least kHeavyMin points:
+// One block per query cell holding at least kHeavyMin points, in a single
+// pass that runs before the prefix sum of the list lengths:
 //  1. the cell-level sphere: every table entry whose minimum cell-to-cell
 //     bound satisfies b^2 <= floor(d^2) (Sec. II.A) is translated to the query
 //     cell (SWAR add/mask/pack, Sec. II.B); non-empty target cells are listed;
 //  2. their points are moved into the query cell's frame (image shift on
-//     wrapped cyclic axes) and kept when they lie within d of the query cell
-//     box -- the union of the spheres of every point of the cell -- and are
-//     staged in shared memory;
-//  3. write pass only: the staged candidates are sorted by input index;
-//  4. lanes take 32 candidates at a time, warps take the cell's queries: each
-//     (query, 32 candidates) test is one ballot; the count pass adds popc, the
-//     write pass appends the hits at the query's running position, so every
-//     list comes out ascending without a separate sort and with coalesced
-//     stores.
-// A cell whose candidates or queries do not fit is handed to the per-query
-// path (overflow list).
+//     wrapped cyclic axes), kept when they lie within d of the query cell box
+//     (the union of the spheres of every point of the cell) and staged in
+//     shared memory;
+//  3. the staged candidates are put in ascending input-index order: one
+//     counting pass into 1024 buckets by the index's top bits, then an
+//     insertion sort inside each (small) bucket;
+//  4. warps take chunks of 32 candidates (lane = candidate) and test them
+//     against every query of the cell: one ballot per (query, chunk);
+//  5. each query's hits are counted, the cell reserves a region of a scratch
+//     buffer with one atomic, and a warp per query stores its hits there,
+//     ascending.  After the prefix sum, k_cell_copy moves every list to its
+//     place in the output.
+// A cell whose candidates or queries do not fit shared memory, or whose lists
+// do not fit the scratch buffer, hands its queries to the per-query path.
 #include <cmath>
 
 #include "si_host.h"
@@ -25,27 +29,34 @@
 
 namespace si {
 
-template <bool WRITE>
+constexpr int kBuckets = 1024;
+
 struct CellSmem {
-  float4 c[kCellCap];                  // candidate in the query frame; x = NaN: outside cell; w = slot bits
-  // write pass: sort keys (input index << 32 | staging slot); after the
-  // permutation into id order the first kCellCap ints hold the ids
-  unsigned long long key[WRITE ? kCellKeyCap : 1];
+  float4 c[kCellCap];                      // candidate in the query frame; x = NaN: outside cell; w = slot bits
+  unsigned long long key[2 * kCellCap];    // sort buffers: (input index << 32) | staging slot
   union {
-    struct {                           // gather phase: the cell-level sphere's target cells
+    struct {                               // gather: the cell-level sphere's target cells
       unsigned tkey[kCellTCap];
       int tbeg[kCellTCap];
       int tcnt[kCellTCap];
       int tpre[kCellTCap + 1];
       unsigned char tcode[kCellTCap];
     } t;
-    unsigned mask[kCellMaskCap];       // test phase: ballot of each (query, 32 candidates) item
+    struct {                               // bucket sort
+      int start[kBuckets];
+      int cur[kBuckets];
+    } b;
+    unsigned mask[kCellMaskCap];           // tests: ballot of each (query, chunk)
   } u;
-  long long pos[kCellMaxQ];            // count (count pass) / write position (write pass)
+  float4 q[kCellMaxQ];                     // the cell's query points
+  int qcnt[kCellMaxQ];                     // hits per query of the current batch
+  int qoff[kCellMaxQ];                     // their offsets inside the batch's scratch region
+  int scan[kCellThreads / 32];
+  long long base;                          // the batch's scratch region
   int nt, nc, out_seen, item;
 };
 
-size_t cell_smem_bytes() { return sizeof(CellSmem<true>); }
+size_t cell_smem_bytes() { return sizeof(CellSmem); }
 
 __device__ __forceinline__ int warp_incl_scan_i(int v) {
   const int lane = threadIdx.x & 31;
@@ -57,65 +68,33 @@ __device__ __forceinline__ int warp_incl_scan_i(int v) {
   return v;
 }
 
-// Ascending bitonic sort of P 64-bit keys (P a power of two, >= 32) by the
-// whole block.  Element i sits in row i/32, lane i%32.  Stages whose partner
-// distance j is below 32 stay inside a row and run in registers with warp
-// shuffles; wider stages go through shared memory.  Standard network:
-// at merge size k, element i sorts ascending when (i & k) == 0.
-__device__ __forceinline__ unsigned long long bitonic_row_stage(unsigned long long x, int i, int lane,
-                                                                int k, int j) {
-  const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, j);
-  const bool up = (i & k) == 0;
-  const bool lower = (lane & j) == 0;
-  const unsigned long long lo = x < y ? x : y, hi = x < y ? y : x;
-  return (lower == up) ? lo : hi;
-}
-
-__device__ void block_sort_u64(unsigned long long *a, int P) {
+// Exclusive block scan of one int per thread; returns the block total.
+__device__ __forceinline__ int block_excl_scan_i(int v, int &total, int *scan) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int rows = P >> 5;
-  // merge sizes 2..32: every row on its own, in registers
-  for (int r = wid; r < rows; r += nw) {
-    const int i = r * 32 + lane;
-    unsigned long long x = a[i];
-    for (int k = 2; k <= 32; k <<= 1)
-      for (int j = k >> 1; j > 0; j >>= 1) x = bitonic_row_stage(x, i, lane, k, j);
-    a[i] = x;
+  const int inc = warp_incl_scan_i(v);
+  if (lane == 31) scan[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const int x = lane < nw ? scan[lane] : 0;
+    const int y = warp_incl_scan_i(x);
+    if (lane < nw) scan[lane] = y;
   }
   __syncthreads();
-  for (int k = 64; k <= P; k <<= 1) {
-    for (int j = k >> 1; j >= 32; j >>= 1) {
-      for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const int l = i ^ j;
-        if (l > i) {
-          const unsigned long long x = a[i], y = a[l];
-          if ((x > y) == ((i & k) == 0)) {
-            a[i] = y;
-            a[l] = x;
-          }
-        }
-      }
-      __syncthreads();
-    }
-    for (int r = wid; r < rows; r += nw) {
-      const int i = r * 32 + lane;
-      unsigned long long x = a[i];
-      for (int j = 16; j > 0; j >>= 1) x = bitonic_row_stage(x, i, lane, k, j);
-      a[i] = x;
-    }
-    __syncthreads();
-  }
+  total = scan[nw - 1];
+  const int before = wid > 0 ? scan[wid - 1] : 0;
+  __syncthreads();
+  return before + inc - v;
 }
 
-template <bool WRITE>
 __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams P, Band B, unsigned flags,
-                                                       const int *__restrict__ heavy, int *work,
-                                                       int *__restrict__ over,
-                                                       long long *__restrict__ counts,
-                                                       const long long *__restrict__ offsets,
-                                                       int *__restrict__ ids, long long cap) {
+                                                          const int *__restrict__ heavy, int *work,
+                                                          int *__restrict__ over,
+                                                          long long *__restrict__ counts,
+                                                          long long *__restrict__ scr_off,
+                                                          int *__restrict__ scratch, long long scr_cap,
+                                                          unsigned long long *scr_top) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CellSmem<WRITE> &S = *reinterpret_cast<CellSmem<WRITE> *>(smem_raw);
+  CellSmem &S = *reinterpret_cast<CellSmem *>(smem_raw);
   const int nheavy = heavy[0];
   const int n = min((int)(P.dg * P.dg), g.n_max);
   const int n_tab = __ldg(g.tab_end + n);
@@ -123,10 +102,10 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   const float box2 = (P.dg + g.eps) * (P.dg + g.eps);
-  if (WRITE && offsets[g.n] > cap) {
-    if (tid == 0 && blockIdx.x == 0) atomicOr(g.status, ST_CAPACITY);
-    return;
-  }
+  // bucket of an input index: its top 10 bits within [0, n)
+  int idbits = 1;
+  while (idbits < 31 && (1 << idbits) < g.n) ++idbits;
+  const int bshift = max(idbits - 10, 0);
   for (;;) {
     if (tid == 0) S.item = atomicAdd(work, 1);
     __syncthreads();
@@ -171,7 +150,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
       }
       __syncthreads();
       const int nt = S.nt;
-      // 2. prefix of target sizes (one warp)
+      // 2a. prefix of target sizes (one warp)
       if (wid == 0) {
         int run = 0;
         for (int b0 = 0; b0 < nt; b0 += 32) {
@@ -185,18 +164,16 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
       }
       __syncthreads();
       const int ntot = S.u.t.tpre[nt];
-      // 3. gather candidates within d of the query cell box, in the query
-      //    frame; each thread keeps kGather loads in flight
+      // 2b. gather: candidates within d of the query cell box, in the query frame
       constexpr int kGather = 4;
       for (int base = 0; base < ntot; base += kGather * blockDim.x) {
-        int cj[kGather];
-        unsigned code[kGather];
+        int cj[kGather], tt[kGather];
         float4 p[kGather];
 #pragma unroll
         for (int r = 0; r < kGather; ++r) {
           const int f = base + r * blockDim.x + tid;
           cj[r] = -1;
-          code[r] = 0;
+          tt[r] = 0;
           if (f < ntot) {
             int lo = 0, hi = nt - 1;
             while (lo < hi) {
@@ -204,8 +181,8 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
               if (S.u.t.tpre[mid] <= f) lo = mid;
               else hi = mid - 1;
             }
+            tt[r] = lo;
             cj[r] = S.u.t.tbeg[lo] + (f - S.u.t.tpre[lo]);
-            code[r] = S.u.t.tcode[lo];
           }
         }
 #pragma unroll
@@ -213,18 +190,18 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
 #pragma unroll
         for (int r = 0; r < kGather; ++r) {
           bool keep = false;
-          float4 cp = p[r];
           if (cj[r] >= 0) {
-            if (code[r] & 64u) {
-              cp.x = __int_as_float(0x7fc00000);   // outside cell: FP64 test for every pair
+            const unsigned code = S.u.t.tcode[tt[r]];
+            if (code & 64u) {
+              p[r].x = __int_as_float(0x7fc00000);   // outside cell: FP64 test for every pair
               keep = true;
             } else {
-              if (code[r] & 3u) cp.x += (code[r] & 1u) ? g.Lx : -g.Lx;
-              if (code[r] & 12u) cp.y += (code[r] & 4u) ? g.Ly : -g.Ly;
-              if (code[r] & 48u) cp.z += (code[r] & 16u) ? g.Lz : -g.Lz;
-              const float ux = (cp.x - g.ox) * g.inv_s - (float)cx;
-              const float uy = (cp.y - g.oy) * g.inv_s - (float)cy;
-              const float uz = (cp.z - g.oz) * g.inv_s - (float)cz;
+              if (code & 3u) p[r].x += (code & 1u) ? g.Lx : -g.Lx;
+              if (code & 12u) p[r].y += (code & 4u) ? g.Ly : -g.Ly;
+              if (code & 48u) p[r].z += (code & 16u) ? g.Lz : -g.Lz;
+              const float ux = (p[r].x - g.ox) * g.inv_s - (float)cx;
+              const float uy = (p[r].y - g.oy) * g.inv_s - (float)cy;
+              const float uz = (p[r].z - g.oz) * g.inv_s - (float)cz;
               const float gx = fmaxf(fmaxf(-ux, ux - 1.f), 0.f);
               const float gy = fmaxf(fmaxf(-uy, uy - 1.f), 0.f);
               const float gz = fmaxf(fmaxf(-uz, uz - 1.f), 0.f);
@@ -236,11 +213,12 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
           if (lane == 0 && m) wbase = atomicAdd(&S.nc, __popc(m));
           wbase = __shfl_sync(0xffffffffu, wbase, 0);
           if (keep) {
-            const int idx = wbase + __popc(m & lt_mask);
-            if (idx < kCellCap) {
+            const int at = wbase + __popc(m & lt_mask);
+            if (at < kCellCap) {
+              float4 cp = p[r];
               cp.w = __int_as_float(cj[r]);
-              S.c[idx] = cp;
-              if (WRITE) S.key[idx] = ((unsigned long long)(unsigned)__ldg(g.perm + cj[r]) << 32) | (unsigned)idx;
+              S.c[at] = cp;
+              S.key[at] = ((unsigned long long)(unsigned)__ldg(g.perm + cj[r]) << 32) | (unsigned)at;
             }
           }
         }
@@ -249,120 +227,215 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
       fits = S.nc <= kCellCap;
     }
     if (!fits) {
-      if (!WRITE && tid == 0) {
+      // the per-query path takes every query of this cell
+      for (int i = tid; i < nq; i += blockDim.x) {
         const int o = atomicAdd(over, 1);
-        over[1 + o] = (int)key;
+        over[1 + o] = qs + i;
+        scr_off[__ldg(g.perm + qs + i)] = -1;
       }
       __syncthreads();
       continue;
     }
     const int nc = S.nc;
-    for (int i = tid; i < nq; i += blockDim.x) S.pos[i] = 0;
-    int *cid = reinterpret_cast<int *>(S.key);    // ids in candidate order (write pass)
-    if (WRITE) {
-      // candidates into ascending input-index order: sort the keys, then
-      // permute positions and ids through registers
-      int P2 = 32;
-      while (P2 < nc) P2 <<= 1;
-      for (int i = nc + tid; i < P2; i += blockDim.x) S.key[i] = ~0ull;
-      __syncthreads();
-      block_sort_u64(S.key, P2);
-      constexpr int kPer = (kCellCap + kCellThreads - 1) / kCellThreads;
-      float4 rc[kPer];
-      int rid[kPer];
+    for (int i = tid; i < nq; i += blockDim.x) S.q[i] = g.spos[qs + i];
+    // 3. ascending input index: counting pass into buckets, then each bucket
+    //    (a handful of keys) sorted by insertion
+    unsigned long long *src = S.key, *dst = S.key + kCellCap;
+    for (int b = tid; b < kBuckets; b += blockDim.x) S.u.b.start[b] = 0;
+    __syncthreads();
+    for (int p = tid; p < nc; p += blockDim.x) atomicAdd(&S.u.b.start[(int)(src[p] >> 32) >> bshift], 1);
+    __syncthreads();
+    {
+      constexpr int kPerB = kBuckets / kCellThreads;
+      int v[kPerB], sum = 0;
 #pragma unroll
-      for (int r = 0; r < kPer; ++r) {
-        const int k = tid + r * kCellThreads;
-        if (k < nc) {
-          const unsigned long long kk = S.key[k];
-          rc[r] = S.c[(int)(kk & 0xffffffffull)];
-          rid[r] = (int)(kk >> 32);
-        }
+      for (int r = 0; r < kPerB; ++r) {
+        v[r] = S.u.b.start[tid * kPerB + r];
+        sum += v[r];
       }
-      __syncthreads();
+      int total;
+      int run = block_excl_scan_i(sum, total, S.scan);
 #pragma unroll
-      for (int r = 0; r < kPer; ++r) {
-        const int k = tid + r * kCellThreads;
-        if (k < nc) {
-          S.c[k] = rc[r];
-          cid[k] = rid[r];
-        }
+      for (int r = 0; r < kPerB; ++r) {
+        S.u.b.start[tid * kPerB + r] = run;
+        S.u.b.cur[tid * kPerB + r] = run;
+        run += v[r];
       }
     }
     __syncthreads();
-    // 4. (query, 32 candidates) items spread evenly over all warps; each
-    //    item is one ballot: lanes test their candidate against the query
+    for (int p = tid; p < nc; p += blockDim.x) {
+      const unsigned long long x = src[p];
+      dst[atomicAdd(&S.u.b.cur[(int)(x >> 32) >> bshift], 1)] = x;
+    }
+    __syncthreads();
+    for (int b = tid; b < kBuckets; b += blockDim.x) {
+      const int lo = S.u.b.start[b], hi = S.u.b.cur[b];
+      for (int i = lo + 1; i < hi; ++i) {
+        const unsigned long long x = dst[i];
+        int p = i;
+        while (p > lo && dst[p - 1] > x) {
+          dst[p] = dst[p - 1];
+          --p;
+        }
+        dst[p] = x;
+      }
+    }
+    __syncthreads();
+    // permute the candidates into id order; ids go to the spare buffer
+    constexpr int kPer = (kCellCap + kCellThreads - 1) / kCellThreads;
+    float4 rc[kPer];
+    int rid[kPer];
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int k = tid + r * kCellThreads;
+      if (k < nc) {
+        const unsigned long long kk = dst[k];
+        rc[r] = S.c[(int)(kk & 0xffffffffull)];
+        rid[r] = (int)(kk >> 32);
+      }
+    }
+    __syncthreads();
+    int *cid = reinterpret_cast<int *>(src);
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int k = tid + r * kCellThreads;
+      if (k < nc) {
+        S.c[k] = rc[r];
+        cid[k] = rid[r];
+      }
+    }
+    __syncthreads();
+    // 4. tests: items (chunk of 32 candidates, group of queries) over all warps
     const int nchunk = (nc + 31) >> 5;
-    const int qbatch = WRITE ? max(1, min(nq, kCellMaskCap / nchunk)) : nq;
+    const int qbatch = max(1, min(nq, kCellMaskCap / max(nchunk, 1)));
     for (int qb = 0; qb < nq; qb += qbatch) {
       const int nqb = min(qbatch, nq - qb);
-      const int nitems = nqb * nchunk;
+      const int qsz = max(1, min(nqb, (nqb * nchunk + 2 * nw - 1) / (2 * nw)));
+      const int ngrp = (nqb + qsz - 1) / qsz;
+      const int nitems = nchunk * ngrp;
       for (int it = wid; it < nitems; it += nw) {
-        const int ql = it / nchunk;
-        const int k = (it - ql * nchunk) * 32 + lane;
-        const int sq = qs + qb + ql;               // the query's sorted slot
-        const float4 q = g.spos[sq];
-        bool hit = false;
-        if (k < nc) {
-          const float4 c = S.c[k];
+        const int grp = it / nchunk;
+        const int ch = it - grp * nchunk;
+        const int k = ch * 32 + lane;
+        float4 c = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+        if (k < nc) c = S.c[k];
+        const int j = __float_as_int(c.w);
+        const int q_end = min(nqb, (grp + 1) * qsz);
+        for (int ql = grp * qsz; ql < q_end; ++ql) {
+          const float4 q = S.q[qb + ql];
           const float dx = c.x - q.x, dy = c.y - q.y, dz = c.z - q.z;
           const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-          const int j = __float_as_int(c.w);
-          hit = d2 <= B.lo_w;
-          if (!hit && !(d2 > B.hi_w)) hit = canon_d2(q, g.spos[j], g) <= B.r2;
-          if (!incl_self) hit = hit && j != sq;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (lane == 0) {
-          if (WRITE) S.u.mask[it] = m;
-          else if (m) atomicAdd(reinterpret_cast<unsigned long long *>(&S.pos[qb + ql]),
-                                (unsigned long long)__popc(m));
+          bool hit = d2 <= B.lo_w;
+          if (!hit && !(d2 > B.hi_w) && k < nc) hit = canon_d2(q, g.spos[j], g) <= B.r2;
+          if (!incl_self) hit = hit && j != qs + qb + ql;
+          const unsigned m = __ballot_sync(0xffffffffu, hit);
+          if (lane == 0) S.u.mask[ql * nchunk + ch] = m;
         }
       }
-      if (WRITE) {
-        __syncthreads();
-        // 5. emission: one warp per query, chunks in ascending id order
-        for (int ql = wid; ql < nqb; ql += nw) {
-          const int id = __ldg(g.perm + qs + qb + ql);
-          long long base = offsets[id];
-          for (int ch = 0; ch < nchunk; ++ch) {
-            const unsigned m = S.u.mask[ql * nchunk + ch];
-            if (m) {
-              if ((m >> lane) & 1u) ids[base + __popc(m & lt_mask)] = cid[ch * 32 + lane];
-              base += __popc(m);
-            }
-          }
-          if (lane == 0 && base != offsets[id + 1]) atomicOr(g.status, ST_INTERNAL);
-        }
-        __syncthreads();
-      }
-    }
-    if (!WRITE) {
       __syncthreads();
-      for (int i = tid; i < nq; i += blockDim.x) counts[__ldg(g.perm + qs + i)] = S.pos[i];
+      // 5. counts, one scratch region for the batch, lists stored ascending
+      for (int ql = wid; ql < nqb; ql += nw) {
+        int cnt = 0;
+        for (int c0 = 0; c0 < nchunk; c0 += 32) {
+          const int ch = c0 + lane;
+          cnt += ch < nchunk ? __popc(S.u.mask[ql * nchunk + ch]) : 0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0) S.qcnt[ql] = cnt;
+      }
+      __syncthreads();
+      {
+        const int v = tid < nqb ? S.qcnt[tid] : 0;   // nqb <= kCellMaxQ == blockDim
+        int total;
+        const int ex = block_excl_scan_i(v, total, S.scan);
+        if (tid < nqb) S.qoff[tid] = ex;
+        if (tid == 0) {
+          const unsigned long long b = atomicAdd(scr_top, (unsigned long long)total);
+          S.base = (b + (unsigned long long)total <= (unsigned long long)scr_cap) ? (long long)b : -1ll;
+        }
+      }
+      __syncthreads();
+      const long long sbase = S.base;
+      for (int ql = wid; ql < nqb; ql += nw) {
+        const int s = qs + qb + ql;
+        const int id = __ldg(g.perm + s);
+        if (sbase < 0) {
+          // scratch full: this query goes to the per-query path
+          if (lane == 0) {
+            const int o = atomicAdd(over, 1);
+            over[1 + o] = s;
+            scr_off[id] = -1;
+          }
+          continue;
+        }
+        const long long qbase = sbase + S.qoff[ql];
+        if (lane == 0) {
+          counts[id] = S.qcnt[ql];
+          scr_off[id] = qbase;
+        }
+        long long wpos = qbase;
+        for (int c0 = 0; c0 < nchunk; c0 += 32) {
+          const int ch = c0 + lane;
+          const unsigned mm = ch < nchunk ? S.u.mask[ql * nchunk + ch] : 0u;
+          const int cnt = __popc(mm);
+          const int inc = warp_incl_scan_i(cnt);
+          const int lim = min(32, nchunk - c0);
+          for (int i = 0; i < lim; ++i) {
+            const unsigned mi = __shfl_sync(0xffffffffu, mm, i);
+            const int oi = __shfl_sync(0xffffffffu, inc - cnt, i);
+            if ((mi >> lane) & 1u) scratch[wpos + oi + __popc(mi & lt_mask)] = cid[(c0 + i) * 32 + lane];
+          }
+          wpos += __shfl_sync(0xffffffffu, inc, 31);
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
-si_status launch_cell_pass(bool write, const GridDev &g, const WalkParams &P, const Band &B,
-                           unsigned flags, const int *heavy, int *work, int *over, long long *counts,
-                           const long long *offsets, int *ids, long long cap, cudaStream_t st) {
-  if (write) {
-    const size_t smem = sizeof(CellSmem<true>);
-    const int grid = 148 * 2;
-    SI_CUDA_TRY(cudaFuncSetAttribute(k_cell<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SI_KLAUNCH("k_cell_write", st,
-               k_cell<true><<<grid, kCellThreads, smem, st>>>(g, P, B, flags, heavy, work, over, counts,
-                                                              offsets, ids, cap));
-  } else {
-    const size_t smem = sizeof(CellSmem<false>);
-    const int grid = 148 * 2;   // 2 blocks of 512 threads fit the register file
-    SI_CUDA_TRY(cudaFuncSetAttribute(k_cell<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SI_KLAUNCH("k_cell_count", st,
-               k_cell<false><<<grid, kCellThreads, smem, st>>>(g, P, B, flags, heavy, work, over, counts,
-                                                               offsets, ids, cap));
+// After the prefix sum: every heavy query's list from the scratch buffer to
+// its place in the output (a warp per query, coalesced both ways).
+__global__ void __launch_bounds__(256) k_cell_copy(GridDev g, const int *__restrict__ heavy,
+                                                   const long long *__restrict__ scr_off,
+                                                   const int *__restrict__ scratch,
+                                                   const long long *__restrict__ offsets, int *ids,
+                                                   long long cap) {
+  if (offsets[g.n] > cap) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(g.status, ST_CAPACITY);
+    return;
   }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+  const int nheavy = heavy[0];
+  for (int item = blockIdx.x; item < nheavy; item += gridDim.x) {
+    const unsigned key = (unsigned)heavy[1 + item];
+    const int qs = __ldg(g.cell_start + key), qe = __ldg(g.cell_start + key + 1);
+    for (int s = qs + w; s < qe; s += nwb) {
+      const int id = __ldg(g.perm + s);
+      const long long src = scr_off[id];
+      if (src < 0) continue;
+      const long long dst = offsets[id];
+      const int len = (int)(offsets[id + 1] - dst);
+      for (int i = lane; i < len; i += 32) ids[dst + i] = scratch[src + i];
+    }
+  }
+}
+
+si_status launch_cell_pass(const GridDev &g, const WalkParams &P, const Band &B, unsigned flags,
+                           const int *heavy, int *work, int *over, long long *counts, long long *scr_off,
+                           int *scratch, long long scr_cap, unsigned long long *scr_top, cudaStream_t st) {
+  const size_t smem = sizeof(CellSmem);
+  SI_CUDA_TRY(cudaFuncSetAttribute(k_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SI_KLAUNCH("k_cell", st,
+             k_cell<<<148 * 2, kCellThreads, smem, st>>>(g, P, B, flags, heavy, work, over, counts, scr_off,
+                                                        scratch, scr_cap, scr_top));
+  return SI_OK;
+}
+
+si_status launch_cell_copy(const GridDev &g, const int *heavy, const long long *scr_off, const int *scratch,
+                           const long long *offsets, int *ids, long long cap, cudaStream_t st) {
+  SI_KLAUNCH("k_cell_copy", st,
+             k_cell_copy<<<148 * 8, 256, 0, st>>>(g, heavy, scr_off, scratch, offsets, ids, cap));
   return SI_OK;
 }
 

@@ -9,6 +9,7 @@
 #include <new>
 
 #include "si_host.h"
+#include "si_sort.cuh"
 
 namespace si {
 
@@ -414,6 +415,119 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const float4 *__restrict__ 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Order the points of every cell by input index.  The scatter places them in
+// atomic arrival order; ordered cells make every later step deterministic and
+// give the cell kernel runs of candidates already sorted by id.  Only the
+// permutation is sorted; positions are then gathered again from the input.
+// ---------------------------------------------------------------------------
+constexpr int kOrderLocal = 16;      // cells up to this size: one thread, insertion sort
+constexpr int kOrderWarps = 8;
+constexpr int kOrderWarpCap = 2048;  // cells up to this size: one warp, shared memory
+constexpr int kOrderBlockCap = 16384;
+
+__global__ void __launch_bounds__(256) k_cell_order(const int *__restrict__ start, int n_cells,
+                                                    const float4 *__restrict__ pos, float4 *spos,
+                                                    int *perm, int *bigq) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const int b = __ldg(start + c), m = __ldg(start + c + 1) - b;
+  if (m < 2) return;
+  if (m > kOrderLocal) {
+    const int slot = atomicAdd(bigq, 1);
+    bigq[1 + slot] = c;
+    return;
+  }
+  int id[kOrderLocal];
+  bool moved = false;
+  for (int i = 0; i < m; ++i) {
+    const int v = perm[b + i];
+    int p = i;
+    while (p > 0 && id[p - 1] > v) {
+      id[p] = id[p - 1];
+      --p;
+    }
+    id[p] = v;
+    moved |= p != i;
+  }
+  if (!moved) return;
+  for (int i = 0; i < m; ++i) {
+    perm[b + i] = id[i];
+    spos[b + i] = __ldg(pos + id[i]);
+  }
+}
+
+__global__ void __launch_bounds__(kOrderWarps * 32) k_cell_order_big(const int *__restrict__ start,
+                                                                    const float4 *__restrict__ pos,
+                                                                    float4 *spos, int *perm,
+                                                                    const int *__restrict__ bigq,
+                                                                    int *hugeq) {
+  extern __shared__ int obuf[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int *buf = obuf + w * kOrderWarpCap;
+  const int nq = bigq[0];
+  for (int item = blockIdx.x * kOrderWarps + w; item < nq; item += gridDim.x * kOrderWarps) {
+    const int c = bigq[1 + item];
+    const int b = __ldg(start + c), m = __ldg(start + c + 1) - b;
+    if (m > kOrderWarpCap) {
+      if (lane == 0) {
+        const int slot = atomicAdd(hugeq, 1);
+        hugeq[1 + slot] = c;
+      }
+      continue;
+    }
+    for (int i = lane; i < m; i += 32) buf[i] = perm[b + i];
+    __syncwarp();
+    bitonic_padded(buf, m, lane, 32, WarpSync());
+    for (int i = lane; i < m; i += 32) {
+      perm[b + i] = buf[i];
+      spos[b + i] = __ldg(pos + buf[i]);
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(512) k_cell_order_huge(const int *__restrict__ start,
+                                                        const float4 *__restrict__ pos, float4 *spos,
+                                                        int *perm, const int *__restrict__ hugeq) {
+  extern __shared__ int obuf[];
+  const int nq = hugeq[0];
+  for (int item = blockIdx.x; item < nq; item += gridDim.x) {
+    const int c = hugeq[1 + item];
+    const int b = __ldg(start + c), m = __ldg(start + c + 1) - b;
+    int *a = perm + b;
+    if (m <= kOrderBlockCap) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) obuf[i] = a[i];
+      __syncthreads();
+      bitonic_padded(obuf, m, threadIdx.x, blockDim.x, BlockSync());
+      for (int i = threadIdx.x; i < m; i += blockDim.x) a[i] = obuf[i];
+    } else {
+      bitonic_padded(a, m, threadIdx.x, blockDim.x, BlockSync());
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) spos[b + i] = __ldg(pos + a[i]);
+    __syncthreads();
+  }
+}
+
+si_status order_cells(const int *start, int64_t n_cells, const float4 *pos, float4 *spos, int *perm,
+                      int *bigq, int *hugeq, cudaStream_t st) {
+  SI_CUDA_TRY(cudaMemsetAsync(bigq, 0, sizeof(int), st));
+  SI_CUDA_TRY(cudaMemsetAsync(hugeq, 0, sizeof(int), st));
+  SI_KLAUNCH("k_cell_order", st,
+             k_cell_order<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(start, (int)n_cells, pos, spos,
+                                                                              perm, bigq));
+  const size_t wsm = (size_t)kOrderWarps * kOrderWarpCap * sizeof(int);
+  SI_CUDA_TRY(cudaFuncSetAttribute(k_cell_order_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
+  SI_KLAUNCH("k_cell_order_big", st,
+             k_cell_order_big<<<148 * 2, kOrderWarps * 32, wsm, st>>>(start, pos, spos, perm, bigq, hugeq));
+  const size_t bsm = (size_t)kOrderBlockCap * sizeof(int);
+  SI_CUDA_TRY(cudaFuncSetAttribute(k_cell_order_huge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+  SI_KLAUNCH("k_cell_order_huge", st,
+             k_cell_order_huge<<<148, 512, bsm, st>>>(start, pos, spos, perm, hugeq));
+  return SI_OK;
+}
+
 }  // namespace si
 
 using namespace si;
@@ -446,6 +560,9 @@ static void grid_free(si_grid *g) {
   cudaFree(g->hugeq);
   cudaFree(g->heavy);
   cudaFree(g->over);
+  cudaFree(g->scr_off);
+  cudaFree(g->scr_top);
+  cudaFree(g->scratch);
   cudaFree(g->counters);
   cudaFree(g->partial);
   cudaFree(g->cls);
@@ -497,7 +614,11 @@ extern "C" si_status si_grid_create(const si_grid_desc *desc, int64_t n_capacity
   SI_ALLOC(g->longq, (cap1 + 1) * sizeof(int));
   SI_ALLOC(g->hugeq, (cap1 + 1) * sizeof(int));
   SI_ALLOC(g->heavy, (cap1 / kHeavyMinBuild + 2) * sizeof(int));
-  SI_ALLOC(g->over, (cap1 / kHeavyMinBuild + 2) * sizeof(int));
+  SI_ALLOC(g->over, (cap1 + 1) * sizeof(int));
+  SI_ALLOC(g->scr_off, cap1 * sizeof(long long));
+  SI_ALLOC(g->scr_top, sizeof(unsigned long long));
+  g->scr_cap = 4 * cap1;
+  SI_ALLOC(g->scratch, g->scr_cap * sizeof(int));
   SI_ALLOC(g->counters, kCounterInts * sizeof(int));
   g->partial_len = (cap1 + 127) / 128 + 1;
   SI_ALLOC(g->partial, g->partial_len * sizeof(double));
@@ -557,6 +678,10 @@ extern "C" si_status si_grid_build(si_grid *g, const float *d_pos, int64_t n, vo
     SI_KLAUNCH("k_bin_scatter", st, k_bin_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
         (const float4 *)d_pos, (int)n, g->key_slot, g->cell_start, g->spos, g->perm, 1u << g->lat.W,
         g->heavy));
+    // the query kernels are idle during a build: their queues serve as scratch
+    s = order_cells(g->cell_start, g->n_cells, (const float4 *)d_pos, g->spos, g->perm, g->longq, g->hugeq,
+                    st);
+    if (s != SI_OK) return s;
   }
   return SI_OK;
 }

@@ -138,7 +138,11 @@ struct si_grid {
   int *longq = nullptr;          // cap + 1: [0] = count, then query ids of long lists
   int *hugeq = nullptr;          // cap + 1: lists too long for a warp sort
   int *heavy = nullptr;          // [0] = count, then cells with >= kHeavyMin points (set by build)
-  int *over = nullptr;           // [0] = count, then heavy cells that did not fit the cell kernel
+  int *over = nullptr;           // [0] = count, then sorted slots of queries the cell kernel handed back
+  long long *scr_off = nullptr;  // per input index: where the cell kernel put its list (-1: not there)
+  int *scratch = nullptr;        // lists written by the cell kernel before the prefix sum
+  long long scr_cap = 0;
+  unsigned long long *scr_top = nullptr;   // bump allocator of the scratch (also the size needed)
   int *counters = nullptr;       // kCounterInts work counters
   std::vector<int> tab_end_host; // host copy of the table's end[] index
   // sub-cell class tables for the current radius (see si_class.cu)

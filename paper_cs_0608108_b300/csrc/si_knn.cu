@@ -14,11 +14,10 @@
 
 namespace si {
 
-constexpr int kKnnThreads = 64;
+constexpr int kKnnThreads = 128;
 
 struct KnnList {
   // column layout [k * T + t]: thread t's k-th entry; conflict-free
-  double *D;     // canonical D2, NaN until needed
   float *d;      // FP32 squared distance
   int *j;        // sorted slot of the candidate
   int T, t;
@@ -28,7 +27,7 @@ struct KnnList {
 struct Cand {
   float d;
   int j;
-  double D;      // NaN until needed
+  double D;      // canonical D2, NaN until needed
 };
 
 __device__ __forceinline__ double cand_D(Cand &c, const GridDev &g, const QueryGeom &Q) {
@@ -37,22 +36,20 @@ __device__ __forceinline__ double cand_D(Cand &c, const GridDev &g, const QueryG
 }
 
 // a < b in the exact (D2, index) order, deciding in FP32 when the values are
-// further apart than their combined error bound.
-__device__ __forceinline__ bool cand_less(Cand &a, KnnList &L, int kb, const GridDev &g,
+// further apart than their combined error bound; near-ties are decided by the
+// canonical FP64 values (recomputed: they are rare) and then by index.
+__device__ __forceinline__ bool cand_less(Cand &a, const KnnList &L, int kb, const GridDev &g,
                                           const QueryGeom &Q, const PairBand &pb) {
   const float bd = L.d[L.at(kb)];
   const float m = fmaxf(a.d, bd) * 1.000001f;
   const float band = fmaf(pb.c2, m, pb.c1 * sqrtf(m)) + 1e-37f;
   if (a.d + band < bd) return true;
   if (bd + band < a.d) return false;
+  const int jb = L.j[L.at(kb)];
   const double Da = cand_D(a, g, Q);
-  double Db = L.D[L.at(kb)];
-  if (isnan(Db)) {
-    Db = canon_d2(Q.q, g.spos[L.j[L.at(kb)]], g);
-    L.D[L.at(kb)] = Db;
-  }
+  const double Db = canon_d2(Q.q, g.spos[jb], g);
   if (Da != Db) return Da < Db;
-  return __ldg(g.perm + a.j) < __ldg(g.perm + L.j[L.at(kb)]);
+  return __ldg(g.perm + a.j) < __ldg(g.perm + jb);
 }
 
 __global__ void __launch_bounds__(kKnnThreads) k_knn(GridDev g, int K, float dmax_g, int n_query,
@@ -63,8 +60,7 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(GridDev g, int K, float dma
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x;
   KnnList L;
-  L.D = (double *)smem;
-  L.d = (float *)(L.D + (size_t)K * T);
+  L.d = (float *)smem;
   L.j = (int *)(L.d + (size_t)K * T);
   L.T = T;
   L.t = threadIdx.x;
@@ -86,18 +82,16 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(GridDev g, int K, float dma
       p = cnt++;
     }
     while (p > 0 && cand_less(c, L, p - 1, g, Q, pb)) {
-      L.D[L.at(p)] = L.D[L.at(p - 1)];
       L.d[L.at(p)] = L.d[L.at(p - 1)];
       L.j[L.at(p)] = L.j[L.at(p - 1)];
       --p;
     }
-    L.D[L.at(p)] = c.D;
     L.d[L.at(p)] = c.d;
     L.j[L.at(p)] = c.j;
     if (cnt == K) {
       // shrink: anything that can still enter has D2 <= D2_K, and D2_K is
       // at most d_K + its error; cells further than that are skipped and the
-      // walk ends at the first b beyond it
+      // walk ends at the first b beyond it (Sec. II.A, K nearest)
       const float dk = L.d[L.at(K - 1)];
       const float m = dk * 1.000001f;
       kth_hi = fminf(hi_max, dk + fmaf(pb.c2, m, pb.c1 * sqrtf(m)) + 1e-37f);
@@ -106,8 +100,7 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(GridDev g, int K, float dma
     }
   };
 
-  auto cell = [&](const Target &tg) {
-    const int b = __ldg(g.cell_start + tg.key), e = __ldg(g.cell_start + tg.key + 1);
+  auto cell = [&](const Target &tg, int b, int e) {
     for (int j = b; j < e; ++j) {
       if (j == self) continue;
       const float4 p = g.spos[j];
@@ -138,19 +131,46 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(GridDev g, int K, float dma
   if (!Q.outside) {
     bool out_seen = false;
     const int te = __ldg(g.tab_end + n_query);
-    for (int i = 0; i < te; ++i) {
-      const TabEntry e = g.tab[i];
-      if ((float)e.b2 > cut2) break;            // early cut-off (Sec. II.A)
-      if (cell_t2(e, Q) > cut2) continue;      // exact cell test (Eq. 1)
-      const Target tg = translate(e, Q, g);
-      if (tg.outside) {
-        if (out_seen) continue;
-        out_seen = true;
+    constexpr int kG = 4;
+    for (int i0 = 0; i0 < te; i0 += kG) {
+      if ((float)__ldg(&g.tab[i0].b2) > cut2) break;          // early cut-off (Sec. II.A)
+      Target tg[kG];
+      float t2[kG];
+      int cb[kG], ce[kG];
+      bool ok[kG];
+#pragma unroll
+      for (int r = 0; r < kG; ++r) {
+        ok[r] = false;
+        t2[r] = 0.f;
+        if (i0 + r < te) {
+          const TabEntry e = g.tab[i0 + r];
+          t2[r] = cell_t2(e, Q);                               // exact cell test (Eq. 1)
+          ok[r] = (float)e.b2 <= cut2 && t2[r] <= cut2;
+          if (ok[r]) {
+            tg[r] = translate(e, Q, g);
+            if (tg[r].outside && out_seen) ok[r] = false;
+          }
+        }
       }
-      cell(tg);
+#pragma unroll
+      for (int r = 0; r < kG; ++r) {
+        cb[r] = ok[r] ? __ldg(g.cell_start + tg[r].key) : 0;
+        ce[r] = ok[r] ? __ldg(g.cell_start + tg[r].key + 1) : 0;
+      }
+#pragma unroll
+      for (int r = 0; r < kG; ++r) {
+        if (!ok[r] || t2[r] > cut2) continue;                    // cut2 may have shrunk
+        if (tg[r].outside) {                                     // the outside cell: once
+          if (out_seen) continue;
+          out_seen = true;
+        }
+        cell(tg[r], cb[r], ce[r]);
+      }
     }
   } else {
-    auto v = [&](const Target &tg, bool) { cell(tg); };
+    auto v = [&](const Target &tg, bool) {
+      cell(tg, __ldg(g.cell_start + tg.key), __ldg(g.cell_start + tg.key + 1));
+    };
     walk_cube(g, Q, dmax_g, v);
   }
 
@@ -200,7 +220,7 @@ extern "C" si_status si_query_knn(si_grid *g, const float *d_centers, int64_t m,
     B = make_band(lat, r_max_query);
   }
   const PairBand pb = make_pair_band(lat);
-  const size_t smem = (size_t)k * kKnnThreads * 16;
+  const size_t smem = (size_t)k * kKnnThreads * 8;
   SI_CUDA_TRY(cudaFuncSetAttribute(k_knn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const unsigned blocks = (unsigned)((m + kKnnThreads - 1) / kKnnThreads);
   SI_KLAUNCH("k_knn", st, k_knn<<<blocks, kKnnThreads, smem, st>>>(g->dev(), k, dmax_g, n_query, B, pb, flags, d_ids, d_d2,

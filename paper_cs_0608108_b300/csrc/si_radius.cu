@@ -12,6 +12,7 @@
 
 #include "si_host.h"
 #include "si_radius.cuh"
+#include "si_sort.cuh"
 
 namespace si {
 
@@ -21,8 +22,7 @@ struct CountVisitor {
   const Band &B;
   int self;
   long long count;
-  __device__ __forceinline__ void operator()(const Target &t, bool full) {
-    const int b = __ldg(g.cell_start + t.key), e = __ldg(g.cell_start + t.key + 1);
+  __device__ __forceinline__ void operator()(const Target &t, bool full, int b, int e) {
     if (full) {
       count += e - b - ((self >= b && self < e) ? 1 : 0);
       return;
@@ -31,6 +31,9 @@ struct CountVisitor {
       const float4 p = g.spos[j];
       if (j != self && pair_hit(g, Q, t, B, p)) ++count;
     }
+  }
+  __device__ __forceinline__ void operator()(const Target &t, bool full) {
+    (*this)(t, full, __ldg(g.cell_start + t.key), __ldg(g.cell_start + t.key + 1));
   }
 };
 
@@ -59,12 +62,14 @@ struct WriteVisitor {
     }
     ++k;
   }
-  __device__ __forceinline__ void operator()(const Target &t, bool full) {
-    const int b = __ldg(g.cell_start + t.key), e = __ldg(g.cell_start + t.key + 1);
+  __device__ __forceinline__ void operator()(const Target &t, bool full, int b, int e) {
     for (int j = b; j < e; ++j) {
       if (j == self) continue;
       if (full || pair_hit(g, Q, t, B, g.spos[j])) emit(__ldg(g.perm + j));
     }
+  }
+  __device__ __forceinline__ void operator()(const Target &t, bool full) {
+    (*this)(t, full, __ldg(g.cell_start + t.key), __ldg(g.cell_start + t.key + 1));
   }
 };
 
@@ -148,7 +153,7 @@ __global__ void __launch_bounds__(kClassThreads) k_radius_cls(GridDev g, WalkPar
     radius_one<WRITE, kWalkClasses>(gs, P, B, flags, s, heavy_min, counts, offsets, ids, cap, longq);
 }
 
-// Queries of the heavy cells that did not fit the cell kernel: per query.
+// Queries the cell kernel handed back (listed by sorted slot): per query.
 template <bool WRITE>
 __global__ void __launch_bounds__(kQueryThreads) k_radius_over(GridDev g, WalkParams P, Band B,
                                                                unsigned flags, const int *over,
@@ -156,55 +161,9 @@ __global__ void __launch_bounds__(kQueryThreads) k_radius_over(GridDev g, WalkPa
                                                                const long long *offsets, int *ids,
                                                                long long cap, int *longq) {
   const int nover = over[0];
-  for (int item = blockIdx.x; item < nover; item += gridDim.x) {
-    const unsigned key = (unsigned)over[1 + item];
-    const int qs = __ldg(g.cell_start + key), qe = __ldg(g.cell_start + key + 1);
-    for (int s = qs + threadIdx.x; s < qe; s += blockDim.x)
-      radius_one<WRITE, kWalkPaper>(g, P, B, flags, s, 0, counts, offsets, ids, cap, longq);
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nover; i += gridDim.x * blockDim.x)
+    radius_one<WRITE, kWalkPaper>(g, P, B, flags, over[1 + i], 0, counts, offsets, ids, cap, longq);
 }
-
-// Ascending bitonic sort of a[0..n) with +inf padding up to the next power
-// of two, by `lanes` cooperating threads (rank = thread's index among them);
-// sync() separates the stages.  Every compare-exchange puts the smaller value
-// at the lower index (first step of each merge compares mirrored pairs), so
-// a pair whose upper index is past n never moves anything.
-template <class Sync>
-__device__ __forceinline__ void bitonic_padded(int *a, int n, int rank, int lanes, Sync sync) {
-  int P = 1;
-  while (P < n) P <<= 1;
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int i = rank; i < P / 2; i += lanes) {
-      const int lo = (i / (k / 2)) * k + (i % (k / 2));
-      const int hi = (lo / k) * k + (k - 1 - (lo % k));
-      if (hi < n && a[hi] < a[lo]) {
-        const int t = a[lo];
-        a[lo] = a[hi];
-        a[hi] = t;
-      }
-    }
-    sync();
-    for (int h = k / 4; h >= 1; h >>= 1) {
-      for (int i = rank; i < P / 2; i += lanes) {
-        const int lo = (i / h) * 2 * h + (i % h);
-        const int hi = lo + h;
-        if (hi < n && a[hi] < a[lo]) {
-          const int t = a[lo];
-          a[lo] = a[hi];
-          a[hi] = t;
-        }
-      }
-      sync();
-    }
-  }
-}
-
-struct WarpSync {
-  __device__ __forceinline__ void operator()() const { __syncwarp(); }
-};
-struct BlockSync {
-  __device__ __forceinline__ void operator()() const { __syncthreads(); }
-};
 
 // One warp per queued list (up to kSortWarpCap ids, in shared memory); longer
 // lists are passed on to the block sort.
@@ -341,30 +300,52 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   const bool heavy = !cube && n_tab >= 0 && g->tab_end_host[n_tab] <= kCellTCap;
   const int heavy_min = heavy ? kHeavyMin : 0;
   long long *off = (long long *)d_offsets;
-  SI_CUDA_TRY(cudaMemsetAsync(off, 0, sizeof(long long), st));
-  SI_CUDA_TRY(cudaMemsetAsync(g->counters, 0, kCounterInts * sizeof(int), st));
-  SI_CUDA_TRY(cudaMemsetAsync(g->over, 0, sizeof(int), st));
   const unsigned blocks = (unsigned)((m + kQueryThreads - 1) / kQueryThreads);
-  int *work_c = g->counters, *work_w = g->counters + 1;
   si_status s;
-  if (m > 0) {
-    if ((s = launch_light<false>(walk, g, dv, P, B, flags, heavy_min, off + 1, nullptr, nullptr, 0,
+  // count phase: per-query counts of light cells, the cell kernel's counts
+  // and scratch lists for heavy cells, per-query counts of what it handed back
+  auto count_phase = [&]() -> si_status {
+    SI_CUDA_TRY(cudaMemsetAsync(off, 0, sizeof(long long), st));
+    SI_CUDA_TRY(cudaMemsetAsync(g->counters, 0, kCounterInts * sizeof(int), st));
+    SI_CUDA_TRY(cudaMemsetAsync(g->over, 0, sizeof(int), st));
+    SI_CUDA_TRY(cudaMemsetAsync(g->scr_top, 0, sizeof(unsigned long long), st));
+    if (m == 0) return SI_OK;
+    si_status r;
+    if ((r = launch_light<false>(walk, g, dv, P, B, flags, heavy_min, off + 1, nullptr, nullptr, 0,
                                  nullptr, blocks, st)) != SI_OK)
-      return s;
+      return r;
     if (heavy) {
-      if ((s = launch_cell_pass(false, dv, P, B, flags, g->heavy, work_c, g->over, off + 1, nullptr,
-                                nullptr, 0, st)) != SI_OK)
-        return s;
+      if ((r = launch_cell_pass(dv, P, B, flags, g->heavy, g->counters, g->over, off + 1, g->scr_off,
+                                g->scratch, g->scr_cap, g->scr_top, st)) != SI_OK)
+        return r;
       SI_KLAUNCH("k_radius_over_count", st,
                  k_radius_over<false><<<148 * 4, kQueryThreads, 0, st>>>(dv, P, B, flags, g->over,
                                                                          off + 1, nullptr, nullptr, 0,
                                                                          nullptr));
     }
-    if ((s = scan_inclusive_i64(off + 1, off + 1, m, g->scan_i64, st)) != SI_OK) return s;
-  }
+    return scan_inclusive_i64(off + 1, off + 1, m, g->scan_i64, st);
+  };
+  if ((s = count_phase()) != SI_OK) return s;
   if (h_total) {
     SI_CUDA_TRY(cudaMemcpyAsync(g->h_pinned, off + m, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    SI_CUDA_TRY(cudaMemcpyAsync(g->h_pinned + 1, g->scr_top, sizeof(long long), cudaMemcpyDeviceToHost, st));
     SI_CUDA_TRY(cudaStreamSynchronize(st));
+    // cells whose lists did not fit the scratch took the per-query path;
+    // make room and count again so that the cell kernel serves them
+    if (heavy && g->h_pinned[1] > g->scr_cap) {
+      const long long want = g->h_pinned[1] + g->h_pinned[1] / 4 + 1024;
+      int *fresh = nullptr;
+      if (cudaMalloc((void **)&fresh, want * sizeof(int)) == cudaSuccess) {
+        cudaFree(g->scratch);
+        g->scratch = fresh;
+        g->scr_cap = want;
+        if ((s = count_phase()) != SI_OK) return s;
+        SI_CUDA_TRY(cudaMemcpyAsync(g->h_pinned, off + m, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        SI_CUDA_TRY(cudaStreamSynchronize(st));
+      } else {
+        cudaGetLastError();   // keep the old scratch; results stay exact
+      }
+    }
     *h_total = g->h_pinned[0];
     if (*h_total > ids_capacity) return fail(SI_ERR_CAPACITY, "neighbor id buffer too small");
   }
@@ -375,8 +356,7 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
                               g->longq, blocks, st)) != SI_OK)
     return s;
   if (heavy) {
-    if ((s = launch_cell_pass(true, dv, P, B, flags, g->heavy, work_w, g->over, nullptr, off, d_ids,
-                              ids_capacity, st)) != SI_OK)
+    if ((s = launch_cell_copy(dv, g->heavy, g->scr_off, g->scratch, off, d_ids, ids_capacity, st)) != SI_OK)
       return s;
     SI_KLAUNCH("k_radius_over_write", st,
                k_radius_over<true><<<148 * 4, kQueryThreads, 0, st>>>(dv, P, B, flags, g->over, nullptr,

@@ -12,8 +12,7 @@ constexpr int kClassThreads = 256;   // per-query kernel with shared-memory clas
 constexpr int kInlineSort = 32;      // lists up to this length are sorted while written
 constexpr int kHeavyMin = kHeavyMinBuild;   // cells with this many points take the cell path
 constexpr int kCellThreads = 512;
-constexpr int kCellCap = 3072;       // staged candidates per query cell
-constexpr int kCellKeyCap = 4096;    // power of two >= kCellCap (sort keys)
+constexpr int kCellCap = 2560;       // staged candidates per query cell
 constexpr int kCellMaxQ = 512;       // queries of one cell in one block
 constexpr int kCellTCap = 512;       // target cells of the cell-level sphere
 constexpr int kCellMaskCap = 4096;   // (query, 32-candidate) ballots kept per query batch
@@ -22,8 +21,10 @@ constexpr int kSortWarpCap = 2048;   // lists a warp sorts in shared memory
 constexpr int kSortBlockCap = 16384; // lists a block sorts in shared memory
 
 size_t cell_smem_bytes();
-si_status launch_cell_pass(bool write, const GridDev &g, const WalkParams &P, const Band &B,
-                           unsigned flags, const int *heavy, int *work, int *over, long long *counts,
+si_status launch_cell_pass(const GridDev &g, const WalkParams &P, const Band &B, unsigned flags,
+                           const int *heavy, int *work, int *over, long long *counts, long long *scr_off,
+                           int *scratch, long long scr_cap, unsigned long long *scr_top, cudaStream_t st);
+si_status launch_cell_copy(const GridDev &g, const int *heavy, const long long *scr_off, const int *scratch,
                            const long long *offsets, int *ids, long long cap, cudaStream_t st);
 
 }  // namespace si

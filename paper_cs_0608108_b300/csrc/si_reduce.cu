@@ -23,8 +23,10 @@ struct ReduceVisitor {
   int self;
   bool want_grad;
   float e, gx, gy, gz;
-  __device__ __forceinline__ void operator()(const Target &t, bool) {
-    const int b = __ldg(g.cell_start + t.key), en = __ldg(g.cell_start + t.key + 1);
+  __device__ __forceinline__ void operator()(const Target &t, bool f) {
+    (*this)(t, f, __ldg(g.cell_start + t.key), __ldg(g.cell_start + t.key + 1));
+  }
+  __device__ __forceinline__ void operator()(const Target &t, bool, int b, int en) {
     for (int j = b; j < en; ++j) {
       if (j == self) continue;
       const float4 p = g.spos[j];
