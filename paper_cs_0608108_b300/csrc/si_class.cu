@@ -27,6 +27,11 @@ int64_t class_capacity(const Lattice &lat, int64_t table_entries) {
   return cap <= (int64_t)kClassCapMax ? cap : 0;
 }
 
+// Entry layout (one per x-row run of cells):
+//   bits  0..47  the run's (0, oy, oz) offset in unpacked form ((w+1)-bit fields)
+//   bits 48..55  ox_lo, the run's first x offset (int8)
+//   bits 56..62  run length in cells (1..127)
+//   bit  63      every cell of the run lies wholly within d of the sub-box
 void build_class_tables(const Lattice &lat, double dg, int q, std::vector<unsigned long long> &ent,
                         std::vector<int> &begin) {
   const int W = lat.W;
@@ -35,26 +40,16 @@ void build_class_tables(const Lattice &lat, double dg, int q, std::vector<unsign
   int lim[3];
   for (int a = 0; a < 3; ++a)
     lim[a] = ((lat.cyc >> a) & 1u) ? reach : std::min(reach, (1 << lat.w[a]) - 1);
-  struct Off {
-    int b2, o[3];
-  };
-  std::vector<Off> offs;
-  for (int oz = -lim[2]; oz <= lim[2]; ++oz)
-    for (int oy = -lim[1]; oy <= lim[1]; ++oy)
-      for (int ox = -lim[0]; ox <= lim[0]; ++ox) {
-        const int o[3] = {ox, oy, oz};
-        int b2 = 0;
-        for (int a = 0; a < 3; ++a) {
-          const int b = std::max(std::abs(o[a]) - 1, 0);
-          b2 += b * b;
-        }
-        if ((double)b2 <= dg * dg) offs.push_back({b2, {ox, oy, oz}});
-      }
-  std::stable_sort(offs.begin(), offs.end(), [](const Off &x, const Off &y) { return x.b2 < y.b2; });
   const double m = lat.eps;                 // sub-box grown by the binning margin
   const double d_in = dg - 2.0 * lat.eps;   // inclusion uses d shrunk by the margin
+  struct Run {
+    int b2;                                 // smallest b^2 of the run's cells (center-to-edge order)
+    int oy, oz, lo, len;
+    bool full;
+  };
   ent.clear();
   begin.assign((size_t)q * q * q + 1, 0);
+  std::vector<Run> runs;
   for (int k = 0; k < q; ++k)
     for (int j = 0; j < q; ++j)
       for (int i = 0; i < q; ++i) {
@@ -66,21 +61,43 @@ void build_class_tables(const Lattice &lat, double dg, int q, std::vector<unsign
           lo[a] = (double)idx[a] / q - m;
           hi[a] = (double)(idx[a] + 1) / q + m;
         }
-        for (const Off &f : offs) {
-          double g2 = 0.0, far2 = 0.0;
-          for (int a = 0; a < 3; ++a) {
-            const double gap = std::max(std::max((double)f.o[a] - hi[a], lo[a] - (double)(f.o[a] + 1)), 0.0);
-            g2 += gap * gap;
-            const double far = std::max((double)(f.o[a] + 1) - lo[a], hi[a] - (double)f.o[a]);
-            far2 += far * far;
+        runs.clear();
+        for (int oz = -lim[2]; oz <= lim[2]; ++oz)
+          for (int oy = -lim[1]; oy <= lim[1]; ++oy) {
+            // cells of this row within dg of the sub-box form one x-interval
+            Run r{1 << 30, oy, oz, 0, 0, true};
+            for (int ox = -lim[0]; ox <= lim[0]; ++ox) {
+              const int o[3] = {ox, oy, oz};
+              double g2 = 0.0, far2 = 0.0;
+              int b2 = 0;
+              for (int a = 0; a < 3; ++a) {
+                const double gap =
+                    std::max(std::max((double)o[a] - hi[a], lo[a] - (double)(o[a] + 1)), 0.0);
+                g2 += gap * gap;
+                const double far = std::max((double)(o[a] + 1) - lo[a], hi[a] - (double)o[a]);
+                far2 += far * far;
+                const int bb = std::max(std::abs(o[a]) - 1, 0);
+                b2 += bb * bb;
+              }
+              if (g2 > dg * dg) continue;
+              if (r.len == 0) r.lo = ox;
+              r.len = ox - r.lo + 1;          // convex region: the kept ox are contiguous
+              r.b2 = std::min(r.b2, b2);
+              r.full = r.full && d_in > 0.0 && far2 <= d_in * d_in;
+            }
+            if (r.len > 0) runs.push_back(r);
           }
-          if (g2 > dg * dg) continue;
+        std::stable_sort(runs.begin(), runs.end(), [](const Run &x, const Run &y) { return x.b2 < y.b2; });
+        for (const Run &r : runs) {
           unsigned long long u = 0;
-          for (int a = 0; a < 3; ++a) {
+          const int o[3] = {0, r.oy, r.oz};
+          for (int a = 1; a < 3; ++a) {
             const unsigned long long fieldmask = (1ull << (lat.w[a] + 1)) - 1ull;
-            u |= ((unsigned long long)(long long)f.o[a] & fieldmask) << pos[a];
+            u |= ((unsigned long long)(long long)o[a] & fieldmask) << pos[a];
           }
-          if (d_in > 0.0 && far2 <= d_in * d_in) u |= 1ull << 63;
+          u |= (unsigned long long)(unsigned char)(signed char)r.lo << 48;
+          u |= (unsigned long long)(r.len & 127) << 56;
+          if (r.full) u |= 1ull << 63;
           ent.push_back(u);
         }
       }

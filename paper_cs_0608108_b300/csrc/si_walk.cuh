@@ -60,7 +60,11 @@ __device__ __forceinline__ void walk_sphere(const GridDev &g, const QueryGeom &Q
 // precomputed lists holding exactly the cells within d of that sub-cell box,
 // center to edge; no run-time cell test is needed.  This refines the 64
 // direction-bit tables of Sec. III.A (which select by f < zeta only).
-// cls / begin may point to global or to shared memory (plain loads).
+// cls / begin may point to global or to shared memory (plain loads).  Each
+// entry is an x-row run of cells; consecutive x cells are consecutive packed
+// indices (Sec. II.B), so a run's points are one contiguous range of the
+// sorted array: two cell-start loads per run.  The visitor is called as
+// visit(target, whole_run_inside, first_point, end_point).
 template <class V>
 __device__ __forceinline__ void walk_classes_in(const GridDev &g, const QueryGeom &Q,
                                                 const unsigned long long *cls, const int *begin, int q,
@@ -70,17 +74,60 @@ __device__ __forceinline__ void walk_classes_in(const GridDev &g, const QueryGeo
   const int k = min((int)(Q.phi[2] * (float)q), q - 1);
   const int c = (k * q + j) * q + i;
   const int b = begin[c], e = begin[c + 1];
+  const int Gx = 1 << g.wx;
+  const bool cyc_x = g.cyc & 1u;
   bool out_seen = false;
+  auto outside = [&]() {
+    if (out_seen) return;
+    out_seen = true;
+    Target t;
+    t.key = g.outside;
+    t.outside = true;
+    t.wrapped = false;
+    t.qx = Q.q.x;
+    t.qy = Q.q.y;
+    t.qz = Q.q.z;
+    visit(t, false, __ldg(g.cell_start + g.outside), __ldg(g.cell_start + g.outside + 1));
+  };
   for (int t = b; t < e; ++t) {
     const unsigned long long E = cls[t];
-    const Target tg = translate_raw(E & ~(1ull << 63), Q, g);
+    const int lo = (int)(signed char)((E >> 48) & 0xffull);
+    const int len = (int)((E >> 56) & 127ull);
+    const bool full = (E >> 63) != 0ull;
+    // the row's y and z by the SWAR add (x field stays the query's own)
+    Target tg = translate_raw(E & ((1ull << 48) - 1ull), Q, g);
     if (tg.outside) {
-      if (out_seen) continue;
-      out_seen = true;
+      outside();
+      continue;
     }
-    visit(tg, (E >> 63) != 0ull && !tg.outside);
+    const unsigned row = tg.key - (unsigned)Q.c[0];   // packed index of x = 0 in that row
+    int x0 = Q.c[0] + lo, x1 = x0 + len - 1;
+    if (!cyc_x) {
+      if (x0 < 0 || x1 >= Gx) outside();
+      x0 = max(x0, 0);
+      x1 = min(x1, Gx - 1);
+      if (x0 > x1) continue;
+    } else if (x0 < 0 || x1 >= Gx) {
+      // the run crosses the cyclic x boundary: the wrapped part first
+      const int wa = x0 < 0 ? x0 + Gx : 0;
+      const int wb = x0 < 0 ? Gx - 1 : x1 - Gx;
+      Target tw = tg;
+      tw.qx = Q.q.x + (x0 < 0 ? g.Lx : -g.Lx);
+      tw.wrapped = true;
+      visit(tw, full, __ldg(g.cell_start + row + wa), __ldg(g.cell_start + row + wb + 1));
+      x0 = max(x0, 0);
+      x1 = min(x1, Gx - 1);
+    }
+    visit(tg, full, __ldg(g.cell_start + row + x0), __ldg(g.cell_start + row + x1 + 1));
   }
 }
+
+// Adapter: a visitor that loads its cell range itself, for the prefetching walk.
+template <class V>
+struct RangeAdapter {
+  V &v;
+  __device__ __forceinline__ void operator()(const Target &t, bool full, int, int) { v(t, full); }
+};
 
 template <class V>
 __device__ __forceinline__ void walk_classes(const GridDev &g, const QueryGeom &Q, V &visit) {
