@@ -154,11 +154,19 @@ class RadiusWork:
 
     def heavy_split(self, k):
         """(fraction of queries, fraction of hits) served by the cell-at-a-time
-        kernels for scene k: queries whose cell holds >= 8 points."""
+        kernels for scene k: queries whose cell holds >= 8 points, or >= 3 with
+        >= 12 points in it and its two x-neighbors (keys key-1..key+1)."""
         start, _, perm = (t.cpu().numpy() for t in self.grids[k].cell_arrays())
         cnt = np.diff(start)
         cnt[-1] = 0                      # the outside cell is never a heavy cell
-        heavy_slot = np.repeat(cnt >= 8, cnt.clip(min=0))[: len(perm)]
+        nc = len(cnt) - 1                # lattice cells; key nc is the outside cell
+        row = np.zeros(len(cnt), dtype=np.int64)
+        if nc >= 3:
+            key = np.arange(1, nc - 1)
+            row[1:nc - 1] = start[key + 2] - start[key - 1]
+        heavy = (cnt >= 8) | ((cnt >= 3) & (row >= 12))
+        heavy[-1] = False
+        heavy_slot = np.repeat(heavy, cnt.clip(min=0))[: len(perm)]
         if self.method == "cube":
             heavy_slot[:] = False
         off = self.off[k].cpu().numpy()

@@ -1,7 +1,7 @@
 // Radius query for heavily loaded cells (Sec. I: with many objects per cell
 // the cost of processing cells dominates, so it pays to share that work).
 //
-// One block per query cell holding at least kHeavyMin points, in a single
+// One block per heavy query cell (heavy_cell), in a single
 // pass that runs before the prefix sum of the list lengths:
 //  1. the cell-level sphere: every table entry whose minimum cell-to-cell
 //     bound satisfies b^2 <= floor(d^2) (Sec. II.A) is translated to the query
@@ -84,6 +84,27 @@ __device__ __forceinline__ int block_excl_scan_i(int v, int &total, int *scan) {
   const int before = wid > 0 ? scan[wid - 1] : 0;
   __syncthreads();
   return before + inc - v;
+}
+
+// Packed FP32 pairs (low half = first value) and the squared distance of
+// two candidates to one query with f32x2 instructions.
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+  return ((unsigned long long)__float_as_uint(b) << 32) | (unsigned long long)__float_as_uint(a);
+}
+__device__ __forceinline__ float lo_half(unsigned long long v) { return __uint_as_float((unsigned)v); }
+__device__ __forceinline__ float hi_half(unsigned long long v) { return __uint_as_float((unsigned)(v >> 32)); }
+
+__device__ __forceinline__ unsigned long long dist2_x2(unsigned long long X, unsigned long long Y,
+                                                       unsigned long long Z, const float4 &q) {
+  const unsigned long long qx = pack2(q.x, q.x), qy = pack2(q.y, q.y), qz = pack2(q.z, q.z);
+  unsigned long long dx, dy, dz, d2;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(X), "l"(qx));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(Y), "l"(qy));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(Z), "l"(qz));
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d2) : "l"(dx), "l"(dx));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d2) : "l"(dy), "l"(dy), "l"(d2));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d2) : "l"(dz), "l"(dz), "l"(d2));
+  return d2;
 }
 
 __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams P, Band B, unsigned flags,
@@ -305,36 +326,57 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
       }
     }
     __syncthreads();
-    // 4. tests: items (chunk of 32 candidates, group of queries) over all warps
+    // 4. tests.  Items (two chunks of 32 candidates, group of queries) are
+    //    spread over all warps; a lane holds candidates k and k + 32 and runs
+    //    both distances at once with packed FP32x2 arithmetic (the same
+    //    round-to-nearest operations, in the same order, as the scalar path).
     const int nchunk = (nc + 31) >> 5;
+    const int npair = (nchunk + 1) >> 1;
     const int qbatch = max(1, min(nq, kCellMaskCap / max(nchunk, 1)));
     for (int qb = 0; qb < nq; qb += qbatch) {
       const int nqb = min(qbatch, nq - qb);
-      const int qsz = max(1, min(nqb, (nqb * nchunk + 2 * nw - 1) / (2 * nw)));
+      const int qsz = max(1, min(nqb, (nqb * npair + 2 * nw - 1) / (2 * nw)));
       const int ngrp = (nqb + qsz - 1) / qsz;
-      const int nitems = nchunk * ngrp;
+      const int nitems = npair * ngrp;
       for (int it = wid; it < nitems; it += nw) {
-        const int grp = it / nchunk;
-        const int ch = it - grp * nchunk;
-        const int k = ch * 32 + lane;
-        float4 c = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-        if (k < nc) c = S.c[k];
-        const int j = __float_as_int(c.w);
+        const int grp = it / npair;
+        const int cp = it - grp * npair;
+        const int k0 = cp * 64 + lane, k1 = k0 + 32;
+        const float4 c0 = k0 < nc ? S.c[k0] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+        const float4 c1 = k1 < nc ? S.c[k1] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+        const unsigned long long X = pack2(c0.x, c1.x), Y = pack2(c0.y, c1.y), Z = pack2(c0.z, c1.z);
+        const int ch0 = 2 * cp, ch1 = 2 * cp + 1;
         const int q_end = min(nqb, (grp + 1) * qsz);
         for (int ql = grp * qsz; ql < q_end; ++ql) {
           const float4 q = S.q[qb + ql];
-          const float dx = c.x - q.x, dy = c.y - q.y, dz = c.z - q.z;
-          const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-          bool hit = d2 <= B.lo_w;
-          if (!hit && !(d2 > B.hi_w) && k < nc) hit = canon_d2(q, g.spos[j], g) <= B.r2;
-          if (!incl_self) hit = hit && j != qs + qb + ql;
-          const unsigned m = __ballot_sync(0xffffffffu, hit);
-          if (lane == 0) S.u.mask[ql * nchunk + ch] = m;
+          const unsigned long long D2 = dist2_x2(X, Y, Z, q);
+          const float d0 = lo_half(D2), d1 = hi_half(D2);
+          bool h0 = d0 <= B.lo_w, h1 = d1 <= B.lo_w;
+          if (!h0 && !(d0 > B.hi_w) && k0 < nc) h0 = canon_d2(q, g.spos[__float_as_int(c0.w)], g) <= B.r2;
+          if (!h1 && !(d1 > B.hi_w) && k1 < nc) h1 = canon_d2(q, g.spos[__float_as_int(c1.w)], g) <= B.r2;
+          const unsigned m0 = __ballot_sync(0xffffffffu, h0);
+          const unsigned m1 = __ballot_sync(0xffffffffu, h1);
+          if (lane == 0) {
+            S.u.mask[ql * nchunk + ch0] = m0;
+            if (ch1 < nchunk) S.u.mask[ql * nchunk + ch1] = m1;
+          }
         }
       }
       __syncthreads();
-      // 5. counts, one scratch region for the batch, lists stored ascending
+      // 5. the query's own bit cleared (it is always a candidate and a hit),
+      //    counts, one scratch region for the batch, lists stored ascending
       for (int ql = wid; ql < nqb; ql += nw) {
+        if (!incl_self && lane == 0) {
+          const int id = __ldg(g.perm + qs + qb + ql);
+          int lo = 0, hi = nc - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (cid[mid] < id) lo = mid + 1;
+            else hi = mid;
+          }
+          S.u.mask[ql * nchunk + (lo >> 5)] &= ~(1u << (lo & 31));
+        }
+        __syncwarp();
         int cnt = 0;
         for (int c0 = 0; c0 < nchunk; c0 += 32) {
           const int ch = c0 + lane;

@@ -215,6 +215,36 @@ bool build_tables(const int w[3], unsigned cyc, int n_max, HostTables &out, std:
       out.tab_end[n] = (int)i;
     }
   }
+  // x-rows of the sphere for the K-nearest walk: every (oy, oz) whose y-z
+  // minimum bound is within n_max, center to edge
+  {
+    struct RowRaw {
+      int b2, oy, oz;
+    };
+    std::vector<RowRaw> rr;
+    for (int oz = -lim[2]; oz <= lim[2]; ++oz)
+      for (int oy = -lim[1]; oy <= lim[1]; ++oy) {
+        const int by = std::max(std::abs(oy) - 1, 0), bz = std::max(std::abs(oz) - 1, 0);
+        if (by * by + bz * bz <= n_max) rr.push_back({by * by + bz * bz, oy, oz});
+      }
+    std::stable_sort(rr.begin(), rr.end(), [](const RowRaw &a, const RowRaw &b) { return a.b2 < b.b2; });
+    out.rows.clear();
+    for (const RowRaw &r : rr) {
+      RowEntry e;
+      unsigned long long u = 0;
+      const int o[3] = {0, r.oy, r.oz};
+      for (int a = 1; a < 3; ++a) {
+        const unsigned long long fieldmask = (1ull << (w[a] + 1)) - 1ull;
+        u |= ((unsigned long long)(long long)o[a] & fieldmask) << pos[a];
+      }
+      e.unp = u;
+      e.oy = (short)r.oy;
+      e.oz = (short)r.oz;
+      e.b2 = r.b2;
+      out.rows.push_back(e);
+    }
+    out.row_lim_x = lim[0];
+  }
   // Specialized tables: for shell fl (fl^2 <= b2 < (fl+1)^2) and the 6-bit
   // mask of directions where f < zeta, drop every non-center offset whose
   // directions all have their bit set (Eq. 2: then t > d).
@@ -263,6 +293,9 @@ si_status upload_tables(const HostTables &h, DevTables &d) {
   if ((s = upload(h.spec, d.spec)) != SI_OK) return s;
   if ((s = upload(h.spec_begin, d.spec_begin)) != SI_OK) return s;
   if ((s = upload(h.spec_end, d.spec_end)) != SI_OK) return s;
+  if ((s = upload(h.rows, d.rows)) != SI_OK) return s;
+  d.n_rows = (int)h.rows.size();
+  d.row_lim_x = h.row_lim_x;
   d.n_max = h.n_max;
   d.spec_shells = h.spec_shells;
   d.entries = (int64_t)h.tab.size();
@@ -275,6 +308,7 @@ void free_tables(DevTables &d) {
   cudaFree(d.spec);
   cudaFree(d.spec_begin);
   cudaFree(d.spec_end);
+  cudaFree(d.rows);
   d = DevTables();
 }
 
@@ -315,6 +349,9 @@ void fill_griddev(const Lattice &lat, const DevTables &t, GridDev &g) {
   g.cls = nullptr;
   g.cls_begin = nullptr;
   g.cls_q = 0;
+  g.rows = t.rows;
+  g.n_rows = t.n_rows;
+  g.row_lim_x = t.row_lim_x;
 }
 
 // ---------------------------------------------------------------------------
@@ -393,9 +430,8 @@ __global__ void __launch_bounds__(256) k_bin_key(const float4 *__restrict__ pos,
   key_slot[i] = make_uint2(key, (unsigned)slot);
 }
 
-// Scatter into cell order; the first point of every cell holding at least
-// kHeavyMinBuild points (outside cell excepted) lists that cell for the
-// cell-at-a-time query kernels.
+// Scatter into cell order; the first point of every heavy cell (heavy_cell)
+// lists that cell for the cell-at-a-time query kernels.
 __global__ void __launch_bounds__(256) k_bin_scatter(const float4 *__restrict__ pos, int n,
                                                      const uint2 *__restrict__ key_slot,
                                                      const int *__restrict__ start,
@@ -409,7 +445,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const float4 *__restrict__ 
   const int dst = b + (int)ks.y;
   spos[dst] = __ldg(pos + i);
   perm[dst] = i;
-  if (ks.y == 0u && ks.x != outside && __ldg(start + ks.x + 1) - b >= kHeavyMinBuild) {
+  if (ks.y == 0u && heavy_cell(start, ks.x, outside)) {
     const int slot = atomicAdd(heavy, 1);
     heavy[1 + slot] = (int)ks.x;
   }
@@ -613,7 +649,7 @@ extern "C" si_status si_grid_create(const si_grid_desc *desc, int64_t n_capacity
   SI_ALLOC(g->status, sizeof(int));
   SI_ALLOC(g->longq, (cap1 + 1) * sizeof(int));
   SI_ALLOC(g->hugeq, (cap1 + 1) * sizeof(int));
-  SI_ALLOC(g->heavy, (cap1 / kHeavyMinBuild + 2) * sizeof(int));
+  SI_ALLOC(g->heavy, (cap1 / kHeavyMinDense + 2) * sizeof(int));
   SI_ALLOC(g->over, (cap1 + 1) * sizeof(int));
   SI_ALLOC(g->scr_off, cap1 * sizeof(long long));
   SI_ALLOC(g->scr_top, sizeof(unsigned long long));

@@ -15,7 +15,6 @@ namespace si {
 constexpr int kCounterInts = 8;
 constexpr long long kClassCapMax = 1ll << 22;   // class-table entries a grid may hold
 constexpr size_t kClassSmemMax = 48 * 1024;      // class tables staged in shared memory up to this
-constexpr int kHeavyMinBuild = 8;   // must equal kHeavyMin of the radius kernels
 
 // Record a message for si_last_error() (per host thread) and return `s`.
 si_status fail(si_status s, const std::string &msg);
@@ -58,6 +57,8 @@ struct HostTables {
   std::vector<int> spec_end;       // 64 * spec_shells^2
   int n_max = 0;
   int spec_shells = 0;
+  std::vector<RowEntry> rows;      // x-rows of the sphere, by b2 of their y-z offset
+  int row_lim_x = 0;
 };
 
 // Largest shell with specialized tables: 64 copies of a shell cost memory
@@ -76,7 +77,8 @@ struct DevTables {
   TabEntry *spec = nullptr;
   int *spec_begin = nullptr;
   int *spec_end = nullptr;
-  int n_max = 0, spec_shells = 0;
+  RowEntry *rows = nullptr;
+  int n_max = 0, spec_shells = 0, n_rows = 0, row_lim_x = 0;
   int64_t entries = 0;
 };
 si_status upload_tables(const HostTables &h, DevTables &d);

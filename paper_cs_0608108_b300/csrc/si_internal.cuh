@@ -27,6 +27,15 @@ struct __align__(16) TabEntry {
 };
 static_assert(sizeof(TabEntry) == 16, "table entry must be 16 bytes");
 
+// One x-row of the sphere's cells (for the K-nearest walk): the row's (0, oy,
+// oz) offset in unpacked form and its minimum-bound squared y-z distance.
+struct __align__(16) RowEntry {
+  unsigned long long unp;
+  short oy, oz;
+  int b2;
+};
+static_assert(sizeof(RowEntry) == 16, "row entry must be 16 bytes");
+
 // Everything a query kernel needs, passed by value (kernel parameter space).
 struct GridDev {
   const float4 *spos;        // sorted positions (cell order)
@@ -57,9 +66,30 @@ struct GridDev {
   const unsigned long long *cls;   // entries: unpacked offset | bit 63 = whole cell inside
   const int *cls_begin;            // q^3 + 1
   int cls_q;                       // 0: no class tables
+  const RowEntry *rows;            // x-rows sorted by b2 (K-nearest walk)
+  int n_rows;
+  int row_lim_x;                   // |ox| bound of the rows' x extent
 };
 
 enum : int { ST_INVALID = 1, ST_CAPACITY = 2, ST_INTERNAL = 4, ST_TIMEOUT = 8 };
+
+// Heavy cells take the cell-at-a-time radius kernel: at least kHeavyMin
+// points, or at least kHeavyMinDense points in a dense x-row (the cell and
+// its two x neighbours hold kHeavyRowDense or more), where sharing one walk
+// pays even for few queries.  The binning lists them and the per-query
+// kernels skip their queries with this same predicate; either path gives
+// the same lists.
+constexpr int kHeavyMin = 8;
+constexpr int kHeavyMinDense = 3;
+constexpr int kHeavyRowDense = 12;
+
+__device__ __forceinline__ bool heavy_cell(const int *start, unsigned key, unsigned outside) {
+  if (key >= outside) return false;
+  const int m = __ldg(start + key + 1) - __ldg(start + key);
+  if (m >= kHeavyMin) return true;
+  if (m < kHeavyMinDense || key < 1u || key + 2u > outside) return false;
+  return __ldg(start + key + 2) - __ldg(start + key - 1) >= kHeavyRowDense;
+}
 
 // ---------------------------------------------------------------------------
 // Cell of one coordinate (Sec. II.B: power-of-two lattice; Sec. II.B last

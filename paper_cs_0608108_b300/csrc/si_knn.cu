@@ -129,43 +129,62 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(GridDev g, int K, float dma
   };
 
   if (!Q.outside) {
+    // Center to edge over x-rows (y-z minimum bound b2 ascending).  For each
+    // row the exact y-z distance of the query and the current cut give the
+    // x-interval of cells that can still hold a closer point: one contiguous
+    // range of sorted points (consecutive x cells are consecutive packed
+    // indices, Sec. II.B).  The walk ends at the first row whose bound
+    // exceeds the cut (early cut-off, Sec. II.A).
     bool out_seen = false;
-    const int te = __ldg(g.tab_end + n_query);
-    constexpr int kG = 4;
-    for (int i0 = 0; i0 < te; i0 += kG) {
-      if ((float)__ldg(&g.tab[i0].b2) > cut2) break;          // early cut-off (Sec. II.A)
-      Target tg[kG];
-      float t2[kG];
-      int cb[kG], ce[kG];
-      bool ok[kG];
-#pragma unroll
-      for (int r = 0; r < kG; ++r) {
-        ok[r] = false;
-        t2[r] = 0.f;
-        if (i0 + r < te) {
-          const TabEntry e = g.tab[i0 + r];
-          t2[r] = cell_t2(e, Q);                               // exact cell test (Eq. 1)
-          ok[r] = (float)e.b2 <= cut2 && t2[r] <= cut2;
-          if (ok[r]) {
-            tg[r] = translate(e, Q, g);
-            if (tg[r].outside && out_seen) ok[r] = false;
-          }
-        }
+    const int Gx = 1 << g.wx;
+    const bool cyc_x = g.cyc & 1u;
+    auto outside = [&]() {
+      if (out_seen) return;
+      out_seen = true;
+      Target t;
+      t.key = g.outside;
+      t.outside = true;
+      t.wrapped = false;
+      t.qx = Q.q.x;
+      t.qy = Q.q.y;
+      t.qz = Q.q.z;
+      cell(t, __ldg(g.cell_start + g.outside), __ldg(g.cell_start + g.outside + 1));
+    };
+    for (int r = 0; r < g.n_rows; ++r) {
+      const RowEntry R = g.rows[r];
+      if ((float)R.b2 > cut2) break;
+      if (R.b2 > n_query) break;
+      const float ty = R.oy > 0 ? (float)(R.oy - 1) + Q.zp[1] : (R.oy < 0 ? (float)(-R.oy - 1) + Q.zn[1] : 0.f);
+      const float tz = R.oz > 0 ? (float)(R.oz - 1) + Q.zp[2] : (R.oz < 0 ? (float)(-R.oz - 1) + Q.zn[2] : 0.f);
+      const float rem = cut2 - fmaf(ty, ty, tz * tz);
+      if (rem < 0.f) continue;
+      const float h = sqrtf(rem) + g.eps;
+      const int lo = max((int)floorf(Q.u[0] - h) - Q.c[0], -g.row_lim_x);
+      const int hi = min((int)floorf(Q.u[0] + h) - Q.c[0], g.row_lim_x);
+      if (lo > hi) continue;
+      Target tg = translate_raw(R.unp, Q, g);
+      if (tg.outside) {
+        outside();
+        continue;
       }
-#pragma unroll
-      for (int r = 0; r < kG; ++r) {
-        cb[r] = ok[r] ? __ldg(g.cell_start + tg[r].key) : 0;
-        ce[r] = ok[r] ? __ldg(g.cell_start + tg[r].key + 1) : 0;
+      const unsigned row = tg.key - (unsigned)Q.c[0];
+      int x0 = Q.c[0] + lo, x1 = Q.c[0] + hi;
+      if (!cyc_x) {
+        if (x0 < 0 || x1 >= Gx) outside();
+        x0 = max(x0, 0);
+        x1 = min(x1, Gx - 1);
+        if (x0 > x1) continue;
+      } else if (x0 < 0 || x1 >= Gx) {
+        const int wa = x0 < 0 ? x0 + Gx : 0;
+        const int wb = x0 < 0 ? Gx - 1 : x1 - Gx;
+        Target tw = tg;
+        tw.qx = Q.q.x + (x0 < 0 ? g.Lx : -g.Lx);
+        tw.wrapped = true;
+        cell(tw, __ldg(g.cell_start + row + wa), __ldg(g.cell_start + row + wb + 1));
+        x0 = max(x0, 0);
+        x1 = min(x1, Gx - 1);
       }
-#pragma unroll
-      for (int r = 0; r < kG; ++r) {
-        if (!ok[r] || t2[r] > cut2) continue;                    // cut2 may have shrunk
-        if (tg[r].outside) {                                     // the outside cell: once
-          if (out_seen) continue;
-          out_seen = true;
-        }
-        cell(tg[r], cb[r], ce[r]);
-      }
+      cell(tg, __ldg(g.cell_start + row + x0), __ldg(g.cell_start + row + x1 + 1));
     }
   } else {
     auto v = [&](const Target &tg, bool) {

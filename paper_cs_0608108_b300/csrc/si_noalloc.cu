@@ -47,7 +47,7 @@ constexpr size_t kOffSpos = align256(kOffStart + sizeof(int) * (kNAMaxCells + 1)
 constexpr size_t kOffPerm = align256(kOffSpos + sizeof(float4) * kNAMaxPoints);
 constexpr size_t kOffScan = align256(kOffPerm + sizeof(int) * kNAMaxPoints);
 constexpr size_t kOffHeavy = align256(kOffScan + sizeof(int) * (kNAMaxCells / 4096 + 2));
-constexpr size_t kOffPartial = align256(kOffHeavy + sizeof(int) * (kNAMaxPoints / 8 + 2));
+constexpr size_t kOffPartial = align256(kOffHeavy + sizeof(int) * (kNAMaxPoints / kHeavyMinDense + 2));
 constexpr size_t kOffStatus = align256(kOffPartial + sizeof(double) * kNAMaxBlocks);
 constexpr size_t kNoAllocBytes = align256(kOffStatus + sizeof(int));
 

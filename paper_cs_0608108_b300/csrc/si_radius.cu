@@ -42,7 +42,8 @@ struct WriteVisitor {
   const QueryGeom &Q;
   const Band &B;
   int self;
-  int *out;        // this query's list
+  int *out;        // this query's list (global), or its staging slots (shared)
+  int stride;      // distance between consecutive slots of `out`
   int len;         // its final length
   int k;           // ids written so far
   bool sort_inline;
@@ -51,14 +52,14 @@ struct WriteVisitor {
     if (sort_inline) {
       int p = k;
       while (p > 0) {
-        const int prev = out[p - 1];
+        const int prev = out[(p - 1) * stride];
         if (prev <= id) break;
-        out[p] = prev;
+        out[p * stride] = prev;
         --p;
       }
-      out[p] = id;
+      out[p * stride] = id;
     } else {
-      out[k] = id;
+      out[k * stride] = id;
     }
     ++k;
   }
@@ -83,18 +84,18 @@ __device__ __forceinline__ void walk_one(const GridDev &g, const QueryGeom &Q, c
   else walk_sphere(g, Q, P, v);
 }
 
-// One query by one thread.  heavy_min > 0: queries whose cell holds at least
-// heavy_min points are left to the cell kernel.
+// One query by one thread.  heavy_min > 0: queries of heavy cells
+// (heavy_cell) are left to the cell kernel.
+// stage (nullable): this thread's kInlineSort shared slots, `stride` apart;
+// short lists are sorted there and stored once.
 template <bool WRITE, int WALK>
 __device__ __forceinline__ void radius_one(const GridDev &g, const WalkParams &P, const Band &B,
                                            unsigned flags, int s, int heavy_min, long long *counts,
                                            const long long *offsets, int *ids, long long cap,
-                                           int *longq) {
+                                           int *longq, int *stage = nullptr, int stride = 0) {
   const QueryGeom Q = make_geom(g.spos[s], g);
-  if (heavy_min > 0 && !Q.outside) {
-    const unsigned key = pack3(Q.c[0], Q.c[1], Q.c[2], g);
-    if (__ldg(g.cell_start + key + 1) - __ldg(g.cell_start + key) >= heavy_min) return;
-  }
+  if (heavy_min > 0 && !Q.outside && heavy_cell(g.cell_start, pack3(Q.c[0], Q.c[1], Q.c[2], g), g.outside))
+    return;
   const int self = (flags & SI_INCLUDE_SELF) ? -1 : s;
   const int orig = __ldg(g.perm + s);
   if (!WRITE) {
@@ -110,9 +111,13 @@ __device__ __forceinline__ void radius_one(const GridDev &g, const WalkParams &P
       return;
     }
     const bool sort_all = !(flags & SI_NO_SORT);
-    WriteVisitor v{g, Q, B, self, ids + base, len, 0, sort_all && len <= kInlineSort};
+    const bool inl = sort_all && len <= kInlineSort;
+    const bool staged = inl && stage != nullptr;
+    WriteVisitor v{g, Q, B, self, staged ? stage : ids + base, staged ? stride : 1, len, 0, inl};
     walk_one<WALK>(g, Q, P, v);
     if (v.k != len) atomicOr(g.status, ST_INTERNAL);
+    if (staged)
+      for (int i = 0; i < len; ++i) ids[base + i] = stage[i * stride];
     if (sort_all && len > kInlineSort) {
       const int slot = atomicAdd(longq, 1);
       longq[1 + slot] = orig;
@@ -143,6 +148,8 @@ __global__ void __launch_bounds__(kClassThreads) k_radius_cls(GridDev g, WalkPar
   extern __shared__ __align__(16) unsigned long long cls_smem[];
   const int nbeg = g.cls_q * g.cls_q * g.cls_q + 1;
   int *beg_smem = reinterpret_cast<int *>(cls_smem + n_entries);
+  // write pass: short lists are sorted in shared slots, column-interleaved
+  int *stage = WRITE ? beg_smem + ((nbeg + 3) & ~3) + threadIdx.x : nullptr;
   for (int i = threadIdx.x; i < n_entries; i += blockDim.x) cls_smem[i] = __ldg(g.cls + i);
   for (int i = threadIdx.x; i < nbeg; i += blockDim.x) beg_smem[i] = __ldg(g.cls_begin + i);
   __syncthreads();
@@ -150,7 +157,8 @@ __global__ void __launch_bounds__(kClassThreads) k_radius_cls(GridDev g, WalkPar
   gs.cls = cls_smem;
   gs.cls_begin = beg_smem;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.n; s += gridDim.x * blockDim.x)
-    radius_one<WRITE, kWalkClasses>(gs, P, B, flags, s, heavy_min, counts, offsets, ids, cap, longq);
+    radius_one<WRITE, kWalkClasses>(gs, P, B, flags, s, heavy_min, counts, offsets, ids, cap, longq,
+                                    stage, kClassThreads);
 }
 
 // Queries the cell kernel handed back (listed by sorted slot): per query.
@@ -251,7 +259,10 @@ static si_status launch_light(int walk, const si_grid *gr, const GridDev &dv, co
                k_radius<WRITE, kWalkCube><<<blocks, kQueryThreads, 0, st>>>(dv, P, B, flags, 0, counts,
                                                                             off, ids, cap, longq));
   } else if (walk == kWalkClasses && gr->cls_smem_bytes > 0) {
-    const size_t smem = gr->cls_smem_bytes;
+    const int nbeg = gr->cls_q * gr->cls_q * gr->cls_q + 1;
+    const size_t smem = gr->cls_host.size() * sizeof(unsigned long long) +
+                        (size_t)((nbeg + 3) & ~3) * sizeof(int) +
+                        (WRITE ? (size_t)kInlineSort * kClassThreads * sizeof(int) : 0);
     SI_CUDA_TRY(cudaFuncSetAttribute(k_radius_cls<WRITE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     int per_sm = 0;

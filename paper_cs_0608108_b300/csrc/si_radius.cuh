@@ -10,7 +10,6 @@ namespace si {
 constexpr int kQueryThreads = 128;   // per-query kernels
 constexpr int kClassThreads = 256;   // per-query kernel with shared-memory class tables
 constexpr int kInlineSort = 32;      // lists up to this length are sorted while written
-constexpr int kHeavyMin = kHeavyMinBuild;   // cells with this many points take the cell path
 constexpr int kCellThreads = 512;
 constexpr int kCellCap = 2560;       // staged candidates per query cell
 constexpr int kCellMaxQ = 512;       // queries of one cell in one block
