@@ -188,10 +188,12 @@ class RadiusWork:
                 "k_bin_scatter": 8 * n + 16 * n + 4 * C + 16 * n + 4 * n,
                 "k_radius_count": (1 - fq) * cnt_b,
                 "k_radius_write": (1 - fq) * wr_b + (1 - ft) * 4 * tot,
-                # heavy cells: one pass reads their queries' inputs and writes
-                # their lists (to scratch); the copy reads and writes them again
-                "k_cell": fq * cnt_b + ft * 4 * tot,
-                "k_cell_copy": ft * 8 * tot,
+                # heavy cells: one pass reads their queries' points, ids and
+                # cell starts and writes their counts and scratch references;
+                # the expansion reads offsets and references and writes the
+                # lists (the per-cell records in between are not algorithmic)
+                "k_cell": fq * (16 * n + 4 * n + 4 * C + 16 * n),
+                "k_cell_expand": fq * (4 * n + 16 * n) + ft * 4 * tot,
                 "k_radius_count_cube": cnt_b,
                 "k_radius_write_cube": wr_b + 4 * tot,
             }

@@ -1,26 +1,30 @@
 // Radius query for heavily loaded cells (Sec. I: with many objects per cell
 // the cost of processing cells dominates, so it pays to share that work).
 //
-// One block per heavy query cell (heavy_cell), in a single
-// pass that runs before the prefix sum of the list lengths:
+// One block per heavy query cell (heavy_cell), in a single pass that runs
+// before the prefix sum of the list lengths:
 //  1. the cell-level sphere: every table entry whose minimum cell-to-cell
 //     bound satisfies b^2 <= floor(d^2) (Sec. II.A) is translated to the query
 //     cell (SWAR add/mask/pack, Sec. II.B); non-empty target cells are listed;
 //  2. their points are moved into the query cell's frame (image shift on
 //     wrapped cyclic axes), kept when they lie within d of the query cell box
 //     (the union of the spheres of every point of the cell) and staged in
-//     shared memory;
-//  3. the staged candidates are put in ascending input-index order: one
-//     counting pass into 1024 buckets by the index's top bits, then an
-//     insertion sort inside each (small) bucket;
-//  4. warps take chunks of 32 candidates (lane = candidate) and test them
-//     against every query of the cell: one ballot per (query, chunk);
-//  5. each query's hits are counted, the cell reserves a region of a scratch
-//     buffer with one atomic, and a warp per query stores its hits there,
-//     ascending.  After the prefix sum, k_cell_copy moves every list to its
-//     place in the output.
-// A cell whose candidates or queries do not fit shared memory, or whose lists
-// do not fit the scratch buffer, hands its queries to the per-query path.
+//     shared memory; each kept candidate's input index is counted into one of
+//     1024 buckets by its top bits;
+//  3. the staged candidates are put in ascending input-index order (bucket
+//     scatter, then insertion inside each small bucket) and the ordered ids
+//     are stored to the cell's record in a scratch buffer, reserved with one
+//     atomic as soon as the number of candidates is known;
+//  4. warps take (group of queries, 64 candidates) items: a lane holds two
+//     candidates, tests them against each query of the group (one ballot per
+//     32 candidates) and lane 0 stores the two hit masks to the record and
+//     adds their population counts to the query's count.
+// Record of a cell in the scratch buffer: nc, the nc ordered ids, then one
+// 32-bit mask per (query, 32 candidates), query-major.  After the prefix sum,
+// k_cell_expand turns every query's masks into its ids at their place in the
+// output.  A cell whose candidates or queries do not fit shared memory, or
+// whose record does not fit the scratch buffer, hands its queries to the
+// per-query path.
 #include <cmath>
 
 #include "si_host.h"
@@ -30,61 +34,30 @@
 namespace si {
 
 constexpr int kBuckets = 1024;
+constexpr int kQlBits = 9;   // query index inside its cell in a scratch reference
+static_assert(kCellMaxQ <= (1 << kQlBits), "query index field too narrow");
 
 struct CellSmem {
-  float4 c[kCellCap];                      // candidate in the query frame; x = NaN: outside cell; w = slot bits
-  unsigned long long key[2 * kCellCap];    // sort buffers: (input index << 32) | staging slot
-  union {
-    struct {                               // gather: the cell-level sphere's target cells
-      unsigned tkey[kCellTCap];
-      int tbeg[kCellTCap];
-      int tcnt[kCellTCap];
-      int tpre[kCellTCap + 1];
-      unsigned char tcode[kCellTCap];
-    } t;
-    struct {                               // bucket sort
-      int start[kBuckets];
-      int cur[kBuckets];
-    } b;
-    unsigned mask[kCellMaskCap];           // tests: ballot of each (query, chunk)
-  } u;
-  float4 q[kCellMaxQ];                     // the cell's query points
-  int qcnt[kCellMaxQ];                     // hits per query of the current batch
-  int qoff[kCellMaxQ];                     // their offsets inside the batch's scratch region
+  float4 c[kCellCap];                      // candidate in the query frame; x = NaN: outside cell; w = spos slot
+  unsigned long long key[kCellCap];        // (input index << 32) | staging slot, in bucket order
+  int sid[kCellCap];                       // input index of each staged candidate
+  int bstart[kBuckets];                    // bucket counts, then starts
+  int bcur[kBuckets];                      // bucket fill pointers
+  struct {                                 // gather: the cell-level sphere's target cells
+    unsigned tkey[kCellTCap];
+    int tbeg[kCellTCap];
+    int tcnt[kCellTCap];
+    int tpre[kCellTCap + 1];
+    unsigned char tcode[kCellTCap];
+  } t;
+  float4 q[kCellMaxQ];                     // the cell's query points; w = own position among the candidates
+  int qcnt[kCellMaxQ];                     // hits per query
   int scan[kCellThreads / 32];
-  long long base;                          // the batch's scratch region
+  long long base;                          // the cell's record in the scratch buffer (-1: no room)
   int nt, nc, out_seen, item;
 };
 
 size_t cell_smem_bytes() { return sizeof(CellSmem); }
-
-__device__ __forceinline__ int warp_incl_scan_i(int v) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += t;
-  }
-  return v;
-}
-
-// Exclusive block scan of one int per thread; returns the block total.
-__device__ __forceinline__ int block_excl_scan_i(int v, int &total, int *scan) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int inc = warp_incl_scan_i(v);
-  if (lane == 31) scan[wid] = inc;
-  __syncthreads();
-  if (wid == 0) {
-    const int x = lane < nw ? scan[lane] : 0;
-    const int y = warp_incl_scan_i(x);
-    if (lane < nw) scan[lane] = y;
-  }
-  __syncthreads();
-  total = scan[nw - 1];
-  const int before = wid > 0 ? scan[wid - 1] : 0;
-  __syncthreads();
-  return before + inc - v;
-}
 
 // Packed FP32 pairs (low half = first value) and the squared distance of
 // two candidates to one query with f32x2 instructions.
@@ -106,6 +79,9 @@ __device__ __forceinline__ unsigned long long dist2_x2(unsigned long long X, uns
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d2) : "l"(dz), "l"(dz), "l"(d2));
   return d2;
 }
+
+// Scratch reference of a heavy query: its cell's record and its index there.
+__device__ __forceinline__ long long cell_ref(long long rec, int ql) { return (rec << kQlBits) | ql; }
 
 __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams P, Band B, unsigned flags,
                                                           const int *__restrict__ heavy, int *work,
@@ -143,8 +119,14 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
       S.nc = 0;
       S.out_seen = 0;
     }
-    __syncthreads();
+    for (int b = tid; b < kBuckets; b += blockDim.x) S.bstart[b] = 0;
     bool fits = nq <= kCellMaxQ && n_tab <= kCellTCap;
+    if (fits)
+      for (int i = tid; i < nq; i += blockDim.x) {
+        S.q[i] = g.spos[qs + i];
+        S.qcnt[i] = 0;
+      }
+    __syncthreads();
     if (fits) {
       // 1. non-empty target cells of the cell-level sphere
       for (int e = tid; e < n_tab; e += blockDim.x) {
@@ -164,10 +146,10 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
         const int b = __ldg(g.cell_start + tk), c = __ldg(g.cell_start + tk + 1) - b;
         if (c == 0) continue;
         const int t = atomicAdd(&S.nt, 1);
-        S.u.t.tkey[t] = tk;
-        S.u.t.tbeg[t] = b;
-        S.u.t.tcnt[t] = c;
-        S.u.t.tcode[t] = (unsigned char)code;
+        S.t.tkey[t] = tk;
+        S.t.tbeg[t] = b;
+        S.t.tcnt[t] = c;
+        S.t.tcode[t] = (unsigned char)code;
       }
       __syncthreads();
       const int nt = S.nt;
@@ -176,19 +158,20 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
         int run = 0;
         for (int b0 = 0; b0 < nt; b0 += 32) {
           const int t = b0 + lane;
-          const int v = t < nt ? S.u.t.tcnt[t] : 0;
+          const int v = t < nt ? S.t.tcnt[t] : 0;
           const int inc = warp_incl_scan_i(v);
-          if (t < nt) S.u.t.tpre[t] = run + inc - v;
+          if (t < nt) S.t.tpre[t] = run + inc - v;
           run += __shfl_sync(0xffffffffu, inc, 31);
         }
-        if (lane == 0) S.u.t.tpre[nt] = run;
+        if (lane == 0) S.t.tpre[nt] = run;
       }
       __syncthreads();
-      const int ntot = S.u.t.tpre[nt];
-      // 2b. gather: candidates within d of the query cell box, in the query frame
+      const int ntot = S.t.tpre[nt];
+      // 2b. gather: candidates within d of the query cell box, in the query
+      //     frame, with their input indices counted into buckets
       constexpr int kGather = 4;
       for (int base = 0; base < ntot; base += kGather * blockDim.x) {
-        int cj[kGather], tt[kGather];
+        int cj[kGather], tt[kGather], pid[kGather];
         float4 p[kGather];
 #pragma unroll
         for (int r = 0; r < kGather; ++r) {
@@ -199,20 +182,23 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
             int lo = 0, hi = nt - 1;
             while (lo < hi) {
               const int mid = (lo + hi + 1) >> 1;
-              if (S.u.t.tpre[mid] <= f) lo = mid;
+              if (S.t.tpre[mid] <= f) lo = mid;
               else hi = mid - 1;
             }
             tt[r] = lo;
-            cj[r] = S.u.t.tbeg[lo] + (f - S.u.t.tpre[lo]);
+            cj[r] = S.t.tbeg[lo] + (f - S.t.tpre[lo]);
           }
         }
 #pragma unroll
-        for (int r = 0; r < kGather; ++r) p[r] = cj[r] >= 0 ? g.spos[cj[r]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int r = 0; r < kGather; ++r) {
+          p[r] = cj[r] >= 0 ? g.spos[cj[r]] : make_float4(0.f, 0.f, 0.f, 0.f);
+          pid[r] = cj[r] >= 0 ? __ldg(g.perm + cj[r]) : 0;
+        }
 #pragma unroll
         for (int r = 0; r < kGather; ++r) {
           bool keep = false;
           if (cj[r] >= 0) {
-            const unsigned code = S.u.t.tcode[tt[r]];
+            const unsigned code = S.t.tcode[tt[r]];
             if (code & 64u) {
               p[r].x = __int_as_float(0x7fc00000);   // outside cell: FP64 test for every pair
               keep = true;
@@ -239,13 +225,42 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
               float4 cp = p[r];
               cp.w = __int_as_float(cj[r]);
               S.c[at] = cp;
-              S.key[at] = ((unsigned long long)(unsigned)__ldg(g.perm + cj[r]) << 32) | (unsigned)at;
+              S.sid[at] = pid[r];
+              atomicAdd(&S.bstart[pid[r] >> bshift], 1);
             }
           }
         }
       }
       __syncthreads();
       fits = S.nc <= kCellCap;
+    }
+    const int nc = fits ? S.nc : 0;
+    const int nchunk = (nc + 31) >> 5;
+    // the cell's record: nc, ids, masks
+    if (fits && tid == 0) {
+      const long long need = 1 + (long long)nc + (long long)nq * nchunk;
+      const unsigned long long b = atomicAdd(scr_top, (unsigned long long)need);
+      S.base = (b + (unsigned long long)need <= (unsigned long long)scr_cap) ? (long long)b : -1ll;
+    }
+    if (fits) {
+      // 3. ascending input index: scan of the bucket counts, scatter, then
+      //    each bucket (a handful of keys) sorted by insertion
+      constexpr int kPerB = kBuckets / kCellThreads;
+      int v[kPerB], sum = 0;
+#pragma unroll
+      for (int r = 0; r < kPerB; ++r) {
+        v[r] = S.bstart[tid * kPerB + r];
+        sum += v[r];
+      }
+      int total;
+      int run = block_excl_scan_i(sum, total, S.scan);   // its barriers also publish S.base
+#pragma unroll
+      for (int r = 0; r < kPerB; ++r) {
+        S.bstart[tid * kPerB + r] = run;
+        S.bcur[tid * kPerB + r] = run;
+        run += v[r];
+      }
+      fits = S.base >= 0;
     }
     if (!fits) {
       // the per-query path takes every query of this cell
@@ -257,208 +272,181 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
       __syncthreads();
       continue;
     }
-    const int nc = S.nc;
-    for (int i = tid; i < nq; i += blockDim.x) S.q[i] = g.spos[qs + i];
-    // 3. ascending input index: counting pass into buckets, then each bucket
-    //    (a handful of keys) sorted by insertion
-    unsigned long long *src = S.key, *dst = S.key + kCellCap;
-    for (int b = tid; b < kBuckets; b += blockDim.x) S.u.b.start[b] = 0;
-    __syncthreads();
-    for (int p = tid; p < nc; p += blockDim.x) atomicAdd(&S.u.b.start[(int)(src[p] >> 32) >> bshift], 1);
-    __syncthreads();
-    {
-      constexpr int kPerB = kBuckets / kCellThreads;
-      int v[kPerB], sum = 0;
-#pragma unroll
-      for (int r = 0; r < kPerB; ++r) {
-        v[r] = S.u.b.start[tid * kPerB + r];
-        sum += v[r];
-      }
-      int total;
-      int run = block_excl_scan_i(sum, total, S.scan);
-#pragma unroll
-      for (int r = 0; r < kPerB; ++r) {
-        S.u.b.start[tid * kPerB + r] = run;
-        S.u.b.cur[tid * kPerB + r] = run;
-        run += v[r];
-      }
-    }
     __syncthreads();
     for (int p = tid; p < nc; p += blockDim.x) {
-      const unsigned long long x = src[p];
-      dst[atomicAdd(&S.u.b.cur[(int)(x >> 32) >> bshift], 1)] = x;
+      const int id = S.sid[p];
+      S.key[atomicAdd(&S.bcur[id >> bshift], 1)] = ((unsigned long long)(unsigned)id << 32) | (unsigned)p;
     }
     __syncthreads();
     for (int b = tid; b < kBuckets; b += blockDim.x) {
-      const int lo = S.u.b.start[b], hi = S.u.b.cur[b];
+      const int lo = S.bstart[b], hi = S.bcur[b];
       for (int i = lo + 1; i < hi; ++i) {
-        const unsigned long long x = dst[i];
+        const unsigned long long x = S.key[i];
         int p = i;
-        while (p > lo && dst[p - 1] > x) {
-          dst[p] = dst[p - 1];
+        while (p > lo && S.key[p - 1] > x) {
+          S.key[p] = S.key[p - 1];
           --p;
         }
-        dst[p] = x;
+        S.key[p] = x;
       }
     }
     __syncthreads();
-    // permute the candidates into id order; ids go to the spare buffer
+    // permute the candidates into id order; the ordered ids go to the record,
+    // each query notes its own position
+    const long long rec = S.base;
+    int *rec_ids = scratch + rec + 1;
+    unsigned *rec_masks = reinterpret_cast<unsigned *>(rec_ids + nc);
+    if (tid == 0) scratch[rec] = nc;
     constexpr int kPer = (kCellCap + kCellThreads - 1) / kCellThreads;
     float4 rc[kPer];
-    int rid[kPer];
 #pragma unroll
     for (int r = 0; r < kPer; ++r) {
       const int k = tid + r * kCellThreads;
       if (k < nc) {
-        const unsigned long long kk = dst[k];
+        const unsigned long long kk = S.key[k];
         rc[r] = S.c[(int)(kk & 0xffffffffull)];
-        rid[r] = (int)(kk >> 32);
+        rec_ids[k] = (int)(kk >> 32);
       }
     }
     __syncthreads();
-    int *cid = reinterpret_cast<int *>(src);
 #pragma unroll
     for (int r = 0; r < kPer; ++r) {
       const int k = tid + r * kCellThreads;
       if (k < nc) {
         S.c[k] = rc[r];
-        cid[k] = rid[r];
+        const int ql = __float_as_int(rc[r].w) - qs;
+        if (!incl_self && ql >= 0 && ql < nq) S.q[ql].w = __int_as_float(k);
       }
     }
+    if (incl_self)
+      for (int i = tid; i < nq; i += blockDim.x) S.q[i].w = __int_as_float(-1);
     __syncthreads();
     // 4. tests.  Items (two chunks of 32 candidates, group of queries) are
     //    spread over all warps; a lane holds candidates k and k + 32 and runs
     //    both distances at once with packed FP32x2 arithmetic (the same
     //    round-to-nearest operations, in the same order, as the scalar path).
-    const int nchunk = (nc + 31) >> 5;
+    //    A query's own position is never a hit.
     const int npair = (nchunk + 1) >> 1;
-    const int qbatch = max(1, min(nq, kCellMaskCap / max(nchunk, 1)));
-    for (int qb = 0; qb < nq; qb += qbatch) {
-      const int nqb = min(qbatch, nq - qb);
-      const int qsz = max(1, min(nqb, (nqb * npair + 2 * nw - 1) / (2 * nw)));
-      const int ngrp = (nqb + qsz - 1) / qsz;
-      const int nitems = npair * ngrp;
-      for (int it = wid; it < nitems; it += nw) {
-        const int grp = it / npair;
-        const int cp = it - grp * npair;
-        const int k0 = cp * 64 + lane, k1 = k0 + 32;
-        const float4 c0 = k0 < nc ? S.c[k0] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-        const float4 c1 = k1 < nc ? S.c[k1] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-        const unsigned long long X = pack2(c0.x, c1.x), Y = pack2(c0.y, c1.y), Z = pack2(c0.z, c1.z);
-        const int ch0 = 2 * cp, ch1 = 2 * cp + 1;
-        const int q_end = min(nqb, (grp + 1) * qsz);
-        for (int ql = grp * qsz; ql < q_end; ++ql) {
-          const float4 q = S.q[qb + ql];
-          const unsigned long long D2 = dist2_x2(X, Y, Z, q);
-          const float d0 = lo_half(D2), d1 = hi_half(D2);
-          bool h0 = d0 <= B.lo_w, h1 = d1 <= B.lo_w;
-          if (!h0 && !(d0 > B.hi_w) && k0 < nc) h0 = canon_d2(q, g.spos[__float_as_int(c0.w)], g) <= B.r2;
-          if (!h1 && !(d1 > B.hi_w) && k1 < nc) h1 = canon_d2(q, g.spos[__float_as_int(c1.w)], g) <= B.r2;
-          const unsigned m0 = __ballot_sync(0xffffffffu, h0);
-          const unsigned m1 = __ballot_sync(0xffffffffu, h1);
-          if (lane == 0) {
-            S.u.mask[ql * nchunk + ch0] = m0;
-            if (ch1 < nchunk) S.u.mask[ql * nchunk + ch1] = m1;
-          }
-        }
-      }
-      __syncthreads();
-      // 5. the query's own bit cleared (it is always a candidate and a hit),
-      //    counts, one scratch region for the batch, lists stored ascending
-      for (int ql = wid; ql < nqb; ql += nw) {
-        if (!incl_self && lane == 0) {
-          const int id = __ldg(g.perm + qs + qb + ql);
-          int lo = 0, hi = nc - 1;
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (cid[mid] < id) lo = mid + 1;
-            else hi = mid;
-          }
-          S.u.mask[ql * nchunk + (lo >> 5)] &= ~(1u << (lo & 31));
-        }
-        __syncwarp();
-        int cnt = 0;
-        for (int c0 = 0; c0 < nchunk; c0 += 32) {
-          const int ch = c0 + lane;
-          cnt += ch < nchunk ? __popc(S.u.mask[ql * nchunk + ch]) : 0;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        if (lane == 0) S.qcnt[ql] = cnt;
-      }
-      __syncthreads();
-      {
-        const int v = tid < nqb ? S.qcnt[tid] : 0;   // nqb <= kCellMaxQ == blockDim
-        int total;
-        const int ex = block_excl_scan_i(v, total, S.scan);
-        if (tid < nqb) S.qoff[tid] = ex;
-        if (tid == 0) {
-          const unsigned long long b = atomicAdd(scr_top, (unsigned long long)total);
-          S.base = (b + (unsigned long long)total <= (unsigned long long)scr_cap) ? (long long)b : -1ll;
-        }
-      }
-      __syncthreads();
-      const long long sbase = S.base;
-      for (int ql = wid; ql < nqb; ql += nw) {
-        const int s = qs + qb + ql;
-        const int id = __ldg(g.perm + s);
-        if (sbase < 0) {
-          // scratch full: this query goes to the per-query path
-          if (lane == 0) {
-            const int o = atomicAdd(over, 1);
-            over[1 + o] = s;
-            scr_off[id] = -1;
-          }
-          continue;
-        }
-        const long long qbase = sbase + S.qoff[ql];
+    const int qsz = max(1, min(nq, (nq * npair + 2 * nw - 1) / (2 * nw)));
+    const int ngrp = (nq + qsz - 1) / qsz;
+    const int nitems = npair * ngrp;
+    for (int it = wid; it < nitems; it += nw) {
+      const int grp = it / npair;
+      const int cp = it - grp * npair;
+      const int k0 = cp * 64 + lane, k1 = k0 + 32;
+      const float4 c0 = k0 < nc ? S.c[k0] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+      const float4 c1 = k1 < nc ? S.c[k1] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+      const unsigned long long X = pack2(c0.x, c1.x), Y = pack2(c0.y, c1.y), Z = pack2(c0.z, c1.z);
+      const int ch0 = 2 * cp, ch1 = 2 * cp + 1;
+      const int q_end = min(nq, (grp + 1) * qsz);
+      for (int ql = grp * qsz; ql < q_end; ++ql) {
+        const float4 q = S.q[ql];
+        const int own = __float_as_int(q.w);
+        const unsigned long long D2 = dist2_x2(X, Y, Z, q);
+        const float d0 = lo_half(D2), d1 = hi_half(D2);
+        bool h0 = d0 <= B.lo_w, h1 = d1 <= B.lo_w;
+        if (!h0 && !(d0 > B.hi_w) && k0 < nc) h0 = canon_d2(q, g.spos[__float_as_int(c0.w)], g) <= B.r2;
+        if (!h1 && !(d1 > B.hi_w) && k1 < nc) h1 = canon_d2(q, g.spos[__float_as_int(c1.w)], g) <= B.r2;
+        const unsigned m0 = __ballot_sync(0xffffffffu, h0 && k0 != own);
+        const unsigned m1 = __ballot_sync(0xffffffffu, h1 && k1 != own);
         if (lane == 0) {
-          counts[id] = S.qcnt[ql];
-          scr_off[id] = qbase;
-        }
-        long long wpos = qbase;
-        for (int c0 = 0; c0 < nchunk; c0 += 32) {
-          const int ch = c0 + lane;
-          const unsigned mm = ch < nchunk ? S.u.mask[ql * nchunk + ch] : 0u;
-          const int cnt = __popc(mm);
-          const int inc = warp_incl_scan_i(cnt);
-          const int lim = min(32, nchunk - c0);
-          for (int i = 0; i < lim; ++i) {
-            const unsigned mi = __shfl_sync(0xffffffffu, mm, i);
-            const int oi = __shfl_sync(0xffffffffu, inc - cnt, i);
-            if ((mi >> lane) & 1u) scratch[wpos + oi + __popc(mi & lt_mask)] = cid[(c0 + i) * 32 + lane];
-          }
-          wpos += __shfl_sync(0xffffffffu, inc, 31);
+          rec_masks[ql * nchunk + ch0] = m0;
+          if (ch1 < nchunk) rec_masks[ql * nchunk + ch1] = m1;
+          const int c = __popc(m0) + __popc(m1);
+          if (c) atomicAdd(&S.qcnt[ql], c);
         }
       }
-      __syncthreads();
+    }
+    __syncthreads();
+    for (int i = tid; i < nq; i += blockDim.x) {
+      const int id = __ldg(g.perm + qs + i);
+      counts[id] = S.qcnt[i];
+      scr_off[id] = cell_ref(rec, i);
     }
   }
 }
 
-// After the prefix sum: every heavy query's list from the scratch buffer to
-// its place in the output (a warp per query, coalesced both ways).
-__global__ void __launch_bounds__(256) k_cell_copy(GridDev g, const int *__restrict__ heavy,
-                                                   const long long *__restrict__ scr_off,
-                                                   const int *__restrict__ scratch,
-                                                   const long long *__restrict__ offsets, int *ids,
-                                                   long long cap) {
+// After the prefix sum: every heavy query's masks expanded into its ids at
+// their place in the output.  A block per heavy cell: the cell's ordered ids
+// are staged in shared memory (32 per row, rows padded to 33 words so that
+// lanes reading different rows fall in different banks); each warp takes
+// every kExpWarps-th query of the cell.  For 32 masks at a time, lane j takes
+// the j-th, and writes the ids of its set bits, ascending, into the warp's
+// shared buffer after the hits of the masks before it; the warp then stores
+// the buffer to the output with contiguous stores.  Output offsets and mask
+// rows of up to 32 queries are fetched at once, and the next masks are
+// loaded while the current ones are expanded.
+constexpr int kExpWarps = 4;
+constexpr int kExpRows = (kCellCap + 31) / 32;
+
+__global__ void __launch_bounds__(kExpWarps * 32, 8) k_cell_expand(GridDev g, const int *__restrict__ heavy,
+                                                                   const long long *__restrict__ scr_off,
+                                                                   const int *__restrict__ scratch,
+                                                                   const long long *__restrict__ offsets,
+                                                                   int *__restrict__ ids, long long cap) {
+  __shared__ int sids[kExpRows * 33];
+  __shared__ int sbuf[kExpWarps][1024];
   if (offsets[g.n] > cap) {
     if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(g.status, ST_CAPACITY);
     return;
   }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  int *buf = sbuf[wid];
   const int nheavy = heavy[0];
   for (int item = blockIdx.x; item < nheavy; item += gridDim.x) {
     const unsigned key = (unsigned)heavy[1 + item];
     const int qs = __ldg(g.cell_start + key), qe = __ldg(g.cell_start + key + 1);
-    for (int s = qs + w; s < qe; s += nwb) {
-      const int id = __ldg(g.perm + s);
-      const long long src = scr_off[id];
-      if (src < 0) continue;
-      const long long dst = offsets[id];
-      const int len = (int)(offsets[id + 1] - dst);
-      for (int i = lane; i < len; i += 32) ids[dst + i] = scratch[src + i];
+    // every query of a cell has a reference into the same record, or none
+    const long long ref0 = scr_off[__ldg(g.perm + qs)];
+    if (ref0 < 0) continue;   // served by the per-query path (the same for the whole block)
+    const long long rec = ref0 >> kQlBits;
+    const int nc = __ldg(scratch + rec);
+    const int nchunk = (nc + 31) >> 5;
+    const int *rec_ids = scratch + rec + 1;
+    const unsigned *rec_masks = reinterpret_cast<const unsigned *>(rec_ids + nc);
+    __syncthreads();   // the previous cell's ids are no longer read
+    for (int k = tid; k < nc; k += blockDim.x) sids[(k >> 5) * 33 + (k & 31)] = __ldg(rec_ids + k);
+    __syncthreads();
+    const int nmine = (qe - qs - wid + kExpWarps - 1) / kExpWarps;   // this warp's queries
+    for (int i0 = 0; i0 < nmine; i0 += 32) {
+      int qlv = 0;
+      long long dstv = 0;
+      if (i0 + lane < nmine) {
+        const int id = __ldg(g.perm + qs + wid + kExpWarps * (i0 + lane));
+        qlv = (int)(scr_off[id] & ((1 << kQlBits) - 1));
+        dstv = offsets[id];
+      }
+      const int nb = min(32, nmine - i0);
+      int qn = __shfl_sync(0xffffffffu, qlv, 0);
+      unsigned mnext = lane < nchunk ? __ldg(rec_masks + (long long)qn * nchunk + lane) : 0u;
+      for (int j = 0; j < nb; ++j) {
+        const int qj = qn;
+        long long wpos = __shfl_sync(0xffffffffu, dstv, j);
+        if (j + 1 < nb) qn = __shfl_sync(0xffffffffu, qlv, j + 1);
+        for (int c0 = 0; c0 < nchunk; c0 += 32) {
+          unsigned mm = mnext;
+          // prefetch: the rest of this query's masks, else the next query's first 32
+          if (c0 + 32 < nchunk) {
+            const int ch = c0 + 32 + lane;
+            mnext = ch < nchunk ? __ldg(rec_masks + (long long)qj * nchunk + ch) : 0u;
+          } else if (j + 1 < nb) {
+            mnext = lane < nchunk ? __ldg(rec_masks + (long long)qn * nchunk + lane) : 0u;
+          }
+          const int cnt = __popc(mm);
+          const int inc = warp_incl_scan_i(cnt);
+          int o = inc - cnt;
+          const int *row = sids + (c0 + lane) * 33;
+          while (mm) {
+            buf[o++] = row[__ffs(mm) - 1];
+            mm &= mm - 1u;
+          }
+          __syncwarp();
+          const int tot = __shfl_sync(0xffffffffu, inc, 31);
+          for (int i = lane; i < tot; i += 32) ids[wpos + i] = buf[i];
+          __syncwarp();
+          wpos += tot;
+        }
+      }
     }
   }
 }
@@ -474,10 +462,10 @@ si_status launch_cell_pass(const GridDev &g, const WalkParams &P, const Band &B,
   return SI_OK;
 }
 
-si_status launch_cell_copy(const GridDev &g, const int *heavy, const long long *scr_off, const int *scratch,
-                           const long long *offsets, int *ids, long long cap, cudaStream_t st) {
-  SI_KLAUNCH("k_cell_copy", st,
-             k_cell_copy<<<148 * 8, 256, 0, st>>>(g, heavy, scr_off, scratch, offsets, ids, cap));
+si_status launch_cell_expand(const GridDev &g, const int *heavy, const long long *scr_off, const int *scratch,
+                             const long long *offsets, int *ids, long long cap, cudaStream_t st) {
+  SI_KLAUNCH("k_cell_expand", st,
+             k_cell_expand<<<148 * 8, kExpWarps * 32, 0, st>>>(g, heavy, scr_off, scratch, offsets, ids, cap));
   return SI_OK;
 }
 

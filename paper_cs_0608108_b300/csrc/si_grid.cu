@@ -430,25 +430,18 @@ __global__ void __launch_bounds__(256) k_bin_key(const float4 *__restrict__ pos,
   key_slot[i] = make_uint2(key, (unsigned)slot);
 }
 
-// Scatter into cell order; the first point of every heavy cell (heavy_cell)
-// lists that cell for the cell-at-a-time query kernels.
+// Scatter into cell order (points of a cell in atomic arrival order).
 __global__ void __launch_bounds__(256) k_bin_scatter(const float4 *__restrict__ pos, int n,
                                                      const uint2 *__restrict__ key_slot,
                                                      const int *__restrict__ start,
                                                      float4 *__restrict__ spos,
-                                                     int *__restrict__ perm, unsigned outside,
-                                                     int *__restrict__ heavy) {
+                                                     int *__restrict__ perm) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint2 ks = key_slot[i];
-  const int b = __ldg(start + ks.x);
-  const int dst = b + (int)ks.y;
+  const int dst = __ldg(start + ks.x) + (int)ks.y;
   spos[dst] = __ldg(pos + i);
   perm[dst] = i;
-  if (ks.y == 0u && heavy_cell(start, ks.x, outside)) {
-    const int slot = atomicAdd(heavy, 1);
-    heavy[1 + slot] = (int)ks.x;
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -462,12 +455,44 @@ constexpr int kOrderWarps = 8;
 constexpr int kOrderWarpCap = 2048;  // cells up to this size: one warp, shared memory
 constexpr int kOrderBlockCap = 16384;
 
+// The same pass classifies every non-empty cell (cell_class; one thread per
+// cell, so that the neighbours' cell starts are contiguous loads): heavy
+// cells are listed by key, the query slots of dense cells and of light cells
+// are queued (the light ones a block's worth at a time, in cell order), and
+// every slot gets its cell's class byte.
 __global__ void __launch_bounds__(256) k_cell_order(const int *__restrict__ start, int n_cells,
                                                     const float4 *__restrict__ pos, float4 *spos,
-                                                    int *perm, int *bigq) {
+                                                    int *perm, int *bigq, unsigned char *__restrict__ cell_cls,
+                                                    unsigned char *__restrict__ slot_cls, int *__restrict__ heavy,
+                                                    int *__restrict__ dense, int *__restrict__ light, int wx,
+                                                    int wy, int wz) {
+  __shared__ int scan[8];
+  __shared__ int light_base;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_cells) return;
-  const int b = __ldg(start + c), m = __ldg(start + c + 1) - b;
+  int b = 0, m = 0, k = kCellLight;
+  if (c < n_cells) {
+    b = __ldg(start + c);
+    m = __ldg(start + c + 1) - b;
+  }
+  if (m >= 1) {
+    k = cell_class(start, (unsigned)c, (unsigned)(n_cells - 1), wx, wy, wz);
+    cell_cls[c] = (unsigned char)k;
+    if (m <= kOrderLocal)
+      for (int i = 0; i < m; ++i) slot_cls[b + i] = (unsigned char)k;
+    if (k == kCellHeavy) {
+      const int slot = atomicAdd(heavy, 1);
+      heavy[1 + slot] = c;
+    } else if (k == kCellDense) {
+      const int slot = atomicAdd(dense, m);
+      for (int i = 0; i < m; ++i) dense[1 + slot + i] = b + i;
+    }
+  }
+  const int nl = (m >= 1 && k == kCellLight) ? m : 0;
+  int total;
+  const int ex = block_excl_scan_i(nl, total, scan);
+  if (threadIdx.x == 0) light_base = total > 0 ? atomicAdd(light, total) : 0;
+  __syncthreads();
+  for (int i = 0; i < nl; ++i) light[1 + light_base + ex + i] = b + i;
   if (m < 2) return;
   if (m > kOrderLocal) {
     const int slot = atomicAdd(bigq, 1);
@@ -497,7 +522,8 @@ __global__ void __launch_bounds__(kOrderWarps * 32) k_cell_order_big(const int *
                                                                     const float4 *__restrict__ pos,
                                                                     float4 *spos, int *perm,
                                                                     const int *__restrict__ bigq,
-                                                                    int *hugeq) {
+                                                                    int *hugeq, const unsigned char *cell_cls,
+                                                                    unsigned char *__restrict__ slot_cls) {
   extern __shared__ int obuf[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int *buf = obuf + w * kOrderWarpCap;
@@ -505,6 +531,8 @@ __global__ void __launch_bounds__(kOrderWarps * 32) k_cell_order_big(const int *
   for (int item = blockIdx.x * kOrderWarps + w; item < nq; item += gridDim.x * kOrderWarps) {
     const int c = bigq[1 + item];
     const int b = __ldg(start + c), m = __ldg(start + c + 1) - b;
+    const unsigned char k = cell_cls[c];   // written by k_cell_order
+    for (int i = lane; i < m; i += 32) slot_cls[b + i] = k;
     if (m > kOrderWarpCap) {
       if (lane == 0) {
         const int slot = atomicAdd(hugeq, 1);
@@ -547,16 +575,20 @@ __global__ void __launch_bounds__(512) k_cell_order_huge(const int *__restrict__
 }
 
 si_status order_cells(const int *start, int64_t n_cells, const float4 *pos, float4 *spos, int *perm,
-                      int *bigq, int *hugeq, cudaStream_t st) {
+                      int *bigq, int *hugeq, unsigned char *cell_cls, unsigned char *slot_cls, int *heavy,
+                      int *dense, int *light, const int w[3], cudaStream_t st) {
   SI_CUDA_TRY(cudaMemsetAsync(bigq, 0, sizeof(int), st));
   SI_CUDA_TRY(cudaMemsetAsync(hugeq, 0, sizeof(int), st));
   SI_KLAUNCH("k_cell_order", st,
              k_cell_order<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(start, (int)n_cells, pos, spos,
-                                                                              perm, bigq));
+                                                                              perm, bigq, cell_cls, slot_cls,
+                                                                              heavy, dense, light, w[0], w[1],
+                                                                              w[2]));
   const size_t wsm = (size_t)kOrderWarps * kOrderWarpCap * sizeof(int);
   SI_CUDA_TRY(cudaFuncSetAttribute(k_cell_order_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
   SI_KLAUNCH("k_cell_order_big", st,
-             k_cell_order_big<<<148 * 2, kOrderWarps * 32, wsm, st>>>(start, pos, spos, perm, bigq, hugeq));
+             k_cell_order_big<<<148 * 2, kOrderWarps * 32, wsm, st>>>(start, pos, spos, perm, bigq, hugeq,
+                                                                     cell_cls, slot_cls));
   const size_t bsm = (size_t)kOrderBlockCap * sizeof(int);
   SI_CUDA_TRY(cudaFuncSetAttribute(k_cell_order_huge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
   SI_KLAUNCH("k_cell_order_huge", st,
@@ -574,6 +606,8 @@ si::GridDev si_grid::dev() const {
   g.spos = spos;
   g.perm = perm;
   g.cell_start = cell_start;
+  g.cell_cls = cell_cls;
+  g.slot_cls = slot_cls;
   g.n = (int)n;
   g.status = status;
   g.cls = cls;
@@ -587,6 +621,8 @@ static void grid_free(si_grid *g) {
   cudaFree(g->key_slot);
   cudaFree(g->cell_count);
   cudaFree(g->cell_start);
+  cudaFree(g->cell_cls);
+  cudaFree(g->slot_cls);
   cudaFree(g->spos);
   cudaFree(g->perm);
   cudaFree(g->scan_i32);
@@ -596,6 +632,8 @@ static void grid_free(si_grid *g) {
   cudaFree(g->hugeq);
   cudaFree(g->heavy);
   cudaFree(g->over);
+  cudaFree(g->denseq);
+  cudaFree(g->lightq);
   cudaFree(g->scr_off);
   cudaFree(g->scr_top);
   cudaFree(g->scratch);
@@ -642,6 +680,8 @@ extern "C" si_status si_grid_create(const si_grid_desc *desc, int64_t n_capacity
   SI_ALLOC(g->key_slot, cap1 * sizeof(uint2));
   SI_ALLOC(g->cell_count, g->n_cells * sizeof(int));
   SI_ALLOC(g->cell_start, (g->n_cells + 1) * sizeof(int));
+  SI_ALLOC(g->cell_cls, g->n_cells);
+  SI_ALLOC(g->slot_cls, cap1);
   SI_ALLOC(g->spos, cap1 * sizeof(float4));
   SI_ALLOC(g->perm, cap1 * sizeof(int));
   SI_ALLOC(g->scan_i32, scan_scratch_elems(g->n_cells + 1) * sizeof(int));
@@ -651,6 +691,8 @@ extern "C" si_status si_grid_create(const si_grid_desc *desc, int64_t n_capacity
   SI_ALLOC(g->hugeq, (cap1 + 1) * sizeof(int));
   SI_ALLOC(g->heavy, (cap1 / kHeavyMinDense + 2) * sizeof(int));
   SI_ALLOC(g->over, (cap1 + 1) * sizeof(int));
+  SI_ALLOC(g->denseq, (cap1 + 1) * sizeof(int));
+  SI_ALLOC(g->lightq, (cap1 + 1) * sizeof(int));
   SI_ALLOC(g->scr_off, cap1 * sizeof(long long));
   SI_ALLOC(g->scr_top, sizeof(unsigned long long));
   g->scr_cap = 4 * cap1;
@@ -682,6 +724,8 @@ extern "C" si_status si_grid_create(const si_grid_desc *desc, int64_t n_capacity
   e = cudaMemset(g->status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(g->heavy, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(g->over, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g->denseq, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g->lightq, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(g->cell_start, 0, (g->n_cells + 1) * sizeof(int));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -708,14 +752,16 @@ extern "C" si_status si_grid_build(si_grid *g, const float *d_pos, int64_t n, vo
   // cell_start[0] = 0; cell_start[c + 1] = sum of counts of cells 0..c
   SI_CUDA_TRY(cudaMemsetAsync(g->cell_start, 0, sizeof(int), st));
   SI_CUDA_TRY(cudaMemsetAsync(g->heavy, 0, sizeof(int), st));
+  SI_CUDA_TRY(cudaMemsetAsync(g->denseq, 0, sizeof(int), st));
+  SI_CUDA_TRY(cudaMemsetAsync(g->lightq, 0, sizeof(int), st));
   si_status s = scan_inclusive_i32(g->cell_count, g->cell_start + 1, g->n_cells, g->scan_i32, st);
   if (s != SI_OK) return s;
   if (n > 0) {
     SI_KLAUNCH("k_bin_scatter", st, k_bin_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-        (const float4 *)d_pos, (int)n, g->key_slot, g->cell_start, g->spos, g->perm, 1u << g->lat.W,
-        g->heavy));
+        (const float4 *)d_pos, (int)n, g->key_slot, g->cell_start, g->spos, g->perm));
     // the query kernels are idle during a build: their queues serve as scratch
     s = order_cells(g->cell_start, g->n_cells, (const float4 *)d_pos, g->spos, g->perm, g->longq, g->hugeq,
+                    g->cell_cls, g->slot_cls, g->heavy, g->denseq, g->lightq, g->lat.w,
                     st);
     if (s != SI_OK) return s;
   }

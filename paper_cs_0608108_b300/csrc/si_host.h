@@ -141,8 +141,12 @@ struct si_grid {
   int *hugeq = nullptr;          // cap + 1: lists too long for a warp sort
   int *heavy = nullptr;          // [0] = count, then cells with >= kHeavyMin points (set by build)
   int *over = nullptr;           // [0] = count, then sorted slots of queries the cell kernel handed back
-  long long *scr_off = nullptr;  // per input index: where the cell kernel put its list (-1: not there)
-  int *scratch = nullptr;        // lists written by the cell kernel before the prefix sum
+  int *denseq = nullptr;         // [0] = count, then sorted slots of the queries of dense cells (set by build)
+  int *lightq = nullptr;         // [0] = count, then sorted slots of the queries of light cells (set by build)
+  unsigned char *cell_cls = nullptr;   // per cell: kCellLight / kCellHeavy / kCellDense (set by build)
+  unsigned char *slot_cls = nullptr;   // per sorted slot: its cell's class (set by build)
+  long long *scr_off = nullptr;  // per input index: its cell's record and its index there (-1: per-query path)
+  int *scratch = nullptr;        // cell records (ordered candidate ids, hit masks) written before the prefix sum
   long long scr_cap = 0;
   unsigned long long *scr_top = nullptr;   // bump allocator of the scratch (also the size needed)
   int *counters = nullptr;       // kCounterInts work counters

@@ -41,6 +41,8 @@ struct GridDev {
   const float4 *spos;        // sorted positions (cell order)
   const int *perm;           // sorted slot -> input index
   const int *cell_start;     // n_cells + 1
+  const unsigned char *cell_cls;   // per non-empty cell: kCellLight / kCellHeavy / kCellDense
+  const unsigned char *slot_cls;   // per sorted slot: its cell's class
   int n;
   float ox, oy, oz;          // region origin
   float inv_s;               // 1 / cell side (float32)
@@ -73,6 +75,37 @@ struct GridDev {
 
 enum : int { ST_INVALID = 1, ST_CAPACITY = 2, ST_INTERNAL = 4, ST_TIMEOUT = 8 };
 
+// Inclusive warp scan of one int per lane (all 32 lanes take part).
+__device__ __forceinline__ int warp_incl_scan_i(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive block scan of one int per thread (every thread of the block takes
+// part; scan holds blockDim.x / 32 ints of shared memory); returns the block
+// total in `total`.
+__device__ __forceinline__ int block_excl_scan_i(int v, int &total, int *scan) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int inc = warp_incl_scan_i(v);
+  if (lane == 31) scan[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const int x = lane < nw ? scan[lane] : 0;
+    const int y = warp_incl_scan_i(x);
+    if (lane < nw) scan[lane] = y;
+  }
+  __syncthreads();
+  total = scan[nw - 1];
+  const int before = wid > 0 ? scan[wid - 1] : 0;
+  __syncthreads();
+  return before + inc - v;
+}
+
 // Heavy cells take the cell-at-a-time radius kernel: at least kHeavyMin
 // points, or at least kHeavyMinDense points in a dense x-row (the cell and
 // its two x neighbours hold kHeavyRowDense or more), where sharing one walk
@@ -89,6 +122,36 @@ __device__ __forceinline__ bool heavy_cell(const int *start, unsigned key, unsig
   if (m >= kHeavyMin) return true;
   if (m < kHeavyMinDense || key < 1u || key + 2u > outside) return false;
   return __ldg(start + key + 2) - __ldg(start + key - 1) >= kHeavyRowDense;
+}
+
+// Which radius kernels serve a cell's queries, decided once per cell at
+// binning: heavy cells (heavy_cell) one block per cell; dense cells (light,
+// but with at least kDenseN27 points in the 27 cells around them, i.e. long
+// lists) one warp per query; the rest one thread per query.  The outside
+// cell is dense when it holds kDenseN27 points.  Only the work split
+// depends on it; every path gives the same lists.
+enum : int { kCellLight = 0, kCellHeavy = 1, kCellDense = 2 };
+constexpr int kDenseN27 = 24;
+
+__device__ __forceinline__ int cell_class(const int *start, unsigned key, unsigned outside, int wx, int wy,
+                                          int wz) {
+  if (key >= outside) return __ldg(start + key + 1) - __ldg(start + key) >= kDenseN27 ? kCellDense : kCellLight;
+  if (heavy_cell(start, key, outside)) return kCellHeavy;
+  // the 3 x 3 rows of 3 cells around it (y, z wrapped, x clipped)
+  const unsigned Gx = 1u << wx, Gy = 1u << wy, Gz = 1u << wz;
+  const unsigned x = key & (Gx - 1u), y = (key >> wx) & (Gy - 1u), z = key >> (wx + wy);
+  const unsigned x0 = x > 0u ? x - 1u : 0u, x1 = min(x + 1u, Gx - 1u);
+  int sum = 0;
+#pragma unroll
+  for (int dz = -1; dz <= 1; ++dz) {
+    const unsigned zz = (z + (unsigned)dz) & (Gz - 1u);
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      const unsigned row = (zz << (wx + wy)) | (((y + (unsigned)dy) & (Gy - 1u)) << wx);
+      sum += __ldg(start + row + x1 + 1u) - __ldg(start + row + x0);
+    }
+  }
+  return sum >= kDenseN27 ? kCellDense : kCellLight;
 }
 
 // ---------------------------------------------------------------------------

@@ -28,7 +28,7 @@ __global__ void k_bin_key(const float4 *__restrict__ pos, int n, GridDev g, uint
                           int *__restrict__ count);
 __global__ void k_bin_scatter(const float4 *__restrict__ pos, int n, const uint2 *__restrict__ key_slot,
                               const int *__restrict__ start, float4 *__restrict__ spos,
-                              int *__restrict__ perm, unsigned outside, int *__restrict__ heavy);
+                              int *__restrict__ perm);
 
 namespace {
 
@@ -46,8 +46,7 @@ constexpr size_t kOffStart = align256(kOffCount + sizeof(int) * kNAMaxCells);
 constexpr size_t kOffSpos = align256(kOffStart + sizeof(int) * (kNAMaxCells + 1));
 constexpr size_t kOffPerm = align256(kOffSpos + sizeof(float4) * kNAMaxPoints);
 constexpr size_t kOffScan = align256(kOffPerm + sizeof(int) * kNAMaxPoints);
-constexpr size_t kOffHeavy = align256(kOffScan + sizeof(int) * (kNAMaxCells / 4096 + 2));
-constexpr size_t kOffPartial = align256(kOffHeavy + sizeof(int) * (kNAMaxPoints / kHeavyMinDense + 2));
+constexpr size_t kOffPartial = align256(kOffScan + sizeof(int) * (kNAMaxCells / 4096 + 2));
 constexpr size_t kOffStatus = align256(kOffPartial + sizeof(double) * kNAMaxBlocks);
 constexpr size_t kNoAllocBytes = align256(kOffStatus + sizeof(int));
 
@@ -176,7 +175,6 @@ extern "C" si_status si_neighbor_energy_noalloc(const si_grid_desc *desc, const 
   float4 *spos = (float4 *)(base + kOffSpos);
   int *perm = (int *)(base + kOffPerm);
   int *scan = (int *)(base + kOffScan);
-  int *heavy = (int *)(base + kOffHeavy);
   double *partial = (double *)(base + kOffPartial);
   int *status = (int *)(base + kOffStatus);
   const int64_t n_cells = (1ll << lat.W) + 1;
@@ -188,9 +186,8 @@ extern "C" si_status si_neighbor_energy_noalloc(const si_grid_desc *desc, const 
   g.cell_start = start;
   g.n = (int)n;
   g.status = status;
-  // what must start at zero: cell counts, the heavy-cell counter, the status
+  // what must start at zero: cell counts, the status
   SI_CUDA_TRY(cudaMemsetAsync(count, 0, n_cells * sizeof(int), st));
-  SI_CUDA_TRY(cudaMemsetAsync(heavy, 0, sizeof(int), st));
   SI_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
   SI_CUDA_TRY(cudaMemsetAsync(start, 0, sizeof(int), st));
   if (n > 0)
@@ -201,7 +198,7 @@ extern "C" si_status si_neighbor_energy_noalloc(const si_grid_desc *desc, const 
   if (n > 0)
     SI_KLAUNCH("k_bin_scatter", st,
                k_bin_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-                   (const float4 *)d_pos, (int)n, key_slot, start, spos, perm, 1u << lat.W, heavy));
+                   (const float4 *)d_pos, (int)n, key_slot, start, spos, perm));
   const unsigned blocks = n > 0 ? (unsigned)((n + kNAThreads - 1) / kNAThreads) : 0u;
   const float r2 = r * r;
   if (blocks > 0)

@@ -5,8 +5,8 @@
 // order so that neighbouring threads walk neighbouring cells (their candidate
 // cells are shared through L1/L2); lists of up to 32 ids are sorted while
 // written, longer ones are queued for a warp (or block) bitonic sort.
-// Queries in cells holding at least kHeavyMin points: one block per cell
-// (si_cell.cu), lists written already sorted.
+// Queries in heavy cells (heavy_cell): one block per cell (si_cell.cu), hit
+// masks over id-ordered candidates, expanded into sorted lists after the scan.
 #include <algorithm>
 #include <cmath>
 
@@ -27,7 +27,8 @@ struct CountVisitor {
       count += e - b - ((self >= b && self < e) ? 1 : 0);
       return;
     }
-    for (int j = b; j < e; ++j) {
+    int j = b;
+    for (; j < e; ++j) {
       const float4 p = g.spos[j];
       if (j != self && pair_hit(g, Q, t, B, p)) ++count;
     }
@@ -64,7 +65,8 @@ struct WriteVisitor {
     ++k;
   }
   __device__ __forceinline__ void operator()(const Target &t, bool full, int b, int e) {
-    for (int j = b; j < e; ++j) {
+    int j = b;
+    for (; j < e; ++j) {
       if (j == self) continue;
       if (full || pair_hit(g, Q, t, B, g.spos[j])) emit(__ldg(g.perm + j));
     }
@@ -84,18 +86,21 @@ __device__ __forceinline__ void walk_one(const GridDev &g, const QueryGeom &Q, c
   else walk_sphere(g, Q, P, v);
 }
 
-// One query by one thread.  heavy_min > 0: queries of heavy cells
-// (heavy_cell) are left to the cell kernel.
+// One query by one thread.  skip: bit 0 leaves the queries of heavy cells to
+// the cell kernel, bit 1 those of dense cells to the warp-per-query kernels
+// (the class byte of the query's cell, copied to every slot at binning).
 // stage (nullable): this thread's kInlineSort shared slots, `stride` apart;
 // short lists are sorted there and stored once.
 template <bool WRITE, int WALK>
 __device__ __forceinline__ void radius_one(const GridDev &g, const WalkParams &P, const Band &B,
-                                           unsigned flags, int s, int heavy_min, long long *counts,
+                                           unsigned flags, int s, unsigned skip, long long *counts,
                                            const long long *offsets, int *ids, long long cap,
                                            int *longq, int *stage = nullptr, int stride = 0) {
+  if (skip) {
+    const int c = g.slot_cls[s];
+    if ((c == kCellHeavy && (skip & 1u)) || (c == kCellDense && (skip & 2u))) return;
+  }
   const QueryGeom Q = make_geom(g.spos[s], g);
-  if (heavy_min > 0 && !Q.outside && heavy_cell(g.cell_start, pack3(Q.c[0], Q.c[1], Q.c[2], g), g.outside))
-    return;
   const int self = (flags & SI_INCLUDE_SELF) ? -1 : s;
   const int orig = __ldg(g.perm + s);
   if (!WRITE) {
@@ -127,12 +132,12 @@ __device__ __forceinline__ void radius_one(const GridDev &g, const WalkParams &P
 
 template <bool WRITE, int WALK>
 __global__ void __launch_bounds__(kQueryThreads) k_radius(GridDev g, WalkParams P, Band B, unsigned flags,
-                                                          int heavy_min, long long *counts,
+                                                          unsigned skip, long long *counts,
                                                           const long long *offsets, int *ids,
                                                           long long cap, int *longq) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.n) return;
-  radius_one<WRITE, WALK>(g, P, B, flags, s, heavy_min, counts, offsets, ids, cap, longq);
+  radius_one<WRITE, WALK>(g, P, B, flags, s, skip, counts, offsets, ids, cap, longq);
 }
 
 // Per-query kernel with the class tables staged in shared memory: a
@@ -141,10 +146,11 @@ __global__ void __launch_bounds__(kQueryThreads) k_radius(GridDev g, WalkParams 
 // shared memory instead of L2.
 template <bool WRITE>
 __global__ void __launch_bounds__(kClassThreads) k_radius_cls(GridDev g, WalkParams P, Band B,
-                                                              unsigned flags, int heavy_min,
+                                                              unsigned flags, unsigned skip,
                                                               int n_entries, long long *counts,
                                                               const long long *offsets, int *ids,
-                                                              long long cap, int *longq) {
+                                                              long long cap, int *longq,
+                                                              const int *__restrict__ list) {
   extern __shared__ __align__(16) unsigned long long cls_smem[];
   const int nbeg = g.cls_q * g.cls_q * g.cls_q + 1;
   int *beg_smem = reinterpret_cast<int *>(cls_smem + n_entries);
@@ -156,9 +162,264 @@ __global__ void __launch_bounds__(kClassThreads) k_radius_cls(GridDev g, WalkPar
   GridDev gs = g;
   gs.cls = cls_smem;
   gs.cls_begin = beg_smem;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.n; s += gridDim.x * blockDim.x)
-    radius_one<WRITE, kWalkClasses>(gs, P, B, flags, s, heavy_min, counts, offsets, ids, cap, longq,
-                                    stage, kClassThreads);
+  // list: the light cells' slots (the other cells have their own kernels);
+  // else every slot, skipping by class byte
+  const int nl = list ? list[0] : g.n;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nl; t += gridDim.x * blockDim.x)
+    radius_one<WRITE, kWalkClasses>(gs, P, B, flags, list ? list[1 + t] : t, list ? 0u : skip, counts, offsets,
+                                    ids, cap, longq, stage, kClassThreads);
+}
+
+// Queries of dense cells (queued at binning): one warp per query.
+//
+// Flattened class walk: lane r decodes row r of each batch of 32 rows of the
+// query's class list into its runs of points (two if the row crosses the
+// cyclic x boundary), so that all run bounds are fetched at once; a warp
+// prefix of the run lengths numbers the batch's candidates and the lanes
+// take them 32 at a time.  fn(hit, j) is called by every lane for each group
+// of 32 (j < 0: no candidate).  The outside cell, if a row reaches it, is
+// taken last, every pair in FP64.  Query points outside the region walk the
+// bounding cube instead (warp visitors below).
+struct FlatRuns {
+  int b[64];
+  int len[64];
+  float qx[64], qy[64], qz[64];
+  unsigned char flags[64];   // bit 0: whole run inside the sphere, bit 1: wrapped image
+  int pre[33];
+};
+
+template <class F>
+__device__ __forceinline__ void warp_class_walk(const GridDev &g, const QueryGeom &Q, const Band &B, int self,
+                                                int lane, FlatRuns &R, F &fn) {
+  const int q = g.cls_q;
+  const int ci = min((int)(Q.phi[0] * (float)q), q - 1);
+  const int cj = min((int)(Q.phi[1] * (float)q), q - 1);
+  const int ck = min((int)(Q.phi[2] * (float)q), q - 1);
+  const int c = (ck * q + cj) * q + ci;
+  const int cb = g.cls_begin[c], ce = g.cls_begin[c + 1];
+  const int Gx = 1 << g.wx;
+  const bool cyc_x = g.cyc & 1u;
+  bool out_any = false;
+  for (int base = cb; base < ce; base += 32) {
+    const int t = base + lane;
+    int b0 = 0, l0 = 0, b1 = 0, l1 = 0;
+    float qx0 = 0.f, qy0 = 0.f, qz0 = 0.f, qx1 = 0.f;
+    unsigned f0 = 0u, f1 = 0u;
+    bool out = false;
+    if (t < ce) {
+      const unsigned long long E = g.cls[t];
+      const int lo = (int)(signed char)((E >> 48) & 0xffull);
+      const int len = (int)((E >> 56) & 127ull);
+      const unsigned full = (unsigned)(E >> 63);
+      const Target tg = translate_raw(E & ((1ull << 48) - 1ull), Q, g);
+      if (tg.outside) {
+        out = true;
+      } else {
+        const unsigned row = tg.key - (unsigned)Q.c[0];
+        int x0 = Q.c[0] + lo, x1 = x0 + len - 1;
+        qx0 = tg.qx;
+        qy0 = tg.qy;
+        qz0 = tg.qz;
+        f0 = full | (tg.wrapped ? 2u : 0u);
+        if (!cyc_x) {
+          if (x0 < 0 || x1 >= Gx) out = true;
+          x0 = max(x0, 0);
+          x1 = min(x1, Gx - 1);
+        } else if (x0 < 0 || x1 >= Gx) {
+          const int wa = x0 < 0 ? x0 + Gx : 0;
+          const int wb = x0 < 0 ? Gx - 1 : x1 - Gx;
+          b1 = __ldg(g.cell_start + row + wa);
+          l1 = __ldg(g.cell_start + row + wb + 1) - b1;
+          qx1 = Q.q.x + (x0 < 0 ? g.Lx : -g.Lx);
+          f1 = full | 2u;
+          x0 = max(x0, 0);
+          x1 = min(x1, Gx - 1);
+        }
+        if (x0 <= x1) {
+          b0 = __ldg(g.cell_start + row + x0);
+          l0 = __ldg(g.cell_start + row + x1 + 1) - b0;
+        }
+      }
+    }
+    out_any |= __any_sync(0xffffffffu, out);
+    R.b[2 * lane] = b0;
+    R.len[2 * lane] = l0;
+    R.qx[2 * lane] = qx0;
+    R.qy[2 * lane] = qy0;
+    R.qz[2 * lane] = qz0;
+    R.flags[2 * lane] = (unsigned char)f0;
+    R.b[2 * lane + 1] = b1;
+    R.len[2 * lane + 1] = l1;
+    R.qx[2 * lane + 1] = qx1;
+    R.qy[2 * lane + 1] = qy0;
+    R.qz[2 * lane + 1] = qz0;
+    R.flags[2 * lane + 1] = (unsigned char)f1;
+    int inc = l0 + l1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    R.pre[lane + 1] = inc;
+    if (lane == 0) R.pre[0] = 0;
+    __syncwarp();
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    for (int f = lane; f - lane < total; f += 32) {
+      int j = -1;
+      bool hit = false;
+      if (f < total) {
+        // the lane whose runs hold candidate f: the last L with pre[L] <= f
+        int L = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (R.pre[L + step] <= f) L += step;
+        int off = f - R.pre[L];
+        int slot = 2 * L;
+        if (off >= R.len[slot]) {
+          off -= R.len[slot];
+          ++slot;
+        }
+        j = R.b[slot] + off;
+        if (j != self) {
+          const unsigned fl = R.flags[slot];
+          if (fl & 1u) {
+            hit = true;
+          } else {
+            const float4 p = g.spos[j];
+            const float dx = p.x - R.qx[slot], dy = p.y - R.qy[slot], dz = p.z - R.qz[slot];
+            const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float blo = (fl & 2u) ? B.lo_w : B.lo, bhi = (fl & 2u) ? B.hi_w : B.hi;
+            hit = d2 <= blo || (!(d2 > bhi) && canon_d2(Q.q, p, g) <= B.r2);
+          }
+        }
+      }
+      fn(hit, j);
+    }
+    __syncwarp();   // the next batch rewrites R
+  }
+  if (out_any) {
+    const int b = __ldg(g.cell_start + g.outside), e = __ldg(g.cell_start + g.outside + 1);
+    for (int j0 = b; j0 < e; j0 += 32) {
+      const int j = j0 + lane;
+      const bool hit = j < e && j != self && canon_d2(Q.q, g.spos[j], g) <= B.r2;
+      fn(hit, j < e ? j : -1);
+    }
+  }
+}
+
+struct WarpCountVisitor {
+  const GridDev &g;
+  const QueryGeom &Q;
+  const Band &B;
+  int self, lane;
+  long long count;
+  __device__ __forceinline__ void operator()(const Target &t, bool full, int b, int e) {
+    for (int j0 = b; j0 < e; j0 += 32) {
+      const int j = j0 + lane;
+      bool h = j < e && j != self;
+      if (h && !full) h = pair_hit(g, Q, t, B, g.spos[j]);
+      count += __popc(__ballot_sync(0xffffffffu, h));
+    }
+  }
+  __device__ __forceinline__ void operator()(const Target &t, bool full) {
+    (*this)(t, full, __ldg(g.cell_start + t.key), __ldg(g.cell_start + t.key + 1));
+  }
+};
+
+struct WarpWriteVisitor {
+  const GridDev &g;
+  const QueryGeom &Q;
+  const Band &B;
+  int self, lane;
+  int *list;       // the warp's shared list (len <= kDenseCap) or the output list
+  int len, k;
+  __device__ __forceinline__ void add(bool h, int j) {
+    const unsigned m = __ballot_sync(0xffffffffu, h);
+    if (h) {
+      const int p = k + __popc(m & ((1u << lane) - 1u));
+      if (p < len) list[p] = __ldg(g.perm + j);
+    }
+    k += __popc(m);
+  }
+  __device__ __forceinline__ void operator()(const Target &t, bool full, int b, int e) {
+    for (int j0 = b; j0 < e; j0 += 32) {
+      const int j = j0 + lane;
+      bool h = j < e && j != self;
+      if (h && !full) h = pair_hit(g, Q, t, B, g.spos[j]);
+      add(h, j);
+    }
+  }
+  __device__ __forceinline__ void operator()(const Target &t, bool full) {
+    (*this)(t, full, __ldg(g.cell_start + t.key), __ldg(g.cell_start + t.key + 1));
+  }
+};
+
+template <bool WRITE>
+__global__ void __launch_bounds__(kClassThreads, 4) k_radius_dense(GridDev g, WalkParams P, Band B,
+                                                                   unsigned flags, int n_entries,
+                                                                   const int *__restrict__ denseq,
+                                                                   long long *counts, const long long *offsets,
+                                                                   int *ids, long long cap, int *longq) {
+  extern __shared__ __align__(16) unsigned long long cls_smem[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+  const int nq = denseq[0];
+  if (blockIdx.x * nwb >= nq) return;   // no work for this block
+  const int nbeg = g.cls_q * g.cls_q * g.cls_q + 1;
+  int *beg_smem = reinterpret_cast<int *>(cls_smem + n_entries);
+  FlatRuns *runs = reinterpret_cast<FlatRuns *>(beg_smem + ((nbeg + 3) & ~3));
+  int *buf = reinterpret_cast<int *>(runs + nwb) + w * kDenseCap;   // write pass only
+  for (int i = threadIdx.x; i < n_entries; i += blockDim.x) cls_smem[i] = __ldg(g.cls + i);
+  for (int i = threadIdx.x; i < nbeg; i += blockDim.x) beg_smem[i] = __ldg(g.cls_begin + i);
+  __syncthreads();
+  GridDev gs = g;
+  gs.cls = cls_smem;
+  gs.cls_begin = beg_smem;
+  FlatRuns &R = runs[w];
+  for (int item = blockIdx.x * nwb + w; item < nq; item += gridDim.x * nwb) {
+    const int s = denseq[1 + item];
+    const QueryGeom Q = make_geom(g.spos[s], g);
+    const int self = (flags & SI_INCLUDE_SELF) ? -1 : s;
+    const int orig = __ldg(g.perm + s);
+    if (!WRITE) {
+      long long count = 0;
+      if (Q.outside) {
+        WarpCountVisitor v{gs, Q, B, self, lane, 0};
+        walk_cube(gs, Q, P.dg, v);
+        count = v.count;
+      } else {
+        auto fn = [&](bool hit, int) { count += __popc(__ballot_sync(0xffffffffu, hit)); };
+        warp_class_walk(gs, Q, B, self, lane, R, fn);
+      }
+      if (lane == 0) counts[orig] = count;
+    } else {
+      const long long base = offsets[orig];
+      const int len = (int)(offsets[orig + 1] - base);
+      if (len == 0) continue;
+      if (base + len > cap) {
+        if (lane == 0) atomicOr(g.status, ST_CAPACITY);
+        continue;
+      }
+      const bool staged = len <= kDenseCap;
+      WarpWriteVisitor v{gs, Q, B, self, lane, staged ? buf : ids + base, len, 0};
+      if (Q.outside) {
+        walk_cube(gs, Q, P.dg, v);
+      } else {
+        auto fn = [&](bool hit, int j) { v.add(hit, j); };
+        warp_class_walk(gs, Q, B, self, lane, R, fn);
+      }
+      if (v.k != len && lane == 0) atomicOr(g.status, ST_INTERNAL);
+      const bool sort_all = !(flags & SI_NO_SORT);
+      if (staged) {
+        __syncwarp();
+        if (sort_all) bitonic_padded(buf, len, lane, 32, WarpSync());
+        for (int i = lane; i < len; i += 32) ids[base + i] = buf[i];
+        __syncwarp();
+      } else if (sort_all && lane == 0) {
+        const int slot = atomicAdd(longq, 1);
+        longq[1 + slot] = orig;
+      }
+    }
+  }
 }
 
 // Queries the cell kernel handed back (listed by sorted slot): per query.
@@ -249,9 +510,13 @@ static WalkParams walk_params(const Lattice &lat, float r, bool inclusion) {
   return P;
 }
 
+// The class walk with its tables in shared memory: the walk of the
+// warp-per-query kernels for dense cells.
+static bool dense_path(int walk, const si_grid *gr) { return walk == kWalkClasses && gr->cls_smem_bytes > 0; }
+
 template <bool WRITE>
 static si_status launch_light(int walk, const si_grid *gr, const GridDev &dv, const WalkParams &P,
-                              const Band &B, unsigned flags, int heavy_min, long long *counts,
+                              const Band &B, unsigned flags, unsigned skip, long long *counts,
                               const long long *off, int *ids, long long cap, int *longq,
                               unsigned blocks, cudaStream_t st) {
   if (walk == kWalkCube) {
@@ -271,16 +536,37 @@ static si_status launch_light(int walk, const si_grid *gr, const GridDev &dv, co
     const unsigned grid = (unsigned)std::max(1, std::min<int>(per_sm, 8) * 148);
     SI_KLAUNCH(WRITE ? "k_radius_write" : "k_radius_count", st,
                k_radius_cls<WRITE><<<grid, kClassThreads, smem, st>>>(
-                   dv, P, B, flags, heavy_min, (int)gr->cls_host.size(), counts, off, ids, cap, longq));
+                   dv, P, B, flags, skip, (int)gr->cls_host.size(), counts, off, ids, cap, longq,
+                   skip == 3u ? gr->lightq : nullptr));
   } else if (walk == kWalkClasses) {
     SI_KLAUNCH(WRITE ? "k_radius_write_cls_l2" : "k_radius_count_cls_l2", st,
                k_radius<WRITE, kWalkClasses><<<blocks, kQueryThreads, 0, st>>>(
-                   dv, P, B, flags, heavy_min, counts, off, ids, cap, longq));
+                   dv, P, B, flags, skip, counts, off, ids, cap, longq));
   } else {
     SI_KLAUNCH(WRITE ? "k_radius_write_eq2" : "k_radius_count_eq2", st,
                k_radius<WRITE, kWalkPaper><<<blocks, kQueryThreads, 0, st>>>(
-                   dv, P, B, flags, heavy_min, counts, off, ids, cap, longq));
+                   dv, P, B, flags, skip, counts, off, ids, cap, longq));
   }
+  return SI_OK;
+}
+
+template <bool WRITE>
+static si_status launch_dense(const si_grid *gr, const GridDev &dv, const WalkParams &P, const Band &B,
+                              unsigned flags, long long *counts, const long long *off, int *ids,
+                              long long cap, int *longq, cudaStream_t st) {
+  const int nbeg = gr->cls_q * gr->cls_q * gr->cls_q + 1;
+  const size_t smem = gr->cls_host.size() * sizeof(unsigned long long) +
+                      (size_t)((nbeg + 3) & ~3) * sizeof(int) + (kClassThreads / 32) * sizeof(FlatRuns) +
+                      (WRITE ? (size_t)kDenseCap * (kClassThreads / 32) * sizeof(int) : 0);
+  SI_CUDA_TRY(cudaFuncSetAttribute(k_radius_dense<WRITE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  int per_sm = 0;
+  SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radius_dense<WRITE>, kClassThreads,
+                                                            smem));
+  const unsigned grid = (unsigned)std::max(1, std::min<int>(per_sm, 8) * 148);
+  SI_KLAUNCH(WRITE ? "k_radius_dense_write" : "k_radius_dense_count", st,
+             k_radius_dense<WRITE><<<grid, kClassThreads, smem, st>>>(
+                 dv, P, B, flags, (int)gr->cls_host.size(), gr->denseq, counts, off, ids, cap, longq));
   return SI_OK;
 }
 
@@ -309,12 +595,13 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   // the cell path holds the whole cell-level sphere (entries with b^2 <= n)
   const int n_tab = std::min((int)std::floor((double)P.dg * (double)P.dg), g->tables.n_max);
   const bool heavy = !cube && n_tab >= 0 && g->tab_end_host[n_tab] <= kCellTCap;
-  const int heavy_min = heavy ? kHeavyMin : 0;
+  const unsigned skip = (heavy ? 1u : 0u) | (dense_path(walk, g) ? 2u : 0u);
   long long *off = (long long *)d_offsets;
   const unsigned blocks = (unsigned)((m + kQueryThreads - 1) / kQueryThreads);
   si_status s;
   // count phase: per-query counts of light cells, the cell kernel's counts
-  // and scratch lists for heavy cells, per-query counts of what it handed back
+  // and scratch records (ordered candidate ids, hit masks) for heavy cells,
+  // per-query counts of what it handed back
   auto count_phase = [&]() -> si_status {
     SI_CUDA_TRY(cudaMemsetAsync(off, 0, sizeof(long long), st));
     SI_CUDA_TRY(cudaMemsetAsync(g->counters, 0, kCounterInts * sizeof(int), st));
@@ -322,8 +609,11 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
     SI_CUDA_TRY(cudaMemsetAsync(g->scr_top, 0, sizeof(unsigned long long), st));
     if (m == 0) return SI_OK;
     si_status r;
-    if ((r = launch_light<false>(walk, g, dv, P, B, flags, heavy_min, off + 1, nullptr, nullptr, 0,
+    if ((r = launch_light<false>(walk, g, dv, P, B, flags, skip, off + 1, nullptr, nullptr, 0,
                                  nullptr, blocks, st)) != SI_OK)
+      return r;
+    if (dense_path(walk, g) &&
+        (r = launch_dense<false>(g, dv, P, B, flags, off + 1, nullptr, nullptr, 0, nullptr, st)) != SI_OK)
       return r;
     if (heavy) {
       if ((r = launch_cell_pass(dv, P, B, flags, g->heavy, g->counters, g->over, off + 1, g->scr_off,
@@ -341,7 +631,7 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
     SI_CUDA_TRY(cudaMemcpyAsync(g->h_pinned, off + m, sizeof(long long), cudaMemcpyDeviceToHost, st));
     SI_CUDA_TRY(cudaMemcpyAsync(g->h_pinned + 1, g->scr_top, sizeof(long long), cudaMemcpyDeviceToHost, st));
     SI_CUDA_TRY(cudaStreamSynchronize(st));
-    // cells whose lists did not fit the scratch took the per-query path;
+    // cells whose records did not fit the scratch took the per-query path;
     // make room and count again so that the cell kernel serves them
     if (heavy && g->h_pinned[1] > g->scr_cap) {
       const long long want = g->h_pinned[1] + g->h_pinned[1] / 4 + 1024;
@@ -363,17 +653,20 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   if (m == 0) return SI_OK;
   SI_CUDA_TRY(cudaMemsetAsync(g->longq, 0, sizeof(int), st));
   SI_CUDA_TRY(cudaMemsetAsync(g->hugeq, 0, sizeof(int), st));
-  if ((s = launch_light<true>(walk, g, dv, P, B, flags, heavy_min, nullptr, off, d_ids, ids_capacity,
+  if ((s = launch_light<true>(walk, g, dv, P, B, flags, skip, nullptr, off, d_ids, ids_capacity,
                               g->longq, blocks, st)) != SI_OK)
     return s;
   if (heavy) {
-    if ((s = launch_cell_copy(dv, g->heavy, g->scr_off, g->scratch, off, d_ids, ids_capacity, st)) != SI_OK)
+    if ((s = launch_cell_expand(dv, g->heavy, g->scr_off, g->scratch, off, d_ids, ids_capacity, st)) != SI_OK)
       return s;
     SI_KLAUNCH("k_radius_over_write", st,
                k_radius_over<true><<<148 * 4, kQueryThreads, 0, st>>>(dv, P, B, flags, g->over, nullptr,
                                                                       off, d_ids, ids_capacity,
                                                                       g->longq));
   }
+  if (dense_path(walk, g) &&
+      (s = launch_dense<true>(g, dv, P, B, flags, nullptr, off, d_ids, ids_capacity, g->longq, st)) != SI_OK)
+    return s;
   if (!(flags & SI_NO_SORT)) {
     const size_t wsm = (size_t)kSortWarps * kSortWarpCap * sizeof(int);
     SI_CUDA_TRY(cudaFuncSetAttribute(k_sort_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));

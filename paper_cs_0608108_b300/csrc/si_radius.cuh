@@ -10,11 +10,11 @@ namespace si {
 constexpr int kQueryThreads = 128;   // per-query kernels
 constexpr int kClassThreads = 256;   // per-query kernel with shared-memory class tables
 constexpr int kInlineSort = 32;      // lists up to this length are sorted while written
+constexpr int kDenseCap = 512;       // lists a warp of the dense path sorts in shared memory
 constexpr int kCellThreads = 512;
 constexpr int kCellCap = 2560;       // staged candidates per query cell
 constexpr int kCellMaxQ = 512;       // queries of one cell in one block
 constexpr int kCellTCap = 512;       // target cells of the cell-level sphere
-constexpr int kCellMaskCap = 4096;   // (query, 32-candidate) ballots kept per query batch
 constexpr int kSortWarps = 8;
 constexpr int kSortWarpCap = 2048;   // lists a warp sorts in shared memory
 constexpr int kSortBlockCap = 16384; // lists a block sorts in shared memory
@@ -23,7 +23,7 @@ size_t cell_smem_bytes();
 si_status launch_cell_pass(const GridDev &g, const WalkParams &P, const Band &B, unsigned flags,
                            const int *heavy, int *work, int *over, long long *counts, long long *scr_off,
                            int *scratch, long long scr_cap, unsigned long long *scr_top, cudaStream_t st);
-si_status launch_cell_copy(const GridDev &g, const int *heavy, const long long *scr_off, const int *scratch,
-                           const long long *offsets, int *ids, long long cap, cudaStream_t st);
+si_status launch_cell_expand(const GridDev &g, const int *heavy, const long long *scr_off, const int *scratch,
+                             const long long *offsets, int *ids, long long cap, cudaStream_t st);
 
 }  // namespace si

@@ -12,12 +12,15 @@ namespace si {
 // a pair whose upper index is past n never moves anything.
 template <class Sync>
 __device__ __forceinline__ void bitonic_padded(int *a, int n, int rank, int lanes, Sync sync) {
-  int P = 1;
-  while (P < n) P <<= 1;
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int i = rank; i < P / 2; i += lanes) {
-      const int lo = (i / (k / 2)) * k + (i % (k / 2));
-      const int hi = (lo / k) * k + (k - 1 - (lo % k));
+  int lg = 0;
+  while ((1 << lg) < n) ++lg;
+  const int half = (1 << lg) >> 1;
+  // merge width k = 2^ks; pair i of a stage: block of k, then offset inside
+  for (int ks = 1; ks <= lg; ++ks) {
+    const int k = 1 << ks;
+    for (int i = rank; i < half; i += lanes) {
+      const int lo = ((i >> (ks - 1)) << ks) + (i & ((k >> 1) - 1));
+      const int hi = (lo & ~(k - 1)) + (k - 1 - (lo & (k - 1)));
       if (hi < n && a[hi] < a[lo]) {
         const int t = a[lo];
         a[lo] = a[hi];
@@ -25,9 +28,10 @@ __device__ __forceinline__ void bitonic_padded(int *a, int n, int rank, int lane
       }
     }
     sync();
-    for (int h = k / 4; h >= 1; h >>= 1) {
-      for (int i = rank; i < P / 2; i += lanes) {
-        const int lo = (i / h) * 2 * h + (i % h);
+    for (int hs = ks - 2; hs >= 0; --hs) {
+      const int h = 1 << hs;
+      for (int i = rank; i < half; i += lanes) {
+        const int lo = ((i >> hs) << (hs + 1)) + (i & (h - 1));
         const int hi = lo + h;
         if (hi < n && a[hi] < a[lo]) {
           const int t = a[lo];

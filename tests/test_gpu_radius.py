@@ -171,6 +171,45 @@ def test_heavy_mixture_lists_sorted_and_exact():
     assert np.array_equal(np.sort(fwd), np.sort(bwd))
 
 
+def _sparse_cells_with_long_lists(scene, off_o, min_hits=64):
+    """Queries in cells of at most two points whose lists exceed min_hits:
+    their walks pass the per-thread candidate budget, so the warp-per-query
+    kernels serve them."""
+    c = np.floor((scene.pos[:, :3].astype(np.float64) - np.array(scene.origin)) / scene.cell_size)
+    key = np.where((c < 0).any(1) | (c >= 2 ** np.array(scene.log2_cells)).any(1), -1,
+                   c[:, 0] + 2 ** scene.log2_cells[0] * (c[:, 1] + 2 ** scene.log2_cells[1] * c[:, 2]))
+    inside = key >= 0
+    cnt = np.zeros(scene.n, dtype=np.int64)
+    u, inv, k = np.unique(key[inside], return_inverse=True, return_counts=True)
+    cnt[inside] = k[inv]
+    return int(((cnt <= 2) & inside & (np.diff(off_o) > min_hits)).sum())
+
+
+@pytest.mark.parametrize("mask", [7, 0])
+def test_dense_light_queries_exact(mask):
+    # sparse cells beside dense clusters: light queries with long lists; the
+    # non-cyclic variant adds a cluster outside the region (queries outside
+    # the region walk the bounding cube, their outside cell holds hundreds)
+    pos = synth.gaussian_mixture_points(40_000, 31 + mask, n_comp=8, sigma=0.025)
+    if mask == 0:
+        out = synth.gaussian_mixture_points(600, 5, n_comp=1, sigma=0.004)
+        out[:, 0] = 1.0 + 0.01 + out[:, 0] * 0.02
+        pos = np.concatenate([pos, out]).astype(np.float32)
+    scene = synth.Scene(pos, (0, 0, 0), 1 / 32, (5, 5, 5), mask, 1.5 / 32)
+    off_o, ids_o = oracle_radius(scene)
+    assert _sparse_cells_with_long_lists(scene, off_o) > 50
+    off_g, ids_g = gpu_radius(scene)
+    assert_csr_equal(off_g, ids_g, off_o, ids_o)
+    off_s, ids_s = oracle_radius(scene, include_self=True)
+    g = gpu_grid(scene)
+    off_gs, ids_gs = gpu_radius(scene, include_self=True, grid=g)
+    assert_csr_equal(off_gs, ids_gs, off_s, ids_s)
+    off_u, ids_u = gpu_radius(scene, sort=False, grid=g)
+    assert np.array_equal(off_u, off_o)
+    for q in range(0, scene.n, 3):
+        assert np.array_equal(np.sort(ids_u[off_u[q]:off_u[q + 1]]), ids_o[off_o[q]:off_o[q + 1]])
+
+
 @pytest.mark.parametrize("name", ["uniform_1m", "mixture_1m"])
 def test_full_size_1m_configs_sampled(name):
     scene = synth.uniform_1m_scene() if name == "uniform_1m" else synth.mixture_1m_scene()
