@@ -22,9 +22,12 @@
 // Record of a cell in the scratch buffer: nc, the nc ordered ids, then one
 // 32-bit mask per (query, 32 candidates), query-major.  After the prefix sum,
 // k_cell_expand turns every query's masks into its ids at their place in the
-// output.  A cell whose candidates or queries do not fit shared memory, or
-// whose record does not fit the scratch buffer, hands its queries to the
-// per-query path.
+// output.
+// Two configurations: most heavy cells fit a small block (8 warps, 1280
+// candidates, 256 queries, four blocks per SM); a cell that does not is
+// listed for the large one (16 warps, 2560 candidates, 512 queries), launched
+// after it.  A cell that fits neither, or whose record does not fit the
+// scratch buffer, hands its queries to the per-query path.
 #include <cmath>
 
 #include "si_host.h"
@@ -33,31 +36,43 @@
 
 namespace si {
 
-constexpr int kBuckets = 1024;
 constexpr int kQlBits = 9;   // query index inside its cell in a scratch reference
 static_assert(kCellMaxQ <= (1 << kQlBits), "query index field too narrow");
 
+template <int THREADS, int CAP, int MAXQ, int BUCKETS, int MINB>
+struct CellCfg {
+  static constexpr int kThreads = THREADS;   // block size
+  static constexpr int kCap = CAP;           // staged candidates
+  static constexpr int kMaxQ = MAXQ;         // queries of the cell
+  static constexpr int kBuckets = BUCKETS;   // id buckets of the sort
+  static constexpr int kMinBlocks = MINB;    // resident blocks per SM
+  static constexpr int kBucketBits = BUCKETS == 1024 ? 10 : (BUCKETS == 512 ? 9 : 8);
+  static_assert((1 << kBucketBits) == BUCKETS, "bucket count must be 256, 512 or 1024");
+};
+using CellSmall = CellCfg<256, 1280, 256, 512, 4>;
+using CellLarge = CellCfg<kCellThreads, kCellCap, kCellMaxQ, 1024, 2>;
+
+template <class C>
 struct CellSmem {
-  float4 c[kCellCap];                      // candidate in the query frame; x = NaN: outside cell; w = spos slot
-  unsigned long long key[kCellCap];        // (input index << 32) | staging slot, in bucket order
-  int sid[kCellCap];                       // input index of each staged candidate
-  int bstart[kBuckets];                    // bucket counts, then starts
-  int bcur[kBuckets];                      // bucket fill pointers
-  struct {                                 // gather: the cell-level sphere's target cells
-    unsigned tkey[kCellTCap];
+  float4 c[C::kCap];                       // candidate in the query frame; x = NaN: outside cell; w = spos slot
+  unsigned long long key[C::kCap];         // (input index << 32) | staging slot, in bucket order
+  int sid[C::kCap];                        // input index of each staged candidate
+  int bstart[C::kBuckets];                 // bucket counts, then starts
+  int bcur[C::kBuckets];                   // bucket fill pointers
+  struct {                                 // gather: runs of points of the cell-level sphere
     int tbeg[kCellTCap];
     int tcnt[kCellTCap];
     int tpre[kCellTCap + 1];
     unsigned char tcode[kCellTCap];
   } t;
-  float4 q[kCellMaxQ];                     // the cell's query points; w = own position among the candidates
-  int qcnt[kCellMaxQ];                     // hits per query
-  int scan[kCellThreads / 32];
+  float4 q[C::kMaxQ];                      // the cell's query points; w = own position among the candidates
+  int qcnt[C::kMaxQ];                      // hits per query
+  int scan[C::kThreads / 32];
   long long base;                          // the cell's record in the scratch buffer (-1: no room)
   int nt, nc, out_seen, item;
 };
 
-size_t cell_smem_bytes() { return sizeof(CellSmem); }
+size_t cell_smem_bytes() { return sizeof(CellSmem<CellLarge>); }
 
 // Packed FP32 pairs (low half = first value) and the squared distance of
 // two candidates to one query with f32x2 instructions.
@@ -83,32 +98,39 @@ __device__ __forceinline__ unsigned long long dist2_x2(unsigned long long X, uns
 // Scratch reference of a heavy query: its cell's record and its index there.
 __device__ __forceinline__ long long cell_ref(long long rec, int ql) { return (rec << kQlBits) | ql; }
 
-__global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams P, Band B, unsigned flags,
-                                                          const int *__restrict__ heavy, int *work,
-                                                          int *__restrict__ over,
-                                                          long long *__restrict__ counts,
-                                                          long long *__restrict__ scr_off,
-                                                          int *__restrict__ scratch, long long scr_cap,
-                                                          unsigned long long *scr_top) {
+// cells: [0] = count, then cell keys; next (nullable): where cells that do
+// not fit go (else the per-query path takes them).
+template <class C>
+__global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, WalkParams P, Band B,
+                                                                    unsigned flags, const int *__restrict__ cells,
+                                                                    int *work, int *next, int *__restrict__ over,
+                                                                    long long *__restrict__ counts,
+                                                                    long long *__restrict__ scr_off,
+                                                                    int *__restrict__ scratch, long long scr_cap,
+                                                                    unsigned long long *scr_top) {
+  constexpr int kBuckets = C::kBuckets;
+  constexpr int kCap = C::kCap;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CellSmem &S = *reinterpret_cast<CellSmem *>(smem_raw);
-  const int nheavy = heavy[0];
-  const int n = min((int)(P.dg * P.dg), g.n_max);
-  const int n_tab = __ldg(g.tab_end + n);
+  CellSmem<C> &S = *reinterpret_cast<CellSmem<C> *>(smem_raw);
+  const int nheavy = cells[0];
   const bool incl_self = flags & SI_INCLUDE_SELF;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   const float box2 = (P.dg + g.eps) * (P.dg + g.eps);
-  // bucket of an input index: its top 10 bits within [0, n)
+  // bucket of an input index: its top bits within [0, n)
   int idbits = 1;
   while (idbits < 31 && (1 << idbits) < g.n) ++idbits;
-  const int bshift = max(idbits - 10, 0);
+  const int bshift = max(idbits - C::kBucketBits, 0);
   for (;;) {
     if (tid == 0) S.item = atomicAdd(work, 1);
     __syncthreads();
     const int item = S.item;
     if (item >= nheavy) return;
-    const unsigned key = (unsigned)heavy[1 + item];
+    const unsigned key = (unsigned)cells[1 + item];
+    if (next && g.cell_cls[key] == kCellHeavyBig) {   // listed for the large configuration
+      __syncthreads();   // every thread has read S.item before it is rewritten
+      continue;
+    }
     const int qs = g.cell_start[key], nq = g.cell_start[key + 1] - qs;
     const int cx = (int)(key & ((1u << g.wx) - 1u));
     const int cy = (int)((key >> g.wx) & ((1u << g.wy) - 1u));
@@ -120,7 +142,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
       S.out_seen = 0;
     }
     for (int b = tid; b < kBuckets; b += blockDim.x) S.bstart[b] = 0;
-    bool fits = nq <= kCellMaxQ && n_tab <= kCellTCap;
+    bool fits = nq <= C::kMaxQ;
     if (fits)
       for (int i = tid; i < nq; i += blockDim.x) {
         S.q[i] = g.spos[qs + i];
@@ -128,32 +150,51 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
       }
     __syncthreads();
     if (fits) {
-      // 1. non-empty target cells of the cell-level sphere
-      for (int e = tid; e < n_tab; e += blockDim.x) {
-        const TabEntry E = g.tab[e];
-        const unsigned long long s = cu + E.unp;
-        unsigned tk, code = 0;
-        if (s & g.guard_non) {
-          if (atomicExch(&S.out_seen, 1)) continue;   // the outside cell is listed once
-          tk = g.outside;
-          code = 64u;
-        } else {
-          tk = repack(s & g.valid, g);
-          if (s & g.gx) code |= E.ox > 0 ? 1u : 2u;
-          if (s & g.gy) code |= (E.oy > 0 ? 1u : 2u) << 2;
-          if (s & g.gz) code |= (E.oz > 0 ? 1u : 2u) << 4;
-        }
-        const int b = __ldg(g.cell_start + tk), c = __ldg(g.cell_start + tk + 1) - b;
-        if (c == 0) continue;
+      // 1. runs of the cell-level sphere: each x-row of cells within d of the
+      //    query cell (b^2 <= floor(d^2)) is one run of points, or two where
+      //    it crosses the cyclic x boundary; rows leaving the region on a
+      //    non-cyclic axis stand for the outside cell, listed once
+      const int Gx = 1 << g.wx;
+      const bool cyc_x = g.cyc & 1u;
+      auto add_run = [&](unsigned ka, unsigned kb, unsigned code) {
+        const int b = __ldg(g.cell_start + ka), c = __ldg(g.cell_start + kb + 1) - b;
+        if (c == 0) return;
         const int t = atomicAdd(&S.nt, 1);
-        S.t.tkey[t] = tk;
         S.t.tbeg[t] = b;
         S.t.tcnt[t] = c;
         S.t.tcode[t] = (unsigned char)code;
+      };
+      for (int e = tid; e < g.n_crow; e += blockDim.x) {
+        const unsigned long long E = g.crow[e];
+        const int lo = (int)(signed char)((E >> 48) & 0xffull);
+        const int len = (int)((E >> 56) & 127ull);
+        const unsigned long long off = E & ((1ull << 48) - 1ull);
+        const unsigned long long sum = cu + off;   // the row's y and z; x stays the cell's own
+        bool out = (sum & g.guard_non) != 0ull;
+        if (!out) {
+          // image shift of the row's candidates on wrapped y / z (1: +L, 2: -L)
+          unsigned code = 0;
+          if (sum & g.gy) code |= ((off & g.gy) ? 2u : 1u) << 2;
+          if (sum & g.gz) code |= ((off & g.gz) ? 2u : 1u) << 4;
+          const unsigned row = repack(sum & g.valid, g) - (unsigned)cx;   // packed index of x = 0
+          int x0 = cx + lo, x1 = x0 + len - 1;
+          if (!cyc_x) {
+            if (x0 < 0 || x1 >= Gx) out = true;
+            x0 = max(x0, 0);
+            x1 = min(x1, Gx - 1);
+          } else if (x0 < 0 || x1 >= Gx) {
+            const int wa = x0 < 0 ? x0 + Gx : 0, wb = x0 < 0 ? Gx - 1 : x1 - Gx;
+            add_run(row + (unsigned)wa, row + (unsigned)wb, code | (x0 < 0 ? 2u : 1u));
+            x0 = max(x0, 0);
+            x1 = min(x1, Gx - 1);
+          }
+          if (x0 <= x1) add_run(row + (unsigned)x0, row + (unsigned)x1, code);
+        }
+        if (out && !atomicExch(&S.out_seen, 1)) add_run(g.outside, g.outside, 64u);
       }
       __syncthreads();
       const int nt = S.nt;
-      // 2a. prefix of target sizes (one warp)
+      // 2a. prefix of run sizes (one warp)
       if (wid == 0) {
         int run = 0;
         for (int b0 = 0; b0 < nt; b0 += 32) {
@@ -168,47 +209,53 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
       __syncthreads();
       const int ntot = S.t.tpre[nt];
       // 2b. gather: candidates within d of the query cell box, in the query
-      //     frame, with their input indices counted into buckets
+      //     frame, with their input indices counted into buckets.  A warp
+      //     takes 32 * kGather consecutive candidates: the first one's run by
+      //     binary search, the others' by stepping forward.
       constexpr int kGather = 4;
-      for (int base = 0; base < ntot; base += kGather * blockDim.x) {
+      for (int f0 = wid * 32 * kGather; f0 < ntot; f0 += nw * 32 * kGather) {
+        int rr = 0;
+        {
+          int hi = nt - 1;
+          while (rr < hi) {
+            const int mid = (rr + hi + 1) >> 1;
+            if (S.t.tpre[mid] <= f0) rr = mid;
+            else hi = mid - 1;
+          }
+        }
         int cj[kGather], tt[kGather], pid[kGather];
         float4 p[kGather];
 #pragma unroll
-        for (int r = 0; r < kGather; ++r) {
-          const int f = base + r * blockDim.x + tid;
-          cj[r] = -1;
-          tt[r] = 0;
+        for (int u = 0; u < kGather; ++u) {
+          const int f = f0 + u * 32 + lane;
+          cj[u] = -1;
+          tt[u] = 0;
           if (f < ntot) {
-            int lo = 0, hi = nt - 1;
-            while (lo < hi) {
-              const int mid = (lo + hi + 1) >> 1;
-              if (S.t.tpre[mid] <= f) lo = mid;
-              else hi = mid - 1;
-            }
-            tt[r] = lo;
-            cj[r] = S.t.tbeg[lo] + (f - S.t.tpre[lo]);
+            while (S.t.tpre[rr + 1] <= f) ++rr;
+            tt[u] = rr;
+            cj[u] = S.t.tbeg[rr] + (f - S.t.tpre[rr]);
           }
         }
 #pragma unroll
-        for (int r = 0; r < kGather; ++r) {
-          p[r] = cj[r] >= 0 ? g.spos[cj[r]] : make_float4(0.f, 0.f, 0.f, 0.f);
-          pid[r] = cj[r] >= 0 ? __ldg(g.perm + cj[r]) : 0;
+        for (int u = 0; u < kGather; ++u) {
+          p[u] = cj[u] >= 0 ? g.spos[cj[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+          pid[u] = cj[u] >= 0 ? __ldg(g.perm + cj[u]) : 0;
         }
 #pragma unroll
-        for (int r = 0; r < kGather; ++r) {
+        for (int u = 0; u < kGather; ++u) {
           bool keep = false;
-          if (cj[r] >= 0) {
-            const unsigned code = S.t.tcode[tt[r]];
+          if (cj[u] >= 0) {
+            const unsigned code = S.t.tcode[tt[u]];
             if (code & 64u) {
-              p[r].x = __int_as_float(0x7fc00000);   // outside cell: FP64 test for every pair
+              p[u].x = __int_as_float(0x7fc00000);   // outside cell: FP64 test for every pair
               keep = true;
             } else {
-              if (code & 3u) p[r].x += (code & 1u) ? g.Lx : -g.Lx;
-              if (code & 12u) p[r].y += (code & 4u) ? g.Ly : -g.Ly;
-              if (code & 48u) p[r].z += (code & 16u) ? g.Lz : -g.Lz;
-              const float ux = (p[r].x - g.ox) * g.inv_s - (float)cx;
-              const float uy = (p[r].y - g.oy) * g.inv_s - (float)cy;
-              const float uz = (p[r].z - g.oz) * g.inv_s - (float)cz;
+              if (code & 3u) p[u].x += (code & 1u) ? g.Lx : -g.Lx;
+              if (code & 12u) p[u].y += (code & 4u) ? g.Ly : -g.Ly;
+              if (code & 48u) p[u].z += (code & 16u) ? g.Lz : -g.Lz;
+              const float ux = (p[u].x - g.ox) * g.inv_s - (float)cx;
+              const float uy = (p[u].y - g.oy) * g.inv_s - (float)cy;
+              const float uz = (p[u].z - g.oz) * g.inv_s - (float)cz;
               const float gx = fmaxf(fmaxf(-ux, ux - 1.f), 0.f);
               const float gy = fmaxf(fmaxf(-uy, uy - 1.f), 0.f);
               const float gz = fmaxf(fmaxf(-uz, uz - 1.f), 0.f);
@@ -221,18 +268,18 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
           wbase = __shfl_sync(0xffffffffu, wbase, 0);
           if (keep) {
             const int at = wbase + __popc(m & lt_mask);
-            if (at < kCellCap) {
-              float4 cp = p[r];
-              cp.w = __int_as_float(cj[r]);
+            if (at < kCap) {
+              float4 cp = p[u];
+              cp.w = __int_as_float(cj[u]);
               S.c[at] = cp;
-              S.sid[at] = pid[r];
-              atomicAdd(&S.bstart[pid[r] >> bshift], 1);
+              S.sid[at] = pid[u];
+              atomicAdd(&S.bstart[pid[u] >> bshift], 1);
             }
           }
         }
       }
       __syncthreads();
-      fits = S.nc <= kCellCap;
+      fits = S.nc <= kCap;
     }
     const int nc = fits ? S.nc : 0;
     const int nchunk = (nc + 31) >> 5;
@@ -242,10 +289,11 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
       const unsigned long long b = atomicAdd(scr_top, (unsigned long long)need);
       S.base = (b + (unsigned long long)need <= (unsigned long long)scr_cap) ? (long long)b : -1ll;
     }
+    bool room = true;
     if (fits) {
       // 3. ascending input index: scan of the bucket counts, scatter, then
       //    each bucket (a handful of keys) sorted by insertion
-      constexpr int kPerB = kBuckets / kCellThreads;
+      constexpr int kPerB = kBuckets / C::kThreads;
       int v[kPerB], sum = 0;
 #pragma unroll
       for (int r = 0; r < kPerB; ++r) {
@@ -260,9 +308,18 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
         S.bcur[tid * kPerB + r] = run;
         run += v[r];
       }
-      fits = S.base >= 0;
+      room = S.base >= 0;
     }
-    if (!fits) {
+    if (!fits && next) {
+      // the larger configuration takes this cell
+      if (tid == 0) {
+        const int o = atomicAdd(next, 1);
+        next[1 + o] = (int)key;
+      }
+      __syncthreads();
+      continue;
+    }
+    if (!fits || !room) {
       // the per-query path takes every query of this cell
       for (int i = tid; i < nq; i += blockDim.x) {
         const int o = atomicAdd(over, 1);
@@ -297,11 +354,11 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
     int *rec_ids = scratch + rec + 1;
     unsigned *rec_masks = reinterpret_cast<unsigned *>(rec_ids + nc);
     if (tid == 0) scratch[rec] = nc;
-    constexpr int kPer = (kCellCap + kCellThreads - 1) / kCellThreads;
+    constexpr int kPer = (kCap + C::kThreads - 1) / C::kThreads;
     float4 rc[kPer];
 #pragma unroll
     for (int r = 0; r < kPer; ++r) {
-      const int k = tid + r * kCellThreads;
+      const int k = tid + r * C::kThreads;
       if (k < nc) {
         const unsigned long long kk = S.key[k];
         rc[r] = S.c[(int)(kk & 0xffffffffull)];
@@ -311,7 +368,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cell(GridDev g, WalkParams 
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kPer; ++r) {
-      const int k = tid + r * kCellThreads;
+      const int k = tid + r * C::kThreads;
       if (k < nc) {
         S.c[k] = rc[r];
         const int ql = __float_as_int(rc[r].w) - qs;
@@ -451,15 +508,28 @@ __global__ void __launch_bounds__(kExpWarps * 32, 8) k_cell_expand(GridDev g, co
   }
 }
 
-si_status launch_cell_pass(const GridDev &g, const WalkParams &P, const Band &B, unsigned flags,
-                           const int *heavy, int *work, int *over, long long *counts, long long *scr_off,
-                           int *scratch, long long scr_cap, unsigned long long *scr_top, cudaStream_t st) {
-  const size_t smem = sizeof(CellSmem);
-  SI_CUDA_TRY(cudaFuncSetAttribute(k_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  SI_KLAUNCH("k_cell", st,
-             k_cell<<<148 * 2, kCellThreads, smem, st>>>(g, P, B, flags, heavy, work, over, counts, scr_off,
-                                                        scratch, scr_cap, scr_top));
+template <class C>
+static si_status launch_cell_cfg(const char *name, const GridDev &g, const WalkParams &P, const Band &B,
+                                 unsigned flags, const int *cells, int *work, int *next, int *over,
+                                 long long *counts, long long *scr_off, int *scratch, long long scr_cap,
+                                 unsigned long long *scr_top, cudaStream_t st) {
+  const size_t smem = sizeof(CellSmem<C>);
+  SI_CUDA_TRY(cudaFuncSetAttribute(k_cell<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SI_KLAUNCH(name, st,
+             k_cell<C><<<148 * C::kMinBlocks, C::kThreads, smem, st>>>(g, P, B, flags, cells, work, next, over,
+                                                                      counts, scr_off, scratch, scr_cap, scr_top));
   return SI_OK;
+}
+
+si_status launch_cell_pass(const GridDev &g, const WalkParams &P, const Band &B, unsigned flags,
+                           const int *heavy, int *big, int *work, int *over, long long *counts,
+                           long long *scr_off, int *scratch, long long scr_cap, unsigned long long *scr_top,
+                           cudaStream_t st) {
+  si_status s = launch_cell_cfg<CellSmall>("k_cell", g, P, B, flags, heavy, work, big, over, counts, scr_off,
+                                           scratch, scr_cap, scr_top, st);
+  if (s != SI_OK) return s;
+  return launch_cell_cfg<CellLarge>("k_cell_large", g, P, B, flags, big, work + 1, nullptr, over, counts,
+                                    scr_off, scratch, scr_cap, scr_top, st);
 }
 
 si_status launch_cell_expand(const GridDev &g, const int *heavy, const long long *scr_off, const int *scratch,

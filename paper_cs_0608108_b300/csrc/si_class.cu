@@ -108,6 +108,23 @@ void build_class_tables(const Lattice &lat, double dg, int q, std::vector<unsign
 
 using namespace si;
 
+// Cell-level rows for the heavy-cell kernel: the class table of the whole
+// cell (q = 1), i.e. the x-row runs of every cell within d of the query
+// cell, which are the cells with b^2 <= floor(d^2) (Sec. II.A).
+bool si_grid::ensure_cell_rows(float dg, cudaStream_t st) {
+  if (crow_dg == dg) return true;
+  std::vector<int> begin;
+  build_class_tables(lat, (double)dg, 1, crow_host, begin);
+  if ((int64_t)crow_host.size() > crow_cap) return false;
+  if (cudaMemcpyAsync(crow, crow_host.data(), crow_host.size() * sizeof(unsigned long long),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return false;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return false;
+  n_crow = (int)crow_host.size();
+  crow_dg = dg;
+  return true;
+}
+
 // Make the grid's class tables match grown distance dg (cell units); returns
 // false when they cannot (capacity), in which case the Eq. 2 walk is used.
 bool si_grid::ensure_classes(float dg, cudaStream_t st) {

@@ -349,6 +349,8 @@ void fill_griddev(const Lattice &lat, const DevTables &t, GridDev &g) {
   g.cls = nullptr;
   g.cls_begin = nullptr;
   g.cls_q = 0;
+  g.crow = nullptr;
+  g.n_crow = 0;
   g.rows = t.rows;
   g.n_rows = t.n_rows;
   g.row_lim_x = t.row_lim_x;
@@ -464,8 +466,8 @@ __global__ void __launch_bounds__(256) k_cell_order(const int *__restrict__ star
                                                     const float4 *__restrict__ pos, float4 *spos,
                                                     int *perm, int *bigq, unsigned char *__restrict__ cell_cls,
                                                     unsigned char *__restrict__ slot_cls, int *__restrict__ heavy,
-                                                    int *__restrict__ dense, int *__restrict__ light, int wx,
-                                                    int wy, int wz) {
+                                                    int *__restrict__ heavy_big, int *__restrict__ dense,
+                                                    int *__restrict__ light, int wx, int wy, int wz) {
   __shared__ int scan[8];
   __shared__ int light_base;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -479,9 +481,13 @@ __global__ void __launch_bounds__(256) k_cell_order(const int *__restrict__ star
     cell_cls[c] = (unsigned char)k;
     if (m <= kOrderLocal)
       for (int i = 0; i < m; ++i) slot_cls[b + i] = (unsigned char)k;
-    if (k == kCellHeavy) {
+    if (k == kCellHeavy || k == kCellHeavyBig) {
       const int slot = atomicAdd(heavy, 1);
       heavy[1 + slot] = c;
+      if (k == kCellHeavyBig) {
+        const int sb = atomicAdd(heavy_big, 1);
+        heavy_big[1 + sb] = c;
+      }
     } else if (k == kCellDense) {
       const int slot = atomicAdd(dense, m);
       for (int i = 0; i < m; ++i) dense[1 + slot + i] = b + i;
@@ -576,14 +582,14 @@ __global__ void __launch_bounds__(512) k_cell_order_huge(const int *__restrict__
 
 si_status order_cells(const int *start, int64_t n_cells, const float4 *pos, float4 *spos, int *perm,
                       int *bigq, int *hugeq, unsigned char *cell_cls, unsigned char *slot_cls, int *heavy,
-                      int *dense, int *light, const int w[3], cudaStream_t st) {
+                      int *heavy_big, int *dense, int *light, const int w[3], cudaStream_t st) {
   SI_CUDA_TRY(cudaMemsetAsync(bigq, 0, sizeof(int), st));
   SI_CUDA_TRY(cudaMemsetAsync(hugeq, 0, sizeof(int), st));
   SI_KLAUNCH("k_cell_order", st,
              k_cell_order<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(start, (int)n_cells, pos, spos,
                                                                               perm, bigq, cell_cls, slot_cls,
-                                                                              heavy, dense, light, w[0], w[1],
-                                                                              w[2]));
+                                                                              heavy, heavy_big, dense, light,
+                                                                              w[0], w[1], w[2]));
   const size_t wsm = (size_t)kOrderWarps * kOrderWarpCap * sizeof(int);
   SI_CUDA_TRY(cudaFuncSetAttribute(k_cell_order_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
   SI_KLAUNCH("k_cell_order_big", st,
@@ -613,6 +619,8 @@ si::GridDev si_grid::dev() const {
   g.cls = cls;
   g.cls_begin = cls_begin;
   g.cls_q = cls_q;
+  g.crow = crow;
+  g.n_crow = n_crow;
   return g;
 }
 
@@ -631,6 +639,8 @@ static void grid_free(si_grid *g) {
   cudaFree(g->longq);
   cudaFree(g->hugeq);
   cudaFree(g->heavy);
+  cudaFree(g->heavy_big);
+  cudaFree(g->heavy_big_built);
   cudaFree(g->over);
   cudaFree(g->denseq);
   cudaFree(g->lightq);
@@ -641,6 +651,7 @@ static void grid_free(si_grid *g) {
   cudaFree(g->partial);
   cudaFree(g->cls);
   cudaFree(g->cls_begin);
+  cudaFree(g->crow);
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
   free_tables(g->tables);
   delete g;
@@ -690,6 +701,8 @@ extern "C" si_status si_grid_create(const si_grid_desc *desc, int64_t n_capacity
   SI_ALLOC(g->longq, (cap1 + 1) * sizeof(int));
   SI_ALLOC(g->hugeq, (cap1 + 1) * sizeof(int));
   SI_ALLOC(g->heavy, (cap1 / kHeavyMinDense + 2) * sizeof(int));
+  SI_ALLOC(g->heavy_big, (cap1 / kHeavyMinDense + 2) * sizeof(int));
+  SI_ALLOC(g->heavy_big_built, sizeof(int));
   SI_ALLOC(g->over, (cap1 + 1) * sizeof(int));
   SI_ALLOC(g->denseq, (cap1 + 1) * sizeof(int));
   SI_ALLOC(g->lightq, (cap1 + 1) * sizeof(int));
@@ -719,6 +732,16 @@ extern "C" si_status si_grid_create(const si_grid_desc *desc, int64_t n_capacity
     if (e != cudaSuccess) {
       grid_free(g);
       return cuda_fail(e, "cudaMalloc (class tables)");
+    }
+  }
+  // cell-level rows: at most (2 reach + 1)^2 for the largest distance
+  {
+    const int reach = (int)std::floor(std::sqrt((double)g->lat.n_max + 1.0)) + 2;
+    g->crow_cap = (int64_t)(2 * reach + 1) * (2 * reach + 1);
+    e = cudaMalloc((void **)&g->crow, g->crow_cap * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+      grid_free(g);
+      return cuda_fail(e, "cudaMalloc (cell rows)");
     }
   }
   e = cudaMemset(g->status, 0, sizeof(int));
@@ -754,6 +777,7 @@ extern "C" si_status si_grid_build(si_grid *g, const float *d_pos, int64_t n, vo
   SI_CUDA_TRY(cudaMemsetAsync(g->heavy, 0, sizeof(int), st));
   SI_CUDA_TRY(cudaMemsetAsync(g->denseq, 0, sizeof(int), st));
   SI_CUDA_TRY(cudaMemsetAsync(g->lightq, 0, sizeof(int), st));
+  SI_CUDA_TRY(cudaMemsetAsync(g->heavy_big, 0, sizeof(int), st));
   si_status s = scan_inclusive_i32(g->cell_count, g->cell_start + 1, g->n_cells, g->scan_i32, st);
   if (s != SI_OK) return s;
   if (n > 0) {
@@ -761,9 +785,11 @@ extern "C" si_status si_grid_build(si_grid *g, const float *d_pos, int64_t n, vo
         (const float4 *)d_pos, (int)n, g->key_slot, g->cell_start, g->spos, g->perm));
     // the query kernels are idle during a build: their queues serve as scratch
     s = order_cells(g->cell_start, g->n_cells, (const float4 *)d_pos, g->spos, g->perm, g->longq, g->hugeq,
-                    g->cell_cls, g->slot_cls, g->heavy, g->denseq, g->lightq, g->lat.w,
+                    g->cell_cls, g->slot_cls, g->heavy, g->heavy_big, g->denseq, g->lightq, g->lat.w,
                     st);
     if (s != SI_OK) return s;
+    // the radius query appends the cells that overflow the small cell kernel
+    SI_CUDA_TRY(cudaMemcpyAsync(g->heavy_big_built, g->heavy_big, sizeof(int), cudaMemcpyDeviceToDevice, st));
   }
   return SI_OK;
 }

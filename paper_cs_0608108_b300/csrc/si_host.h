@@ -139,7 +139,9 @@ struct si_grid {
   int *status = nullptr;         // device status word
   int *longq = nullptr;          // cap + 1: [0] = count, then query ids of long lists
   int *hugeq = nullptr;          // cap + 1: lists too long for a warp sort
-  int *heavy = nullptr;          // [0] = count, then cells with >= kHeavyMin points (set by build)
+  int *heavy = nullptr;          // [0] = count, then heavy cells (heavy_cell; set by build)
+  int *heavy_big = nullptr;      // [0] = count, then heavy cells for the large cell kernel (build + overflow)
+  int *heavy_big_built = nullptr;   // heavy_big[0] as the build left it
   int *over = nullptr;           // [0] = count, then sorted slots of queries the cell kernel handed back
   int *denseq = nullptr;         // [0] = count, then sorted slots of the queries of dense cells (set by build)
   int *lightq = nullptr;         // [0] = count, then sorted slots of the queries of light cells (set by build)
@@ -161,6 +163,12 @@ struct si_grid {
   std::vector<unsigned long long> cls_host;
   std::vector<int> cls_begin_host;
   bool ensure_classes(float dg, cudaStream_t st);
+  unsigned long long *crow = nullptr;   // cell-level x-row runs (class table with q = 1) for crow_dg
+  int64_t crow_cap = 0;
+  int n_crow = 0;
+  float crow_dg = -1.f;
+  std::vector<unsigned long long> crow_host;
+  bool ensure_cell_rows(float dg, cudaStream_t st);
   double *partial = nullptr;     // reduce partial sums
   int64_t partial_len = 0;
   long long *h_pinned = nullptr; // pinned host scratch (2 values)

@@ -41,7 +41,7 @@ struct GridDev {
   const float4 *spos;        // sorted positions (cell order)
   const int *perm;           // sorted slot -> input index
   const int *cell_start;     // n_cells + 1
-  const unsigned char *cell_cls;   // per non-empty cell: kCellLight / kCellHeavy / kCellDense
+  const unsigned char *cell_cls;   // per non-empty cell: kCellLight / kCellHeavy(Big) / kCellDense
   const unsigned char *slot_cls;   // per sorted slot: its cell's class
   int n;
   float ox, oy, oz;          // region origin
@@ -68,6 +68,8 @@ struct GridDev {
   const unsigned long long *cls;   // entries: unpacked offset | bit 63 = whole cell inside
   const int *cls_begin;            // q^3 + 1
   int cls_q;                       // 0: no class tables
+  const unsigned long long *crow;  // x-row runs of the cells within d of a whole cell (class table with q = 1)
+  int n_crow;
   const RowEntry *rows;            // x-rows sorted by b2 (K-nearest walk)
   int n_rows;
   int row_lim_x;                   // |ox| bound of the rows' x extent
@@ -127,16 +129,19 @@ __device__ __forceinline__ bool heavy_cell(const int *start, unsigned key, unsig
 // Which radius kernels serve a cell's queries, decided once per cell at
 // binning: heavy cells (heavy_cell) one block per cell; dense cells (light,
 // but with at least kDenseN27 points in the 27 cells around them, i.e. long
-// lists) one warp per query; the rest one thread per query.  The outside
-// cell is dense when it holds kDenseN27 points.  Only the work split
+// lists) one warp per query; the rest one thread per query.  Heavy cells
+// with at least kBigN27 points around them are marked for the large
+// configuration of the cell kernel.  The outside cell is dense when it holds
+// kDenseN27 points.  Only the work split
 // depends on it; every path gives the same lists.
-enum : int { kCellLight = 0, kCellHeavy = 1, kCellDense = 2 };
+enum : int { kCellLight = 0, kCellHeavy = 1, kCellDense = 2, kCellHeavyBig = 3 };
 constexpr int kDenseN27 = 24;
+constexpr int kBigN27 = 768;   // heavy cells this crowded go straight to the large cell kernel
 
 __device__ __forceinline__ int cell_class(const int *start, unsigned key, unsigned outside, int wx, int wy,
                                           int wz) {
   if (key >= outside) return __ldg(start + key + 1) - __ldg(start + key) >= kDenseN27 ? kCellDense : kCellLight;
-  if (heavy_cell(start, key, outside)) return kCellHeavy;
+  const bool heavy = heavy_cell(start, key, outside);
   // the 3 x 3 rows of 3 cells around it (y, z wrapped, x clipped)
   const unsigned Gx = 1u << wx, Gy = 1u << wy, Gz = 1u << wz;
   const unsigned x = key & (Gx - 1u), y = (key >> wx) & (Gy - 1u), z = key >> (wx + wy);
@@ -151,6 +156,7 @@ __device__ __forceinline__ int cell_class(const int *start, unsigned key, unsign
       sum += __ldg(start + row + x1 + 1u) - __ldg(start + row + x0);
     }
   }
+  if (heavy) return sum >= kBigN27 ? kCellHeavyBig : kCellHeavy;
   return sum >= kDenseN27 ? kCellDense : kCellLight;
 }
 

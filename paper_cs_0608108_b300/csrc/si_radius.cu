@@ -98,7 +98,7 @@ __device__ __forceinline__ void radius_one(const GridDev &g, const WalkParams &P
                                            int *longq, int *stage = nullptr, int stride = 0) {
   if (skip) {
     const int c = g.slot_cls[s];
-    if ((c == kCellHeavy && (skip & 1u)) || (c == kCellDense && (skip & 2u))) return;
+    if (((c == kCellHeavy || c == kCellHeavyBig) && (skip & 1u)) || (c == kCellDense && (skip & 2u))) return;
   }
   const QueryGeom Q = make_geom(g.spos[s], g);
   const int self = (flags & SI_INCLUDE_SELF) ? -1 : s;
@@ -591,10 +591,10 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   const int walk = cube ? kWalkCube
                         : ((!(flags & SI_WALK_PAPER) && g->ensure_classes(P.dg, st)) ? kWalkClasses
                                                                                     : kWalkPaper);
+  // the cell path holds the runs of the whole cell-level sphere (rows of
+  // cells with b^2 <= floor(d^2), at most two runs per row and the outside cell)
+  const bool heavy = !cube && g->ensure_cell_rows(P.dg, st) && 2 * g->n_crow + 1 <= kCellTCap;
   const GridDev dv = g->dev();
-  // the cell path holds the whole cell-level sphere (entries with b^2 <= n)
-  const int n_tab = std::min((int)std::floor((double)P.dg * (double)P.dg), g->tables.n_max);
-  const bool heavy = !cube && n_tab >= 0 && g->tab_end_host[n_tab] <= kCellTCap;
   const unsigned skip = (heavy ? 1u : 0u) | (dense_path(walk, g) ? 2u : 0u);
   long long *off = (long long *)d_offsets;
   const unsigned blocks = (unsigned)((m + kQueryThreads - 1) / kQueryThreads);
@@ -606,6 +606,7 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
     SI_CUDA_TRY(cudaMemsetAsync(off, 0, sizeof(long long), st));
     SI_CUDA_TRY(cudaMemsetAsync(g->counters, 0, kCounterInts * sizeof(int), st));
     SI_CUDA_TRY(cudaMemsetAsync(g->over, 0, sizeof(int), st));
+    SI_CUDA_TRY(cudaMemcpyAsync(g->heavy_big, g->heavy_big_built, sizeof(int), cudaMemcpyDeviceToDevice, st));
     SI_CUDA_TRY(cudaMemsetAsync(g->scr_top, 0, sizeof(unsigned long long), st));
     if (m == 0) return SI_OK;
     si_status r;
@@ -616,7 +617,7 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
         (r = launch_dense<false>(g, dv, P, B, flags, off + 1, nullptr, nullptr, 0, nullptr, st)) != SI_OK)
       return r;
     if (heavy) {
-      if ((r = launch_cell_pass(dv, P, B, flags, g->heavy, g->counters, g->over, off + 1, g->scr_off,
+      if ((r = launch_cell_pass(dv, P, B, flags, g->heavy, g->heavy_big, g->counters, g->over, off + 1, g->scr_off,
                                 g->scratch, g->scr_cap, g->scr_top, st)) != SI_OK)
         return r;
       SI_KLAUNCH("k_radius_over_count", st,
