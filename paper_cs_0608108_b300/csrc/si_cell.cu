@@ -49,7 +49,7 @@ struct CellCfg {
   static constexpr int kBucketBits = BUCKETS == 1024 ? 10 : (BUCKETS == 512 ? 9 : 8);
   static_assert((1 << kBucketBits) == BUCKETS, "bucket count must be 256, 512 or 1024");
 };
-using CellSmall = CellCfg<256, 1280, 256, 512, 4>;
+using CellSmall = CellCfg<256, 1280, 128, 512, 4>;
 using CellLarge = CellCfg<kCellThreads, kCellCap, kCellMaxQ, 1024, 2>;
 
 template <class C>
@@ -65,7 +65,8 @@ struct CellSmem {
     int tpre[kCellTCap + 1];
     unsigned char tcode[kCellTCap];
   } t;
-  float4 q[C::kMaxQ];                      // the cell's query points; w = own position among the candidates
+  float4 qa[C::kMaxQ];                     // the cell's query points as FP32x2 pairs: (x, x, y, y)
+  float4 qb[C::kMaxQ];                     // (z, z, own position among the candidates, -)
   int qcnt[C::kMaxQ];                      // hits per query
   int scan[C::kThreads / 32];
   long long base;                          // the cell's record in the scratch buffer (-1: no room)
@@ -74,26 +75,12 @@ struct CellSmem {
 
 size_t cell_smem_bytes() { return sizeof(CellSmem<CellLarge>); }
 
-// Packed FP32 pairs (low half = first value) and the squared distance of
-// two candidates to one query with f32x2 instructions.
+// Packed FP32 pairs (low half = first value) for f32x2 instructions.
 __device__ __forceinline__ unsigned long long pack2(float a, float b) {
   return ((unsigned long long)__float_as_uint(b) << 32) | (unsigned long long)__float_as_uint(a);
 }
 __device__ __forceinline__ float lo_half(unsigned long long v) { return __uint_as_float((unsigned)v); }
 __device__ __forceinline__ float hi_half(unsigned long long v) { return __uint_as_float((unsigned)(v >> 32)); }
-
-__device__ __forceinline__ unsigned long long dist2_x2(unsigned long long X, unsigned long long Y,
-                                                       unsigned long long Z, const float4 &q) {
-  const unsigned long long qx = pack2(q.x, q.x), qy = pack2(q.y, q.y), qz = pack2(q.z, q.z);
-  unsigned long long dx, dy, dz, d2;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(X), "l"(qx));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(Y), "l"(qy));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(Z), "l"(qz));
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d2) : "l"(dx), "l"(dx));
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d2) : "l"(dy), "l"(dy), "l"(d2));
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d2) : "l"(dz), "l"(dz), "l"(d2));
-  return d2;
-}
 
 // Scratch reference of a heavy query: its cell's record and its index there.
 __device__ __forceinline__ long long cell_ref(long long rec, int ql) { return (rec << kQlBits) | ql; }
@@ -145,7 +132,9 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
     bool fits = nq <= C::kMaxQ;
     if (fits)
       for (int i = tid; i < nq; i += blockDim.x) {
-        S.q[i] = g.spos[qs + i];
+        const float4 q = g.spos[qs + i];
+        S.qa[i] = make_float4(q.x, q.x, q.y, q.y);
+        S.qb[i] = make_float4(q.z, q.z, __int_as_float(-1), 0.f);
         S.qcnt[i] = 0;
       }
     __syncthreads();
@@ -372,19 +361,19 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
       if (k < nc) {
         S.c[k] = rc[r];
         const int ql = __float_as_int(rc[r].w) - qs;
-        if (!incl_self && ql >= 0 && ql < nq) S.q[ql].w = __int_as_float(k);
+        if (!incl_self && ql >= 0 && ql < nq) S.qb[ql].z = __int_as_float(k);
       }
     }
-    if (incl_self)
-      for (int i = tid; i < nq; i += blockDim.x) S.q[i].w = __int_as_float(-1);
     __syncthreads();
-    // 4. tests.  Items (two chunks of 32 candidates, group of queries) are
-    //    spread over all warps; a lane holds candidates k and k + 32 and runs
-    //    both distances at once with packed FP32x2 arithmetic (the same
-    //    round-to-nearest operations, in the same order, as the scalar path).
-    //    A query's own position is never a hit.
+    // 4. tests.  Items (two chunks of 32 candidates, group of at most 16
+    //    queries) are spread over all warps; a lane holds candidates k and
+    //    k + 32 and runs both distances at once with packed FP32x2 arithmetic
+    //    (the same round-to-nearest operations, in the same order, as the
+    //    scalar path).  Pairs inside the guard band are decided in FP64.  A
+    //    query's own position is never a hit.  Lanes 2i and 2i + 1 keep the
+    //    two masks of the group's i-th query and store them together.
     const int npair = (nchunk + 1) >> 1;
-    const int qsz = max(1, min(nq, (nq * npair + 2 * nw - 1) / (2 * nw)));
+    const int qsz = max(1, min(min(nq, 16), (nq * npair + 2 * nw - 1) / (2 * nw)));
     const int ngrp = (nq + qsz - 1) / qsz;
     const int nitems = npair * ngrp;
     for (int it = wid; it < nitems; it += nw) {
@@ -394,25 +383,37 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
       const float4 c0 = k0 < nc ? S.c[k0] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
       const float4 c1 = k1 < nc ? S.c[k1] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
       const unsigned long long X = pack2(c0.x, c1.x), Y = pack2(c0.y, c1.y), Z = pack2(c0.z, c1.z);
-      const int ch0 = 2 * cp, ch1 = 2 * cp + 1;
-      const int q_end = min(nq, (grp + 1) * qsz);
-      for (int ql = grp * qsz; ql < q_end; ++ql) {
-        const float4 q = S.q[ql];
-        const int own = __float_as_int(q.w);
-        const unsigned long long D2 = dist2_x2(X, Y, Z, q);
+      const int q0 = grp * qsz, q_end = min(nq, q0 + qsz);
+      unsigned mine = 0u;
+      for (int ql = q0; ql < q_end; ++ql) {
+        const float4 qa = S.qa[ql], qb = S.qb[ql];
+        unsigned long long dx, dy, dz, D2;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(X), "l"(pack2(qa.x, qa.y)));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(Y), "l"(pack2(qa.z, qa.w)));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(Z), "l"(pack2(qb.x, qb.y)));
+        asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(D2) : "l"(dx), "l"(dx));
+        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D2) : "l"(dy), "l"(dy), "l"(D2));
+        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D2) : "l"(dz), "l"(dz), "l"(D2));
         const float d0 = lo_half(D2), d1 = hi_half(D2);
         bool h0 = d0 <= B.lo_w, h1 = d1 <= B.lo_w;
-        if (!h0 && !(d0 > B.hi_w) && k0 < nc) h0 = canon_d2(q, g.spos[__float_as_int(c0.w)], g) <= B.r2;
-        if (!h1 && !(d1 > B.hi_w) && k1 < nc) h1 = canon_d2(q, g.spos[__float_as_int(c1.w)], g) <= B.r2;
+        const bool u0 = !h0 && !(d0 > B.hi_w), u1 = !h1 && !(d1 > B.hi_w);
+        if (__any_sync(0xffffffffu, u0 || u1)) {
+          const float4 q = make_float4(qa.x, qa.z, qb.x, 0.f);
+          if (u0 && k0 < nc) h0 = canon_d2(q, g.spos[__float_as_int(c0.w)], g) <= B.r2;
+          if (u1 && k1 < nc) h1 = canon_d2(q, g.spos[__float_as_int(c1.w)], g) <= B.r2;
+        }
+        const int own = __float_as_int(qb.z);
         const unsigned m0 = __ballot_sync(0xffffffffu, h0 && k0 != own);
         const unsigned m1 = __ballot_sync(0xffffffffu, h1 && k1 != own);
-        if (lane == 0) {
-          rec_masks[ql * nchunk + ch0] = m0;
-          if (ch1 < nchunk) rec_masks[ql * nchunk + ch1] = m1;
-          const int c = __popc(m0) + __popc(m1);
-          if (c) atomicAdd(&S.qcnt[ql], c);
-        }
+        const int slot = 2 * (ql - q0);
+        if (lane == slot) mine = m0;
+        if (lane == slot + 1) mine = m1;
       }
+      const int qi = q0 + (lane >> 1), ch = 2 * cp + (lane & 1);
+      if (qi < q_end && ch < nchunk) rec_masks[qi * nchunk + ch] = mine;
+      int c = __popc(mine);
+      c += __shfl_xor_sync(0xffffffffu, c, 1);
+      if ((lane & 1) == 0 && qi < q_end && c) atomicAdd(&S.qcnt[qi], c);
     }
     __syncthreads();
     for (int i = tid; i < nq; i += blockDim.x) {
