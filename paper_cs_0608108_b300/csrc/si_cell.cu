@@ -36,9 +36,6 @@
 
 namespace si {
 
-constexpr int kQlBits = 9;   // query index inside its cell in a scratch reference
-static_assert(kCellMaxQ <= (1 << kQlBits), "query index field too narrow");
-
 template <int THREADS, int CAP, int MAXQ, int BUCKETS, int MINB>
 struct CellCfg {
   static constexpr int kThreads = THREADS;   // block size
@@ -82,9 +79,6 @@ __device__ __forceinline__ unsigned long long pack2(float a, float b) {
 __device__ __forceinline__ float lo_half(unsigned long long v) { return __uint_as_float((unsigned)v); }
 __device__ __forceinline__ float hi_half(unsigned long long v) { return __uint_as_float((unsigned)(v >> 32)); }
 
-// Scratch reference of a heavy query: its cell's record and its index there.
-__device__ __forceinline__ long long cell_ref(long long rec, int ql) { return (rec << kQlBits) | ql; }
-
 // cells: [0] = count, then cell keys; next (nullable): where cells that do
 // not fit go (else the per-query path takes them).
 template <class C>
@@ -92,7 +86,7 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
                                                                     unsigned flags, const int *__restrict__ cells,
                                                                     int *work, int *next, int *__restrict__ over,
                                                                     long long *__restrict__ counts,
-                                                                    long long *__restrict__ scr_off,
+                                                                    long long *__restrict__ cell_rec,
                                                                     int *__restrict__ scratch, long long scr_cap,
                                                                     unsigned long long *scr_top) {
   constexpr int kBuckets = C::kBuckets;
@@ -313,8 +307,8 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
       for (int i = tid; i < nq; i += blockDim.x) {
         const int o = atomicAdd(over, 1);
         over[1 + o] = qs + i;
-        scr_off[__ldg(g.perm + qs + i)] = -1;
       }
+      if (tid == 0) cell_rec[key] = -1;
       __syncthreads();
       continue;
     }
@@ -416,29 +410,27 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
       if ((lane & 1) == 0 && qi < q_end && c) atomicAdd(&S.qcnt[qi], c);
     }
     __syncthreads();
-    for (int i = tid; i < nq; i += blockDim.x) {
-      const int id = __ldg(g.perm + qs + i);
-      counts[id] = S.qcnt[i];
-      scr_off[id] = cell_ref(rec, i);
-    }
+    for (int i = tid; i < nq; i += blockDim.x) counts[__ldg(g.perm + qs + i)] = S.qcnt[i];
+    if (tid == 0) cell_rec[key] = rec;
   }
 }
 
 // After the prefix sum: every heavy query's masks expanded into its ids at
 // their place in the output.  A block per heavy cell: the cell's ordered ids
 // are staged in shared memory (32 per row, rows padded to 33 words so that
-// lanes reading different rows fall in different banks); each warp takes
-// every kExpWarps-th query of the cell.  For 32 masks at a time, lane j takes
-// the j-th, and writes the ids of its set bits, ascending, into the warp's
-// shared buffer after the hits of the masks before it; the warp then stores
-// the buffer to the output with contiguous stores.  Output offsets and mask
-// rows of up to 32 queries are fetched at once, and the next masks are
-// loaded while the current ones are expanded.
+// lanes reading the same position of different rows fall in different
+// banks); each warp takes every kExpWarps-th query of the cell (a query's
+// masks are row `slot - first slot` of the record).  For 32 masks at a time,
+// lane j takes the j-th and, over its 32 bit positions in turn, appends the
+// ids of the set bits to the warp's shared buffer after the hits of the masks
+// before it; the warp then stores the buffer contiguously.  Output offsets of
+// up to 32 queries are fetched at once, and the next masks are loaded while
+// the current ones are expanded.
 constexpr int kExpWarps = 4;
 constexpr int kExpRows = (kCellCap + 31) / 32;
 
 __global__ void __launch_bounds__(kExpWarps * 32, 8) k_cell_expand(GridDev g, const int *__restrict__ heavy,
-                                                                   const long long *__restrict__ scr_off,
+                                                                   const long long *__restrict__ cell_rec,
                                                                    const int *__restrict__ scratch,
                                                                    const long long *__restrict__ offsets,
                                                                    int *__restrict__ ids, long long cap) {
@@ -454,10 +446,8 @@ __global__ void __launch_bounds__(kExpWarps * 32, 8) k_cell_expand(GridDev g, co
   for (int item = blockIdx.x; item < nheavy; item += gridDim.x) {
     const unsigned key = (unsigned)heavy[1 + item];
     const int qs = __ldg(g.cell_start + key), qe = __ldg(g.cell_start + key + 1);
-    // every query of a cell has a reference into the same record, or none
-    const long long ref0 = scr_off[__ldg(g.perm + qs)];
-    if (ref0 < 0) continue;   // served by the per-query path (the same for the whole block)
-    const long long rec = ref0 >> kQlBits;
+    const long long rec = cell_rec[key];
+    if (rec < 0) continue;   // served by the per-query path (the same for the whole block)
     const int nc = __ldg(scratch + rec);
     const int nchunk = (nc + 31) >> 5;
     const int *rec_ids = scratch + rec + 1;
@@ -467,22 +457,17 @@ __global__ void __launch_bounds__(kExpWarps * 32, 8) k_cell_expand(GridDev g, co
     __syncthreads();
     const int nmine = (qe - qs - wid + kExpWarps - 1) / kExpWarps;   // this warp's queries
     for (int i0 = 0; i0 < nmine; i0 += 32) {
-      int qlv = 0;
       long long dstv = 0;
-      if (i0 + lane < nmine) {
-        const int id = __ldg(g.perm + qs + wid + kExpWarps * (i0 + lane));
-        qlv = (int)(scr_off[id] & ((1 << kQlBits) - 1));
-        dstv = offsets[id];
-      }
+      if (i0 + lane < nmine) dstv = offsets[__ldg(g.perm + qs + wid + kExpWarps * (i0 + lane))];
       const int nb = min(32, nmine - i0);
-      int qn = __shfl_sync(0xffffffffu, qlv, 0);
+      int qn = wid + kExpWarps * i0;   // index of the query in its cell = row of its masks
       unsigned mnext = lane < nchunk ? __ldg(rec_masks + (long long)qn * nchunk + lane) : 0u;
       for (int j = 0; j < nb; ++j) {
         const int qj = qn;
         long long wpos = __shfl_sync(0xffffffffu, dstv, j);
-        if (j + 1 < nb) qn = __shfl_sync(0xffffffffu, qlv, j + 1);
+        qn += kExpWarps;
         for (int c0 = 0; c0 < nchunk; c0 += 32) {
-          unsigned mm = mnext;
+          const unsigned mm = mnext;
           // prefetch: the rest of this query's masks, else the next query's first 32
           if (c0 + 32 < nchunk) {
             const int ch = c0 + 32 + lane;
@@ -493,10 +478,12 @@ __global__ void __launch_bounds__(kExpWarps * 32, 8) k_cell_expand(GridDev g, co
           const int cnt = __popc(mm);
           const int inc = warp_incl_scan_i(cnt);
           int o = inc - cnt;
-          const int *row = sids + (c0 + lane) * 33;
-          while (mm) {
-            buf[o++] = row[__ffs(mm) - 1];
-            mm &= mm - 1u;
+          const int *row = sids + (c0 + lane) * 33;   // read only where a bit is set
+#pragma unroll
+          for (int b = 0; b < 32; ++b) {
+            const bool set = (mm >> b) & 1u;
+            if (set) buf[o] = row[b];
+            o += set ? 1 : 0;
           }
           __syncwarp();
           const int tot = __shfl_sync(0xffffffffu, inc, 31);
@@ -512,31 +499,31 @@ __global__ void __launch_bounds__(kExpWarps * 32, 8) k_cell_expand(GridDev g, co
 template <class C>
 static si_status launch_cell_cfg(const char *name, const GridDev &g, const WalkParams &P, const Band &B,
                                  unsigned flags, const int *cells, int *work, int *next, int *over,
-                                 long long *counts, long long *scr_off, int *scratch, long long scr_cap,
+                                 long long *counts, long long *cell_rec, int *scratch, long long scr_cap,
                                  unsigned long long *scr_top, cudaStream_t st) {
   const size_t smem = sizeof(CellSmem<C>);
   SI_CUDA_TRY(cudaFuncSetAttribute(k_cell<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   SI_KLAUNCH(name, st,
              k_cell<C><<<148 * C::kMinBlocks, C::kThreads, smem, st>>>(g, P, B, flags, cells, work, next, over,
-                                                                      counts, scr_off, scratch, scr_cap, scr_top));
+                                                                      counts, cell_rec, scratch, scr_cap, scr_top));
   return SI_OK;
 }
 
 si_status launch_cell_pass(const GridDev &g, const WalkParams &P, const Band &B, unsigned flags,
                            const int *heavy, int *big, int *work, int *over, long long *counts,
-                           long long *scr_off, int *scratch, long long scr_cap, unsigned long long *scr_top,
+                           long long *cell_rec, int *scratch, long long scr_cap, unsigned long long *scr_top,
                            cudaStream_t st) {
-  si_status s = launch_cell_cfg<CellSmall>("k_cell", g, P, B, flags, heavy, work, big, over, counts, scr_off,
+  si_status s = launch_cell_cfg<CellSmall>("k_cell", g, P, B, flags, heavy, work, big, over, counts, cell_rec,
                                            scratch, scr_cap, scr_top, st);
   if (s != SI_OK) return s;
   return launch_cell_cfg<CellLarge>("k_cell_large", g, P, B, flags, big, work + 1, nullptr, over, counts,
-                                    scr_off, scratch, scr_cap, scr_top, st);
+                                    cell_rec, scratch, scr_cap, scr_top, st);
 }
 
-si_status launch_cell_expand(const GridDev &g, const int *heavy, const long long *scr_off, const int *scratch,
+si_status launch_cell_expand(const GridDev &g, const int *heavy, const long long *cell_rec, const int *scratch,
                              const long long *offsets, int *ids, long long cap, cudaStream_t st) {
   SI_KLAUNCH("k_cell_expand", st,
-             k_cell_expand<<<148 * 8, kExpWarps * 32, 0, st>>>(g, heavy, scr_off, scratch, offsets, ids, cap));
+             k_cell_expand<<<148 * 8, kExpWarps * 32, 0, st>>>(g, heavy, cell_rec, scratch, offsets, ids, cap));
   return SI_OK;
 }
 

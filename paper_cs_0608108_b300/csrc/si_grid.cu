@@ -644,7 +644,7 @@ static void grid_free(si_grid *g) {
   cudaFree(g->over);
   cudaFree(g->denseq);
   cudaFree(g->lightq);
-  cudaFree(g->scr_off);
+  cudaFree(g->cell_rec);
   cudaFree(g->scr_top);
   cudaFree(g->scratch);
   cudaFree(g->counters);
@@ -706,7 +706,7 @@ extern "C" si_status si_grid_create(const si_grid_desc *desc, int64_t n_capacity
   SI_ALLOC(g->over, (cap1 + 1) * sizeof(int));
   SI_ALLOC(g->denseq, (cap1 + 1) * sizeof(int));
   SI_ALLOC(g->lightq, (cap1 + 1) * sizeof(int));
-  SI_ALLOC(g->scr_off, cap1 * sizeof(long long));
+  SI_ALLOC(g->cell_rec, g->n_cells * sizeof(long long));
   SI_ALLOC(g->scr_top, sizeof(unsigned long long));
   g->scr_cap = 4 * cap1;
   SI_ALLOC(g->scratch, g->scr_cap * sizeof(int));

@@ -147,7 +147,7 @@ struct si_grid {
   int *lightq = nullptr;         // [0] = count, then sorted slots of the queries of light cells (set by build)
   unsigned char *cell_cls = nullptr;   // per cell: kCellLight / kCellHeavy / kCellDense (set by build)
   unsigned char *slot_cls = nullptr;   // per sorted slot: its cell's class (set by build)
-  long long *scr_off = nullptr;  // per input index: its cell's record and its index there (-1: per-query path)
+  long long *cell_rec = nullptr; // per heavy cell: its record in the scratch buffer (-1: per-query path)
   int *scratch = nullptr;        // cell records (ordered candidate ids, hit masks) written before the prefix sum
   long long scr_cap = 0;
   unsigned long long *scr_top = nullptr;   // bump allocator of the scratch (also the size needed)

@@ -617,7 +617,7 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
         (r = launch_dense<false>(g, dv, P, B, flags, off + 1, nullptr, nullptr, 0, nullptr, st)) != SI_OK)
       return r;
     if (heavy) {
-      if ((r = launch_cell_pass(dv, P, B, flags, g->heavy, g->heavy_big, g->counters, g->over, off + 1, g->scr_off,
+      if ((r = launch_cell_pass(dv, P, B, flags, g->heavy, g->heavy_big, g->counters, g->over, off + 1, g->cell_rec,
                                 g->scratch, g->scr_cap, g->scr_top, st)) != SI_OK)
         return r;
       SI_KLAUNCH("k_radius_over_count", st,
@@ -658,7 +658,7 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
                               g->longq, blocks, st)) != SI_OK)
     return s;
   if (heavy) {
-    if ((s = launch_cell_expand(dv, g->heavy, g->scr_off, g->scratch, off, d_ids, ids_capacity, st)) != SI_OK)
+    if ((s = launch_cell_expand(dv, g->heavy, g->cell_rec, g->scratch, off, d_ids, ids_capacity, st)) != SI_OK)
       return s;
     SI_KLAUNCH("k_radius_over_write", st,
                k_radius_over<true><<<148 * 4, kQueryThreads, 0, st>>>(dv, P, B, flags, g->over, nullptr,

@@ -22,9 +22,9 @@ constexpr int kSortBlockCap = 16384; // lists a block sorts in shared memory
 size_t cell_smem_bytes();
 si_status launch_cell_pass(const GridDev &g, const WalkParams &P, const Band &B, unsigned flags,
                            const int *heavy, int *big, int *work, int *over, long long *counts,
-                           long long *scr_off, int *scratch, long long scr_cap, unsigned long long *scr_top,
+                           long long *cell_rec, int *scratch, long long scr_cap, unsigned long long *scr_top,
                            cudaStream_t st);
-si_status launch_cell_expand(const GridDev &g, const int *heavy, const long long *scr_off, const int *scratch,
+si_status launch_cell_expand(const GridDev &g, const int *heavy, const long long *cell_rec, const int *scratch,
                              const long long *offsets, int *ids, long long cap, cudaStream_t st);
 
 }  // namespace si
