@@ -152,27 +152,45 @@ class RadiusWork:
         for g in self.grids:
             g.sync()
 
-    def heavy_split(self, k):
-        """(fraction of queries, fraction of hits) served by the cell-at-a-time
-        kernels for scene k: queries whose cell holds >= 8 points, or >= 3 with
-        >= 12 points in it and its two x-neighbors (keys key-1..key+1)."""
+    def cell_split(self, k):
+        """Per kernel family, the (fraction of queries, fraction of hits) it
+        serves in scene k, from the cell classes the binning assigns: heavy
+        (>= 8 points, or >= 3 with >= 12 in the cell and its two x-neighbours),
+        large heavy (>= 768 points in the 27 cells around it), dense (not
+        heavy, >= 24 points around it), light (the rest).  Cells that overflow
+        the small configuration at run time are counted as small."""
+        s = self.scenes[k]
         start, _, perm = (t.cpu().numpy() for t in self.grids[k].cell_arrays())
-        cnt = np.diff(start)
-        cnt[-1] = 0                      # the outside cell is never a heavy cell
+        cnt = np.diff(start).astype(np.int64)
         nc = len(cnt) - 1                # lattice cells; key nc is the outside cell
-        row = np.zeros(len(cnt), dtype=np.int64)
+        row = np.zeros(nc + 1, dtype=np.int64)
         if nc >= 3:
             key = np.arange(1, nc - 1)
             row[1:nc - 1] = start[key + 2] - start[key - 1]
         heavy = (cnt >= 8) | ((cnt >= 3) & (row >= 12))
         heavy[-1] = False
-        heavy_slot = np.repeat(heavy, cnt.clip(min=0))[: len(perm)]
+        wx, wy, wz = s.log2_cells
+        c3 = cnt[:nc].reshape(1 << wz, 1 << wy, 1 << wx)
+        xs = c3.copy()
+        xs[:, :, 1:] += c3[:, :, :-1]
+        xs[:, :, :-1] += c3[:, :, 1:]          # x clipped at the region's ends
+        n27 = np.zeros_like(c3)
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                n27 += np.roll(np.roll(xs, dz, 0), dy, 1)   # y, z wrapped
+        n27 = np.append(n27.ravel(), cnt[nc])
+        cls = np.where(heavy, np.where(n27 >= 768, 3, 1), np.where(n27 >= 24, 2, 0))
         if self.method == "cube":
-            heavy_slot[:] = False
+            cls[:] = 0
+        slot_cls = np.repeat(cls, cnt.clip(min=0))[: len(perm)]
         off = self.off[k].cpu().numpy()
         lens = np.diff(off)
-        ids = perm[heavy_slot]
-        return heavy_slot.mean() if len(perm) else 0.0, lens[ids].sum() / max(lens.sum(), 1)
+        tot = max(lens.sum(), 1)
+        out = {}
+        for name, c in (("light", 0), ("small", 1), ("dense", 2), ("large", 3)):
+            sel = slot_cls == c
+            out[name] = (sel.mean() if len(perm) else 0.0, lens[perm[sel]].sum() / tot)
+        return out
 
     def algorithmic_bytes(self):
         """Per-kernel minimum DRAM bytes of one launch, averaged over the scenes:
@@ -180,22 +198,28 @@ class RadiusWork:
         out = {}
         for k, (s, tot) in enumerate(zip(self.scenes, self.totals)):
             n, C = s.n, (1 << sum(s.log2_cells)) + 1
-            fq, ft = self.heavy_split(k)
-            cnt_b = 16 * n + 4 * n + 4 * C + 8 * n
-            wr_b = 16 * n + 4 * n + 4 * C + 8 * n
+            f = self.cell_split(k)
+            fl, fd, fs, fb = (f[c][0] for c in ("light", "dense", "small", "large"))
+            tl, td, ts, tb = (f[c][1] for c in ("light", "dense", "small", "large"))
+            # per-query kernels: the query's point, index and list entry, the
+            # cell starts, the count (count pass) or offset (write pass)
+            q_b = 16 * n + 4 * n + 4 * n + 8 * n
+            # cell kernels: the queries' points and indices, the cell starts,
+            # the counts (the per-cell records in between are not algorithmic)
+            c_b = 16 * n + 4 * n + 8 * n
             per = {
                 "k_bin_key": 16 * n + 8 * n + 8 * C,
                 "k_bin_scatter": 8 * n + 16 * n + 4 * C + 16 * n + 4 * n,
-                "k_radius_count": (1 - fq) * cnt_b,
-                "k_radius_write": (1 - fq) * wr_b + (1 - ft) * 4 * tot,
-                # heavy cells: one pass reads their queries' points, ids and
-                # cell starts and writes their counts and scratch references;
-                # the expansion reads offsets and references and writes the
-                # lists (the per-cell records in between are not algorithmic)
-                "k_cell": fq * (16 * n + 4 * n + 4 * C + 16 * n),
-                "k_cell_expand": fq * (4 * n + 16 * n) + ft * 4 * tot,
-                "k_radius_count_cube": cnt_b,
-                "k_radius_write_cube": wr_b + 4 * tot,
+                "k_radius_count": fl * q_b + fl * 4 * C,
+                "k_radius_write": fl * q_b + fl * 4 * C + tl * 4 * tot,
+                "k_radius_dense_count": fd * q_b + fd * 4 * C,
+                "k_radius_dense_write": fd * q_b + fd * 4 * C + td * 4 * tot,
+                "k_cell": fs * c_b + fs * 4 * C,
+                "k_cell_large": fb * c_b + fb * 4 * C,
+                # the lists of every heavy query, with their offsets and indices
+                "k_cell_expand": (fs + fb) * (4 * n + 8 * n) + (ts + tb) * 4 * tot,
+                "k_radius_count_cube": 16 * n + 4 * n + 4 * C + 8 * n,
+                "k_radius_write_cube": 16 * n + 4 * n + 4 * C + 8 * n + 4 * tot,
             }
             for kk, v in per.items():
                 out.setdefault(kk, []).append(v)
