@@ -127,6 +127,13 @@ class Scene:
     name: str = ""
     extra: dict = field(default_factory=dict)
 
+    def __post_init__(self):
+        # the library takes these as float32: keep the values it will see, so
+        # that both sides of a comparison use the same radius and lattice
+        self.origin = tuple(float(np.float32(o)) for o in self.origin)
+        self.cell_size = float(np.float32(self.cell_size))
+        self.r = float(np.float32(self.r))
+
     @property
     def n(self) -> int:
         return int(self.pos.shape[0])

@@ -29,7 +29,7 @@ def gpu_radius(scene, r=None, method="sphere", include_self=False, sort=True, gr
 
 
 def oracle_radius(scene, r=None, queries=None, include_self=False):
-    r = scene.r if r is None else r
+    r = float(np.float32(scene.r if r is None else r))   # the radius the library receives
     q = np.arange(scene.n) if queries is None else np.asarray(queries)
     self_idx = None if include_self else q
     return oracle.radius(scene.pos, scene.pos[q], scene.box, scene.cyclic_mask, r, self_idx,

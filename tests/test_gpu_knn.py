@@ -22,6 +22,8 @@ def run_knn(scene, k, r_max):
 
 
 def check(scene, k, r_max, ids, d2, cnt, queries):
+    if r_max is not None:
+        r_max = float(np.float32(r_max))   # the radius the library receives
     oi, od, oc = oracle.knn(scene.pos, scene.pos[queries], scene.box, scene.cyclic_mask, k, r_max,
                             queries)
     assert np.array_equal(cnt[queries], oc)
