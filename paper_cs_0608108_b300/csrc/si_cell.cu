@@ -24,10 +24,16 @@
 // k_cell_expand turns every query's masks into its ids at their place in the
 // output.
 // Two configurations: most heavy cells fit a small block (8 warps, 1280
-// candidates, 256 queries, four blocks per SM); a cell that does not is
+// candidates, 128 queries, four blocks per SM); a cell that does not is
 // listed for the large one (16 warps, 2560 candidates, 512 queries), launched
-// after it.  A cell that fits neither, or whose record does not fit the
-// scratch buffer, hands its queries to the per-query path.
+// after it.  The large one splits a cell whose candidates exceed its capacity
+// into slabs of input indices [lo, lo + span): each slab is gathered, sorted
+// and tested on its own, and since every index of a slab is below every
+// index of the next, a query's hits slab after slab are already its sorted
+// list.  A split cell's record is a header (the slab count and each slab
+// record's offset) and one record per slab.  A cell that fits neither, or
+// whose records do not fit the scratch buffer, hands its queries to the
+// per-query path.
 #include <cmath>
 
 #include "si_host.h"
@@ -66,7 +72,8 @@ struct CellSmem {
   float4 qb[C::kMaxQ];                     // (z, z, own position among the candidates, -)
   int qcnt[C::kMaxQ];                      // hits per query
   int scan[C::kThreads / 32];
-  long long base;                          // the cell's record in the scratch buffer (-1: no room)
+  long long base;                          // the slab's record in the scratch buffer (-1: no room)
+  long long hdr;                           // the split cell's header (-1: no room)
   int nt, nc, out_seen, item;
 };
 
@@ -80,7 +87,11 @@ __device__ __forceinline__ float lo_half(unsigned long long v) { return __uint_a
 __device__ __forceinline__ float hi_half(unsigned long long v) { return __uint_as_float((unsigned)(v >> 32)); }
 
 // cells: [0] = count, then cell keys; next (nullable): where cells that do
-// not fit go (else the per-query path takes them).
+// not fit go (else they are split into slabs, or the per-query path takes
+// them).  cell_rec[key]: the record (>= 0), the header of a split cell
+// (-2 - header), or -1 (per-query path).
+constexpr int kMaxSlabs = 256;
+
 template <class C>
 __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, WalkParams P, Band B,
                                                                     unsigned flags, const int *__restrict__ cells,
@@ -91,6 +102,7 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
                                                                     unsigned long long *scr_top) {
   constexpr int kBuckets = C::kBuckets;
   constexpr int kCap = C::kCap;
+  constexpr int kSlabFill = kCap * 3 / 4;   // target candidates per slab (the rest is margin)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CellSmem<C> &S = *reinterpret_cast<CellSmem<C> *>(smem_raw);
   const int nheavy = cells[0];
@@ -98,10 +110,21 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   const float box2 = (P.dg + g.eps) * (P.dg + g.eps);
-  // bucket of an input index: its top bits within [0, n)
-  int idbits = 1;
-  while (idbits < 31 && (1 << idbits) < g.n) ++idbits;
-  const int bshift = max(idbits - C::kBucketBits, 0);
+  const int Gx = 1 << g.wx;
+  const bool cyc_x = g.cyc & 1u;
+  // bucket of an input index: its top bits within the slab's range
+  auto bucket_shift = [&](int range) {
+    int idbits = 1;
+    while (idbits < 31 && (1 << idbits) < range) ++idbits;
+    return max(idbits - C::kBucketBits, 0);
+  };
+  const int bshift_all = bucket_shift(g.n);
+  // reservations are kept even so that headers hold aligned 64-bit offsets
+  auto reserve = [&](long long need) -> long long {
+    need = (need + 1) & ~1ll;
+    const unsigned long long b = atomicAdd(scr_top, (unsigned long long)need);
+    return (b + (unsigned long long)need <= (unsigned long long)scr_cap) ? (long long)b : -1ll;
+  };
   for (;;) {
     if (tid == 0) S.item = atomicAdd(work, 1);
     __syncthreads();
@@ -123,8 +146,8 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
       S.out_seen = 0;
     }
     for (int b = tid; b < kBuckets; b += blockDim.x) S.bstart[b] = 0;
-    bool fits = nq <= C::kMaxQ;
-    if (fits)
+    const bool qfit = nq <= C::kMaxQ;
+    if (qfit)
       for (int i = tid; i < nq; i += blockDim.x) {
         const float4 q = g.spos[qs + i];
         S.qa[i] = make_float4(q.x, q.x, q.y, q.y);
@@ -132,13 +155,12 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
         S.qcnt[i] = 0;
       }
     __syncthreads();
-    if (fits) {
+    int nt = 0, ntot = 0;
+    if (qfit) {
       // 1. runs of the cell-level sphere: each x-row of cells within d of the
       //    query cell (b^2 <= floor(d^2)) is one run of points, or two where
       //    it crosses the cyclic x boundary; rows leaving the region on a
       //    non-cyclic axis stand for the outside cell, listed once
-      const int Gx = 1 << g.wx;
-      const bool cyc_x = g.cyc & 1u;
       auto add_run = [&](unsigned ka, unsigned kb, unsigned code) {
         const int b = __ldg(g.cell_start + ka), c = __ldg(g.cell_start + kb + 1) - b;
         if (c == 0) return;
@@ -176,7 +198,7 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
         if (out && !atomicExch(&S.out_seen, 1)) add_run(g.outside, g.outside, 64u);
       }
       __syncthreads();
-      const int nt = S.nt;
+      nt = S.nt;
       // 2a. prefix of run sizes (one warp)
       if (wid == 0) {
         int run = 0;
@@ -190,20 +212,27 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
         if (lane == 0) S.t.tpre[nt] = run;
       }
       __syncthreads();
-      const int ntot = S.t.tpre[nt];
-      // 2b. gather: candidates within d of the query cell box, in the query
-      //     frame, with their input indices counted into buckets.  A warp
+      ntot = S.t.tpre[nt];
+    }
+    // 2b-4, slab by slab of input indices [lo, hi)
+    int nslab = 1, span = g.n;
+    bool ok = qfit, room = true, split = false;
+    for (int sl = 0; ok && sl < nslab;) {
+      const int lo = sl * span, hi = min(g.n, lo + span);
+      const int bshift = split ? bucket_shift(hi - lo) : bshift_all;
+      // 2b. gather: candidates of the slab within d of the query cell box, in
+      //     the query frame, their indices counted into buckets.  A warp
       //     takes 32 * kGather consecutive candidates: the first one's run by
       //     binary search, the others' by stepping forward.
       constexpr int kGather = 4;
       for (int f0 = wid * 32 * kGather; f0 < ntot; f0 += nw * 32 * kGather) {
         int rr = 0;
         {
-          int hi = nt - 1;
-          while (rr < hi) {
-            const int mid = (rr + hi + 1) >> 1;
+          int top = nt - 1;
+          while (rr < top) {
+            const int mid = (rr + top + 1) >> 1;
             if (S.t.tpre[mid] <= f0) rr = mid;
-            else hi = mid - 1;
+            else top = mid - 1;
           }
         }
         int cj[kGather], tt[kGather], pid[kGather];
@@ -227,7 +256,7 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
 #pragma unroll
         for (int u = 0; u < kGather; ++u) {
           bool keep = false;
-          if (cj[u] >= 0) {
+          if (cj[u] >= 0 && pid[u] >= lo && pid[u] < hi) {
             const unsigned code = S.t.tcode[tt[u]];
             if (code & 64u) {
               p[u].x = __int_as_float(0x7fc00000);   // outside cell: FP64 test for every pair
@@ -255,179 +284,218 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
               float4 cp = p[u];
               cp.w = __int_as_float(cj[u]);
               S.c[at] = cp;
-              S.sid[at] = pid[u];
-              atomicAdd(&S.bstart[pid[u] >> bshift], 1);
+              S.sid[at] = pid[u] - lo;
+              atomicAdd(&S.bstart[(pid[u] - lo) >> bshift], 1);
             }
           }
         }
       }
       __syncthreads();
-      fits = S.nc <= kCap;
-    }
-    const int nc = fits ? S.nc : 0;
-    const int nchunk = (nc + 31) >> 5;
-    // the cell's record: nc, ids, masks
-    if (fits && tid == 0) {
-      const long long need = 1 + (long long)nc + (long long)nq * nchunk;
-      const unsigned long long b = atomicAdd(scr_top, (unsigned long long)need);
-      S.base = (b + (unsigned long long)need <= (unsigned long long)scr_cap) ? (long long)b : -1ll;
-    }
-    bool room = true;
-    if (fits) {
+      const int nc = S.nc;
+      if (nc > kCap) {
+        if (!next && !split) {
+          // the large configuration splits the cell into slabs of indices
+          nslab = (nc + kSlabFill - 1) / kSlabFill;
+          split = true;
+          if (nslab > kMaxSlabs) {
+            ok = false;
+            room = false;
+            break;
+          }
+          span = (g.n + nslab - 1) / nslab;
+          __syncthreads();   // every thread has read S.nc before it is reset
+          if (tid == 0) {
+            S.hdr = reserve(2 + 2ll * nslab);
+            if (S.hdr >= 0) scratch[S.hdr] = nslab;
+            S.nc = 0;
+          }
+          for (int b = tid; b < kBuckets; b += blockDim.x) S.bstart[b] = 0;
+          __syncthreads();
+          if (S.hdr < 0) {
+            ok = false;
+            room = false;
+          }
+          continue;   // slab 0 again, under the new span
+        }
+        ok = false;   // small configuration: the large one takes it; a slab that overflows: per-query path
+        room = !split;
+        break;
+      }
+      const int nchunk = (nc + 31) >> 5;
+      // the slab's record: nc, ids, masks
+      if (tid == 0) {
+        S.base = reserve(1 + (long long)nc + (long long)nq * nchunk);
+        if (split && S.base >= 0) reinterpret_cast<long long *>(scratch + S.hdr + 2)[sl] = S.base;
+      }
       // 3. ascending input index: scan of the bucket counts, scatter, then
       //    each bucket (a handful of keys) sorted by insertion
       constexpr int kPerB = kBuckets / C::kThreads;
-      int v[kPerB], sum = 0;
+      int v[kPerB], bsum = 0;
 #pragma unroll
       for (int r = 0; r < kPerB; ++r) {
         v[r] = S.bstart[tid * kPerB + r];
-        sum += v[r];
+        bsum += v[r];
       }
       int total;
-      int run = block_excl_scan_i(sum, total, S.scan);   // its barriers also publish S.base
+      int run = block_excl_scan_i(bsum, total, S.scan);   // its barriers also publish S.base
 #pragma unroll
       for (int r = 0; r < kPerB; ++r) {
         S.bstart[tid * kPerB + r] = run;
         S.bcur[tid * kPerB + r] = run;
         run += v[r];
       }
-      room = S.base >= 0;
+      if (S.base < 0) {
+        ok = false;
+        room = false;
+        break;
+      }
+      __syncthreads();
+      for (int p = tid; p < nc; p += blockDim.x) {
+        const int id = S.sid[p];
+        S.key[atomicAdd(&S.bcur[id >> bshift], 1)] = ((unsigned long long)(unsigned)id << 32) | (unsigned)p;
+      }
+      __syncthreads();
+      for (int b = tid; b < kBuckets; b += blockDim.x) {
+        const int blo = S.bstart[b], bhi = S.bcur[b];
+        for (int i = blo + 1; i < bhi; ++i) {
+          const unsigned long long x = S.key[i];
+          int p = i;
+          while (p > blo && S.key[p - 1] > x) {
+            S.key[p] = S.key[p - 1];
+            --p;
+          }
+          S.key[p] = x;
+        }
+      }
+      __syncthreads();
+      // permute the candidates into id order; the ordered ids go to the record,
+      // each query notes its own position (if its index is in this slab)
+      const long long rec = S.base;
+      int *rec_ids = scratch + rec + 1;
+      unsigned *rec_masks = reinterpret_cast<unsigned *>(rec_ids + nc);
+      if (tid == 0) scratch[rec] = nc;
+      constexpr int kPer = (kCap + C::kThreads - 1) / C::kThreads;
+      float4 rc[kPer];
+#pragma unroll
+      for (int r = 0; r < kPer; ++r) {
+        const int k = tid + r * C::kThreads;
+        if (k < nc) {
+          const unsigned long long kk = S.key[k];
+          rc[r] = S.c[(int)(kk & 0xffffffffull)];
+          rec_ids[k] = (int)(kk >> 32) + lo;
+        }
+      }
+      __syncthreads();
+      if (split) {   // own positions of this slab only
+        for (int i = tid; i < nq; i += blockDim.x) S.qb[i].z = __int_as_float(-1);
+        __syncthreads();
+      }
+#pragma unroll
+      for (int r = 0; r < kPer; ++r) {
+        const int k = tid + r * C::kThreads;
+        if (k < nc) {
+          S.c[k] = rc[r];
+          const int ql = __float_as_int(rc[r].w) - qs;
+          if (!incl_self && ql >= 0 && ql < nq) S.qb[ql].z = __int_as_float(k);
+        }
+      }
+      __syncthreads();
+      // 4. tests.  Items (two chunks of 32 candidates, group of at most 16
+      //    queries) are spread over all warps; a lane holds candidates k and
+      //    k + 32 and runs both distances at once with packed FP32x2 arithmetic
+      //    (the same round-to-nearest operations, in the same order, as the
+      //    scalar path).  Pairs inside the guard band are decided in FP64.  A
+      //    query's own position is never a hit.  Lanes 2i and 2i + 1 keep the
+      //    two masks of the group's i-th query and store them together.
+      const int npair = (nchunk + 1) >> 1;
+      const int qsz = max(1, min(min(nq, 16), (nq * npair + 2 * nw - 1) / (2 * nw)));
+      const int ngrp = (nq + qsz - 1) / qsz;
+      const int nitems = npair * ngrp;
+      for (int it = wid; it < nitems; it += nw) {
+        const int grp = it / npair;
+        const int cp = it - grp * npair;
+        const int k0 = cp * 64 + lane, k1 = k0 + 32;
+        const float4 c0 = k0 < nc ? S.c[k0] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+        const float4 c1 = k1 < nc ? S.c[k1] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+        const unsigned long long X = pack2(c0.x, c1.x), Y = pack2(c0.y, c1.y), Z = pack2(c0.z, c1.z);
+        const int q0 = grp * qsz, q_end = min(nq, q0 + qsz);
+        unsigned mine = 0u;
+        for (int ql = q0; ql < q_end; ++ql) {
+          const float4 qa = S.qa[ql], qb = S.qb[ql];
+          unsigned long long dx, dy, dz, D2;
+          asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(X), "l"(pack2(qa.x, qa.y)));
+          asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(Y), "l"(pack2(qa.z, qa.w)));
+          asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(Z), "l"(pack2(qb.x, qb.y)));
+          asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(D2) : "l"(dx), "l"(dx));
+          asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D2) : "l"(dy), "l"(dy), "l"(D2));
+          asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D2) : "l"(dz), "l"(dz), "l"(D2));
+          const float d0 = lo_half(D2), d1 = hi_half(D2);
+          bool h0 = d0 <= B.lo_w, h1 = d1 <= B.lo_w;
+          const bool u0 = !h0 && !(d0 > B.hi_w), u1 = !h1 && !(d1 > B.hi_w);
+          if (__any_sync(0xffffffffu, u0 || u1)) {
+            const float4 q = make_float4(qa.x, qa.z, qb.x, 0.f);
+            if (u0 && k0 < nc) h0 = canon_d2(q, g.spos[__float_as_int(c0.w)], g) <= B.r2;
+            if (u1 && k1 < nc) h1 = canon_d2(q, g.spos[__float_as_int(c1.w)], g) <= B.r2;
+          }
+          const int own = __float_as_int(qb.z);
+          const unsigned m0 = __ballot_sync(0xffffffffu, h0 && k0 != own);
+          const unsigned m1 = __ballot_sync(0xffffffffu, h1 && k1 != own);
+          const int slot = 2 * (ql - q0);
+          if (lane == slot) mine = m0;
+          if (lane == slot + 1) mine = m1;
+        }
+        const int qi = q0 + (lane >> 1), ch = 2 * cp + (lane & 1);
+        if (qi < q_end && ch < nchunk) rec_masks[qi * nchunk + ch] = mine;
+        int c = __popc(mine);
+        c += __shfl_xor_sync(0xffffffffu, c, 1);
+        if ((lane & 1) == 0 && qi < q_end && c) atomicAdd(&S.qcnt[qi], c);
+      }
+      __syncthreads();
+      if (++sl < nslab) {   // the next slab starts from empty buckets
+        if (tid == 0) S.nc = 0;
+        for (int b = tid; b < kBuckets; b += blockDim.x) S.bstart[b] = 0;
+        __syncthreads();
+      }
     }
-    if (!fits && next) {
-      // the larger configuration takes this cell
-      if (tid == 0) {
-        const int o = atomicAdd(next, 1);
-        next[1 + o] = (int)key;
+    if (!ok) {
+      if (next && room) {
+        // the larger configuration takes this cell
+        if (tid == 0) {
+          const int o = atomicAdd(next, 1);
+          next[1 + o] = (int)key;
+        }
+      } else {
+        // the per-query path takes every query of this cell
+        for (int i = tid; i < nq; i += blockDim.x) {
+          const int o = atomicAdd(over, 1);
+          over[1 + o] = qs + i;
+        }
+        if (tid == 0) cell_rec[key] = -1;
       }
       __syncthreads();
       continue;
     }
-    if (!fits || !room) {
-      // the per-query path takes every query of this cell
-      for (int i = tid; i < nq; i += blockDim.x) {
-        const int o = atomicAdd(over, 1);
-        over[1 + o] = qs + i;
-      }
-      if (tid == 0) cell_rec[key] = -1;
-      __syncthreads();
-      continue;
-    }
-    __syncthreads();
-    for (int p = tid; p < nc; p += blockDim.x) {
-      const int id = S.sid[p];
-      S.key[atomicAdd(&S.bcur[id >> bshift], 1)] = ((unsigned long long)(unsigned)id << 32) | (unsigned)p;
-    }
-    __syncthreads();
-    for (int b = tid; b < kBuckets; b += blockDim.x) {
-      const int lo = S.bstart[b], hi = S.bcur[b];
-      for (int i = lo + 1; i < hi; ++i) {
-        const unsigned long long x = S.key[i];
-        int p = i;
-        while (p > lo && S.key[p - 1] > x) {
-          S.key[p] = S.key[p - 1];
-          --p;
-        }
-        S.key[p] = x;
-      }
-    }
-    __syncthreads();
-    // permute the candidates into id order; the ordered ids go to the record,
-    // each query notes its own position
-    const long long rec = S.base;
-    int *rec_ids = scratch + rec + 1;
-    unsigned *rec_masks = reinterpret_cast<unsigned *>(rec_ids + nc);
-    if (tid == 0) scratch[rec] = nc;
-    constexpr int kPer = (kCap + C::kThreads - 1) / C::kThreads;
-    float4 rc[kPer];
-#pragma unroll
-    for (int r = 0; r < kPer; ++r) {
-      const int k = tid + r * C::kThreads;
-      if (k < nc) {
-        const unsigned long long kk = S.key[k];
-        rc[r] = S.c[(int)(kk & 0xffffffffull)];
-        rec_ids[k] = (int)(kk >> 32);
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kPer; ++r) {
-      const int k = tid + r * C::kThreads;
-      if (k < nc) {
-        S.c[k] = rc[r];
-        const int ql = __float_as_int(rc[r].w) - qs;
-        if (!incl_self && ql >= 0 && ql < nq) S.qb[ql].z = __int_as_float(k);
-      }
-    }
-    __syncthreads();
-    // 4. tests.  Items (two chunks of 32 candidates, group of at most 16
-    //    queries) are spread over all warps; a lane holds candidates k and
-    //    k + 32 and runs both distances at once with packed FP32x2 arithmetic
-    //    (the same round-to-nearest operations, in the same order, as the
-    //    scalar path).  Pairs inside the guard band are decided in FP64.  A
-    //    query's own position is never a hit.  Lanes 2i and 2i + 1 keep the
-    //    two masks of the group's i-th query and store them together.
-    const int npair = (nchunk + 1) >> 1;
-    const int qsz = max(1, min(min(nq, 16), (nq * npair + 2 * nw - 1) / (2 * nw)));
-    const int ngrp = (nq + qsz - 1) / qsz;
-    const int nitems = npair * ngrp;
-    for (int it = wid; it < nitems; it += nw) {
-      const int grp = it / npair;
-      const int cp = it - grp * npair;
-      const int k0 = cp * 64 + lane, k1 = k0 + 32;
-      const float4 c0 = k0 < nc ? S.c[k0] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-      const float4 c1 = k1 < nc ? S.c[k1] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-      const unsigned long long X = pack2(c0.x, c1.x), Y = pack2(c0.y, c1.y), Z = pack2(c0.z, c1.z);
-      const int q0 = grp * qsz, q_end = min(nq, q0 + qsz);
-      unsigned mine = 0u;
-      for (int ql = q0; ql < q_end; ++ql) {
-        const float4 qa = S.qa[ql], qb = S.qb[ql];
-        unsigned long long dx, dy, dz, D2;
-        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(X), "l"(pack2(qa.x, qa.y)));
-        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(Y), "l"(pack2(qa.z, qa.w)));
-        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(Z), "l"(pack2(qb.x, qb.y)));
-        asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(D2) : "l"(dx), "l"(dx));
-        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D2) : "l"(dy), "l"(dy), "l"(D2));
-        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D2) : "l"(dz), "l"(dz), "l"(D2));
-        const float d0 = lo_half(D2), d1 = hi_half(D2);
-        bool h0 = d0 <= B.lo_w, h1 = d1 <= B.lo_w;
-        const bool u0 = !h0 && !(d0 > B.hi_w), u1 = !h1 && !(d1 > B.hi_w);
-        if (__any_sync(0xffffffffu, u0 || u1)) {
-          const float4 q = make_float4(qa.x, qa.z, qb.x, 0.f);
-          if (u0 && k0 < nc) h0 = canon_d2(q, g.spos[__float_as_int(c0.w)], g) <= B.r2;
-          if (u1 && k1 < nc) h1 = canon_d2(q, g.spos[__float_as_int(c1.w)], g) <= B.r2;
-        }
-        const int own = __float_as_int(qb.z);
-        const unsigned m0 = __ballot_sync(0xffffffffu, h0 && k0 != own);
-        const unsigned m1 = __ballot_sync(0xffffffffu, h1 && k1 != own);
-        const int slot = 2 * (ql - q0);
-        if (lane == slot) mine = m0;
-        if (lane == slot + 1) mine = m1;
-      }
-      const int qi = q0 + (lane >> 1), ch = 2 * cp + (lane & 1);
-      if (qi < q_end && ch < nchunk) rec_masks[qi * nchunk + ch] = mine;
-      int c = __popc(mine);
-      c += __shfl_xor_sync(0xffffffffu, c, 1);
-      if ((lane & 1) == 0 && qi < q_end && c) atomicAdd(&S.qcnt[qi], c);
-    }
-    __syncthreads();
     for (int i = tid; i < nq; i += blockDim.x) counts[__ldg(g.perm + qs + i)] = S.qcnt[i];
-    if (tid == 0) cell_rec[key] = rec;
+    if (tid == 0) cell_rec[key] = split ? -2 - S.hdr : S.base;
   }
 }
 
 // After the prefix sum: every heavy query's masks expanded into its ids at
-// their place in the output.  A block per heavy cell: the cell's ordered ids
-// are staged in shared memory (32 per row, rows padded to 33 words so that
-// lanes reading the same position of different rows fall in different
-// banks); each warp takes every kExpWarps-th query of the cell (a query's
-// masks are row `slot - first slot` of the record).  For 32 masks at a time,
-// lane j takes the j-th and, over its 32 bit positions in turn, appends the
-// ids of the set bits to the warp's shared buffer after the hits of the masks
-// before it; the warp then stores the buffer contiguously.  Output offsets of
-// up to 32 queries are fetched at once, and the next masks are loaded while
-// the current ones are expanded.
+// their place in the output.  A block per heavy cell, slab after slab (one
+// for an unsplit cell): the slab's ordered ids are staged in shared memory
+// (32 per row, rows padded to 33 words so that lanes reading the same
+// position of different rows fall in different banks); each warp takes every
+// kExpWarps-th query of the cell (a query's masks are row `slot - first slot`
+// of the slab record).  The warp keeps its queries' write positions in
+// registers (its t-th query in lane t % 32, slot t / 32), fetched at once and
+// carried from slab to slab.  For 32 masks at a time, lane j takes the j-th
+// and, over its 32 bit positions in turn, appends the ids of the set bits to
+// the warp's shared buffer after the hits of the masks before it; the warp
+// then stores the buffer contiguously.  The next masks are loaded while the
+// current ones are expanded.
 constexpr int kExpWarps = 4;
 constexpr int kExpRows = (kCellCap + 31) / 32;
+constexpr int kExpSlots = (kCellMaxQ + 32 * kExpWarps - 1) / (32 * kExpWarps);   // positions per lane
 
 __global__ void __launch_bounds__(kExpWarps * 32, 8) k_cell_expand(GridDev g, const int *__restrict__ heavy,
                                                                    const long long *__restrict__ cell_rec,
@@ -445,34 +513,48 @@ __global__ void __launch_bounds__(kExpWarps * 32, 8) k_cell_expand(GridDev g, co
   const int nheavy = heavy[0];
   for (int item = blockIdx.x; item < nheavy; item += gridDim.x) {
     const unsigned key = (unsigned)heavy[1 + item];
-    const int qs = __ldg(g.cell_start + key), qe = __ldg(g.cell_start + key + 1);
-    const long long rec = cell_rec[key];
-    if (rec < 0) continue;   // served by the per-query path (the same for the whole block)
-    const int nc = __ldg(scratch + rec);
-    const int nchunk = (nc + 31) >> 5;
-    const int *rec_ids = scratch + rec + 1;
-    const unsigned *rec_masks = reinterpret_cast<const unsigned *>(rec_ids + nc);
-    __syncthreads();   // the previous cell's ids are no longer read
-    for (int k = tid; k < nc; k += blockDim.x) sids[(k >> 5) * 33 + (k & 31)] = __ldg(rec_ids + k);
-    __syncthreads();
-    const int nmine = (qe - qs - wid + kExpWarps - 1) / kExpWarps;   // this warp's queries
-    for (int i0 = 0; i0 < nmine; i0 += 32) {
-      long long dstv = 0;
-      if (i0 + lane < nmine) dstv = offsets[__ldg(g.perm + qs + wid + kExpWarps * (i0 + lane))];
-      const int nb = min(32, nmine - i0);
-      int qn = wid + kExpWarps * i0;   // index of the query in its cell = row of its masks
-      unsigned mnext = lane < nchunk ? __ldg(rec_masks + (long long)qn * nchunk + lane) : 0u;
-      for (int j = 0; j < nb; ++j) {
-        const int qj = qn;
-        long long wpos = __shfl_sync(0xffffffffu, dstv, j);
-        qn += kExpWarps;
+    const long long ref = cell_rec[key];
+    if (ref == -1) continue;   // served by the per-query path (the same for the whole block)
+    const int qs = __ldg(g.cell_start + key), nq = __ldg(g.cell_start + key + 1) - qs;
+    int nslab = 1;
+    const long long *slabs = nullptr;
+    if (ref < -1) {
+      const long long hdr = -2 - ref;
+      nslab = __ldg(scratch + hdr);
+      slabs = reinterpret_cast<const long long *>(scratch + hdr + 2);
+    }
+    const int nmine = (nq - wid + kExpWarps - 1) / kExpWarps;   // this warp's queries: wid + kExpWarps t
+    long long wpos_of[kExpSlots];
+#pragma unroll
+    for (int k = 0; k < kExpSlots; ++k) {
+      const int t = k * 32 + lane;
+      wpos_of[k] = t < nmine ? offsets[__ldg(g.perm + qs + wid + kExpWarps * t)] : 0ll;
+    }
+    for (int sl = 0; sl < nslab; ++sl) {
+      const long long rec = slabs ? slabs[sl] : ref;
+      const int nc = __ldg(scratch + rec);
+      const int nchunk = (nc + 31) >> 5;
+      const int *rec_ids = scratch + rec + 1;
+      const unsigned *rec_masks = reinterpret_cast<const unsigned *>(rec_ids + nc);
+      __syncthreads();   // the previous slab's (or cell's) ids are no longer read
+      for (int k = tid; k < nc; k += blockDim.x) sids[(k >> 5) * 33 + (k & 31)] = __ldg(rec_ids + k);
+      __syncthreads();
+      unsigned mnext = (nmine > 0 && lane < nchunk) ? __ldg(rec_masks + (long long)wid * nchunk + lane) : 0u;
+      for (int t = 0; t < nmine; ++t) {
+        const int ql = wid + kExpWarps * t, qn = ql + kExpWarps;
+        long long mine = wpos_of[0];
+#pragma unroll
+        for (int k = 1; k < kExpSlots; ++k)
+          if ((t >> 5) == k) mine = wpos_of[k];
+        long long wpos = __shfl_sync(0xffffffffu, mine, t & 31);
+        const unsigned *mk = rec_masks + (long long)ql * nchunk;
         for (int c0 = 0; c0 < nchunk; c0 += 32) {
           const unsigned mm = mnext;
           // prefetch: the rest of this query's masks, else the next query's first 32
           if (c0 + 32 < nchunk) {
             const int ch = c0 + 32 + lane;
-            mnext = ch < nchunk ? __ldg(rec_masks + (long long)qj * nchunk + ch) : 0u;
-          } else if (j + 1 < nb) {
+            mnext = ch < nchunk ? __ldg(mk + ch) : 0u;
+          } else if (qn < nq) {
             mnext = lane < nchunk ? __ldg(rec_masks + (long long)qn * nchunk + lane) : 0u;
           }
           const int cnt = __popc(mm);
@@ -490,6 +572,11 @@ __global__ void __launch_bounds__(kExpWarps * 32, 8) k_cell_expand(GridDev g, co
           for (int i = lane; i < tot; i += 32) ids[wpos + i] = buf[i];
           __syncwarp();
           wpos += tot;
+        }
+        if (lane == (t & 31)) {
+#pragma unroll
+          for (int k = 0; k < kExpSlots; ++k)
+            if ((t >> 5) == k) wpos_of[k] = wpos;
         }
       }
     }

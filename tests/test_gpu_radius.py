@@ -210,6 +210,33 @@ def test_dense_light_queries_exact(mask):
         assert np.array_equal(np.sort(ids_u[off_u[q]:off_u[q + 1]]), ids_o[off_o[q]:off_o[q + 1]])
 
 
+@pytest.mark.parametrize("mask", [7, 0])
+def test_cells_split_into_index_slabs(mask):
+    # ~15 points per cell and r = 2.9 cells: every cell has ~2.9k candidates,
+    # more than the large cell kernel stages, so cells are split into slabs of
+    # input indices whose hits concatenate into the sorted lists
+    pos = synth.uniform_points(60_000, 41 + mask)
+    scene = synth.Scene(pos, (0, 0, 0), 1 / 16, (4, 4, 4), mask, 2.9 / 16)
+    off_o, ids_o = oracle_radius(scene)
+    g = gpu_grid(scene)
+    off_g, ids_g = gpu_radius(scene, grid=g)
+    assert_csr_equal(off_g, ids_g, off_o, ids_o)
+    assert np.diff(off_o).mean() > 1000
+    if mask == 7:
+        off_s, ids_s = oracle_radius(scene, include_self=True)
+        off_gs, ids_gs = gpu_radius(scene, include_self=True, grid=g)
+        assert_csr_equal(off_gs, ids_gs, off_s, ids_s)
+
+
+def test_cells_split_into_three_or_more_slabs_sampled():
+    pos = synth.uniform_points(100_000, 43)
+    scene = synth.Scene(pos, (0, 0, 0), 1 / 16, (4, 4, 4), 7, 2.9 / 16)
+    off_g, ids_g = gpu_radius(scene)
+    q = np.random.default_rng(3).choice(scene.n, 800, replace=False)
+    assert_sampled_equal(off_g, ids_g, scene, q)
+    assert off_g[-1] % 2 == 0
+
+
 @pytest.mark.parametrize("name", ["uniform_1m", "mixture_1m"])
 def test_full_size_1m_configs_sampled(name):
     scene = synth.uniform_1m_scene() if name == "uniform_1m" else synth.mixture_1m_scene()
