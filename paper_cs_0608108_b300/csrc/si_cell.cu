@@ -120,6 +120,9 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
   };
   const int bshift_all = bucket_shift(g.n);
   // reservations are kept even so that headers hold aligned 64-bit offsets
+  // (scr_top also tells the host how much scratch a call needs: a cell whose
+  // reservation fails adds a bound for the slabs it did not reach)
+  auto slab_bound = [&](int nq) { return 2ll + kCap + (long long)nq * ((kCap + 31) / 32); };
   auto reserve = [&](long long need) -> long long {
     need = (need + 1) & ~1ll;
     const unsigned long long b = atomicAdd(scr_top, (unsigned long long)need);
@@ -307,6 +310,7 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
           if (tid == 0) {
             S.hdr = reserve(2 + 2ll * nslab);
             if (S.hdr >= 0) scratch[S.hdr] = nslab;
+            else atomicAdd(scr_top, (unsigned long long)(nslab * slab_bound(nq)));
             S.nc = 0;
           }
           for (int b = tid; b < kBuckets; b += blockDim.x) S.bstart[b] = 0;
@@ -345,6 +349,8 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
         run += v[r];
       }
       if (S.base < 0) {
+        if (split && tid == 0 && sl + 1 < nslab)
+          atomicAdd(scr_top, (unsigned long long)((nslab - sl - 1) * slab_bound(nq)));
         ok = false;
         room = false;
         break;
