@@ -181,10 +181,13 @@ si_status si_neighbor_energy_noalloc(const si_grid_desc *desc, const float *d_po
 
 /* ---------------------------------------------------------------------------
  * Batched scenes: many independent grids served together.
- * Each scene has its own lattice, cyclic mask, radius and points; all scenes
- * are binned and queried by a fixed, small number of launches (one persistent
- * query kernel pulls (scene, query tile) items from a device work queue), so
- * that the whole batch can be captured once in a CUDA graph and replayed.
+ * Each scene has its own lattice, cyclic mask, radius and points.  Scenes
+ * with short expected lists are binned and queried together by a fixed,
+ * small number of launches (one persistent query kernel pulls (scene, query
+ * tile) items from a device work queue); scenes with long lists each run the
+ * single-scene pipeline of si_grid_build + si_query_radius on a grid of
+ * their own, on concurrent branches.  The whole batch is captured once in a
+ * CUDA graph and replayed.
  * ------------------------------------------------------------------------- */
 typedef struct {
   si_grid_desc desc;       /* r_max is ignored; the scene's r sizes its tables */
@@ -205,9 +208,11 @@ typedef struct si_batch si_batch;
 si_status si_batch_create(const si_scene *scenes, int n_scenes, uint32_t flags, si_batch **out);
 
 /* Run the batch on `stream`: bin all scenes, count, scan, write, sort.
- * Asynchronous; capacity overflow is reported by si_batch_sync.
- * use_graph != 0: the first call captures the launches into a CUDA graph
- * and every call replays it. */
+ * Capacity overflow is reported by si_batch_sync.  The first call runs
+ * eagerly and waits for the GPU (the long-list scenes build their radius
+ * tables and size their scratch from the list totals); later calls are
+ * asynchronous.  use_graph != 0: the first call also captures the launches
+ * into a CUDA graph, and every later call replays it. */
 si_status si_batch_run(si_batch *b, int use_graph, void *stream);
 
 /* Wait, then report the per-scene totals (h_totals[n_scenes], host,

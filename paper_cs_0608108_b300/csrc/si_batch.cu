@@ -1,10 +1,19 @@
 // Batched scenes: many independent grids (own lattice, cyclic mask, radius,
-// point set) binned and queried together.  All scenes' cells live in one
-// concatenated cell array and all points in one sorted array, so binning is
-// a fixed number of launches for the whole batch, and the two query passes
-// are persistent kernels that pull (scene, tile of queries) items from a
-// device work queue ordered heaviest first.  Nothing synchronises with the
-// host, so the whole sequence can be captured in a CUDA graph and replayed.
+// point set) served together, in one CUDA graph.
+//
+// Light scenes (short lists) are fused: all their cells live in one
+// concatenated cell array and all their points in one sorted array, so
+// binning is a fixed number of launches for all of them, and the two query
+// passes are persistent kernels that pull (scene, tile of queries) items
+// from a device work queue ordered heaviest first.
+// Heavy scenes (long lists, crowded cells) each get a grid of their own and
+// the single-scene pipeline (binning with cell classes, per-query, per-warp
+// and per-cell kernels, slab splitting, expansion), whose work per scene is
+// large enough to fill the GPU's share it gets: they run on concurrent
+// branches of the same graph, heaviest first on the least-loaded branch.
+// The first run is eager (it builds the heavy scenes' radius tables and
+// sizes their scratch, which needs host round trips); with use_graph the
+// launches are then captured once and replayed.
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -21,6 +30,7 @@ constexpr int kQTile = 128;
 constexpr int kBatchInlineSort = 32;
 constexpr int kBatchSortThreads = 512;
 constexpr int kBatchSortSmem = 8192;
+constexpr double kBatchHeavyHits = 24.0;   // expected list length from which a scene gets its own pipeline
 
 struct SceneDev {
   GridDev g;               // spos/perm: batch-global arrays; cell_start: the scene's cells
@@ -237,8 +247,23 @@ __global__ void __launch_bounds__(kBatchSortThreads) k_batch_sort(const SceneDev
 using namespace si;
 
 struct si_batch {
-  int n_scenes = 0;
+  struct Heavy {
+    int scene;                    // index in `scenes`
+    si_grid *grid;
+    double work;                  // expected hits
+    int branch;
+  };
+  int n_scenes = 0;               // all scenes
   std::vector<si_scene> scenes;
+  uint32_t flags = 0;
+  std::vector<int> fused;         // original index of each fused (light) scene
+  std::vector<Heavy> heavy;
+  int n_branches = 0;             // concurrent graph branches for heavy scenes
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> branch_done;
+  cudaEvent_t fork = nullptr;
+  bool warmed = false;
+  int warm_status = 0;            // SI_ERR_* of the eager first run of the heavy scenes
   std::vector<DevTables> tables;
   std::vector<Lattice> lats;
   int64_t n_total = 0, cells_total = 0;
@@ -264,6 +289,10 @@ static void batch_free(si_batch *b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto &h : b->heavy) si_grid_destroy(h.grid);
+  for (cudaStream_t s : b->branch) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->branch_done) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
   for (auto &t : b->tables) free_tables(t);
   cudaFree(b->d_scenes);
   cudaFree(b->d_bin_items);
@@ -304,7 +333,8 @@ extern "C" si_status si_batch_create(const si_scene *scenes, int n_scenes, uint3
   if (!b) return fail(SI_ERR_OOM, "host allocation failed");
   b->n_scenes = n_scenes;
   b->scenes.assign(scenes, scenes + n_scenes);
-  std::vector<SceneDev> hs(n_scenes);
+  b->flags = flags;
+  std::vector<SceneDev> hs;
   std::vector<Item> bin_items;
   struct QItem {
     Item it;
@@ -325,6 +355,23 @@ extern "C" si_status si_batch_create(const si_scene *scenes, int n_scenes, uint3
       batch_free(b);
       return fail(s, "scene " + std::to_string(k) + ": " + si_last_error());
     }
+    // expected list length: load times the sphere's volume in cells
+    const double dcell = (double)sc.r * lat.inv_s;
+    const double hits = (double)sc.n / (double)(1ll << lat.W) * 4.0 / 3.0 * M_PI * dcell * dcell * dcell;
+    if (!(flags & SI_METHOD_CUBE) && sc.n > 0 && hits >= kBatchHeavyHits) {
+      si_grid_desc desc = sc.desc;
+      desc.r_max = sc.r;
+      si_grid *gr = nullptr;
+      if ((s = si_grid_create(&desc, sc.n, &gr)) != SI_OK) {
+        const std::string why = si_last_error();
+        batch_free(b);
+        return fail(s, "scene " + std::to_string(k) + ": " + why);
+      }
+      b->heavy.push_back({k, gr, (double)sc.n * hits, 0});
+      continue;
+    }
+    const int fi = (int)b->fused.size();
+    b->fused.push_back(k);
     HostTables ht;
     std::string err;
     if (!build_tables(lat.w, lat.cyc, lat.n_max, ht, err)) {
@@ -338,7 +385,8 @@ extern "C" si_status si_batch_create(const si_scene *scenes, int n_scenes, uint3
     }
     b->tables.push_back(dt);
     b->lats.push_back(lat);
-    SceneDev &S = hs[k];
+    hs.emplace_back();
+    SceneDev &S = hs.back();
     fill_griddev(lat, dt, S.g);
     S.g.n = (int)sc.n;
     S.pbase = b->n_total;
@@ -363,10 +411,10 @@ extern "C" si_status si_batch_create(const si_scene *scenes, int n_scenes, uint3
     S.B = make_band(lat, sc.r);
     S.cube = (flags & SI_METHOD_CUBE) ? 1 : (plan_cube(d) ? 1 : 0);
     S.include_self = (flags & SI_INCLUDE_SELF) ? 1 : 0;
-    for (int64_t f = 0; f < sc.n; f += kBinTile) bin_items.push_back({k, (int)f});
+    for (int64_t f = 0; f < sc.n; f += kBinTile) bin_items.push_back({fi, (int)f});
     // cost of one query tile: cells visited x (1 + load): heaviest first
     const double cells = 1.0 + 6.0 * d + 3.0 * M_PI * d * d + 4.0 / 3.0 * M_PI * d * d * d;
-    for (int64_t f = 0; f < sc.n; f += kQTile) q_items.push_back({{k, (int)f}, cells * (1.0 + load)});
+    for (int64_t f = 0; f < sc.n; f += kQTile) q_items.push_back({{fi, (int)f}, cells * (1.0 + load)});
     b->n_total += sc.n;
     b->cells_total += (1ll << lat.W) + 1;
   }
@@ -386,7 +434,8 @@ extern "C" si_status si_batch_create(const si_scene *scenes, int n_scenes, uint3
     batch_free(b);                                     \
     return s;                                          \
   }
-  SI_BALLOC(b->d_scenes, n_scenes * sizeof(SceneDev));
+  const int n_fused = (int)hs.size();
+  SI_BALLOC(b->d_scenes, std::max(n_fused, 1) * sizeof(SceneDev));
   SI_BALLOC(b->d_bin_items, std::max<size_t>(bin_items.size(), 1) * sizeof(Item));
   SI_BALLOC(b->d_q_items, std::max<size_t>(qi.size(), 1) * sizeof(Item));
   SI_BALLOC(b->key_slot, N * sizeof(uint2));
@@ -399,22 +448,51 @@ extern "C" si_status si_batch_create(const si_scene *scenes, int n_scenes, uint3
   SI_BALLOC(b->scan_i64, scan_scratch_elems(N) * sizeof(long long));
   SI_BALLOC(b->queues, 2 * sizeof(int));
   SI_BALLOC(b->longq, (1 + 2 * N) * sizeof(int));
-  SI_BALLOC(b->scene_status, n_scenes * sizeof(int));
+  SI_BALLOC(b->scene_status, std::max(n_fused, 1) * sizeof(int));
 #undef SI_BALLOC
-  for (int k = 0; k < n_scenes; ++k) {
+  for (int k = 0; k < n_fused; ++k) {
     hs[k].g.spos = b->spos;
     hs[k].g.perm = b->perm;
     hs[k].g.cell_start = b->start + hs[k].cbase;
     hs[k].g.status = b->scene_status + k;
   }
-  cudaError_t e = cudaMemcpy(b->d_scenes, hs.data(), n_scenes * sizeof(SceneDev), cudaMemcpyHostToDevice);
+  cudaError_t e = n_fused > 0 ? cudaMemcpy(b->d_scenes, hs.data(), n_fused * sizeof(SceneDev), cudaMemcpyHostToDevice)
+                              : cudaSuccess;
   if (e == cudaSuccess && !bin_items.empty())
     e = cudaMemcpy(b->d_bin_items, bin_items.data(), bin_items.size() * sizeof(Item), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !qi.empty())
     e = cudaMemcpy(b->d_q_items, qi.data(), qi.size() * sizeof(Item), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(b->scene_status, 0, n_scenes * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(b->scene_status, 0, std::max(n_fused, 1) * sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_pinned, (n_scenes + 1) * sizeof(long long) * 2);
-  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_status, n_scenes * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_status, std::max(n_fused, 1) * sizeof(int));
+  // heavy scenes: heaviest first on the least-loaded branch
+  b->n_branches = std::min<int>(8, (int)b->heavy.size());
+  {
+    std::vector<size_t> order(b->heavy.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t x, size_t y) { return b->heavy[x].work > b->heavy[y].work; });
+    std::vector<double> load(b->n_branches, 0.0);
+    for (size_t i : order) {
+      const int br = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      b->heavy[i].branch = br;
+      load[br] += b->heavy[i].work;
+    }
+    std::vector<si_batch::Heavy> sorted;
+    for (size_t i : order) sorted.push_back(b->heavy[i]);
+    b->heavy.swap(sorted);
+  }
+  for (int i = 0; e == cudaSuccess && i < b->n_branches; ++i) {
+    cudaStream_t bs;
+    cudaEvent_t be;
+    e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) break;
+    b->branch.push_back(bs);
+    e = cudaEventCreateWithFlags(&be, cudaEventDisableTiming);
+    if (e != cudaSuccess) break;
+    b->branch_done.push_back(be);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     batch_free(b);
@@ -424,13 +502,17 @@ extern "C" si_status si_batch_create(const si_scene *scenes, int n_scenes, uint3
   return SI_OK;
 }
 
+// The fused launches of the light scenes.
 static si_status batch_launches(si_batch *b, cudaStream_t st) {
+  if (b->fused.empty()) return SI_OK;
   const int64_t N = b->n_total;
   SI_CUDA_TRY(cudaMemsetAsync(b->count, 0, b->cells_total * sizeof(int), st));
   SI_CUDA_TRY(cudaMemsetAsync(b->queues, 0, 2 * sizeof(int), st));
   SI_CUDA_TRY(cudaMemsetAsync(b->longq, 0, sizeof(int), st));
-  for (const si_scene &sc : b->scenes)
+  for (int k : b->fused) {
+    const si_scene &sc = b->scenes[k];
     if (sc.n == 0) SI_CUDA_TRY(cudaMemsetAsync(sc.d_offsets, 0, sizeof(int64_t), st));
+  }
   if (b->n_bin_items > 0) {
     SI_KLAUNCH("k_batch_key", st, k_batch_key<<<b->n_bin_items, kBinTile, 0, st>>>(b->d_scenes, b->d_bin_items, b->key_slot, b->count,
                                                      b->scene_status));
@@ -454,27 +536,78 @@ static si_status batch_launches(si_batch *b, cudaStream_t st) {
   return SI_OK;
 }
 
+// One heavy scene through the single-scene pipeline.  total (nullable): the
+// list total, read back (a host round trip that lets the query size its
+// scratch); without it the call is asynchronous.
+static si_status heavy_run(si_batch *b, const si_batch::Heavy &h, cudaStream_t st, int64_t *total) {
+  const si_scene &sc = b->scenes[h.scene];
+  si_status s = si_grid_build(h.grid, sc.d_pos, sc.n, st);
+  if (s != SI_OK) return s;
+  return si_query_radius(h.grid, nullptr, sc.n, sc.r, b->flags & SI_INCLUDE_SELF, sc.d_offsets, sc.d_ids,
+                         sc.ids_capacity, total, st);
+}
+
+// Capture: the fused launches on the origin stream, each heavy scene on its
+// branch, branches forked from and joined back to the origin.
+static si_status batch_capture(si_batch *b) {
+  cudaStream_t cs;
+  SI_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_fail(e, "cudaStreamBeginCapture");
+  }
+  si_status s = SI_OK;
+  if (b->n_branches > 0) {
+    e = cudaEventRecord(b->fork, cs);
+    for (int i = 0; e == cudaSuccess && i < b->n_branches; ++i) e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+    if (e != cudaSuccess) s = cuda_fail(e, "graph fork");
+  }
+  if (s == SI_OK) s = batch_launches(b, cs);
+  for (size_t i = 0; s == SI_OK && i < b->heavy.size(); ++i)
+    s = heavy_run(b, b->heavy[i], b->branch[b->heavy[i].branch], nullptr);
+  for (int i = 0; i < b->n_branches; ++i) {   // joined even after an error, so that the capture can end
+    cudaEventRecord(b->branch_done[i], b->branch[i]);
+    cudaStreamWaitEvent(cs, b->branch_done[i], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cs, &graph);
+  cudaStreamDestroy(cs);
+  if (s != SI_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  b->graph = graph;
+  SI_CUDA_TRY(cudaGraphInstantiate(&b->exec, graph, 0));
+  return SI_OK;
+}
+
 extern "C" si_status si_batch_run(si_batch *b, int use_graph, void *stream) {
   if (!b) return fail(SI_ERR_INVALID, "null batch");
   cudaStream_t st = (cudaStream_t)stream;
-  if (!use_graph) return batch_launches(b, st);
-  if (!b->exec) {
-    // capture on a private stream so the caller's stream may be the legacy one
-    cudaStream_t cs;
-    SI_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    SI_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    si_status s = batch_launches(b, cs);
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(cs, &graph);
-    cudaStreamDestroy(cs);
-    if (s != SI_OK) {
-      if (graph) cudaGraphDestroy(graph);
-      return s;
+  si_status s;
+  if (!b->warmed) {
+    // eager first run: the heavy scenes build their radius tables and size
+    // their scratch from the list totals (host round trips); a capacity
+    // shortfall is reported by si_batch_sync
+    if ((s = batch_launches(b, st)) != SI_OK) return s;
+    for (const auto &h : b->heavy) {
+      int64_t total = 0;
+      s = heavy_run(b, h, st, &total);
+      if (s == SI_ERR_CAPACITY) b->warm_status = SI_ERR_CAPACITY;
+      else if (s != SI_OK) return s;
     }
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    b->graph = graph;
-    SI_CUDA_TRY(cudaGraphInstantiate(&b->exec, graph, 0));
+    b->warmed = true;
+    return use_graph ? batch_capture(b) : SI_OK;
   }
+  if (!use_graph) {
+    if ((s = batch_launches(b, st)) != SI_OK) return s;
+    for (const auto &h : b->heavy)
+      if ((s = heavy_run(b, h, st, nullptr)) != SI_OK) return s;
+    return SI_OK;
+  }
+  if (!b->exec && (s = batch_capture(b)) != SI_OK) return s;
   prof_begin(st);
   SI_CUDA_TRY(cudaGraphLaunch(b->exec, st));
   count_launch();
@@ -485,9 +618,11 @@ extern "C" si_status si_batch_run(si_batch *b, int use_graph, void *stream) {
 extern "C" si_status si_batch_sync(si_batch *b, int64_t *h_totals, void *stream) {
   if (!b) return fail(SI_ERR_INVALID, "null batch");
   cudaStream_t st = (cudaStream_t)stream;
-  SI_CUDA_TRY(cudaMemcpyAsync(b->h_status, b->scene_status, b->n_scenes * sizeof(int),
-                              cudaMemcpyDeviceToHost, st));
-  SI_CUDA_TRY(cudaMemsetAsync(b->scene_status, 0, b->n_scenes * sizeof(int), st));
+  const int nf = (int)b->fused.size();
+  if (nf > 0) {
+    SI_CUDA_TRY(cudaMemcpyAsync(b->h_status, b->scene_status, nf * sizeof(int), cudaMemcpyDeviceToHost, st));
+    SI_CUDA_TRY(cudaMemsetAsync(b->scene_status, 0, nf * sizeof(int), st));
+  }
   for (int k = 0; k < b->n_scenes; ++k) {
     const si_scene &sc = b->scenes[k];
     if (h_totals)
@@ -496,11 +631,22 @@ extern "C" si_status si_batch_sync(si_batch *b, int64_t *h_totals, void *stream)
   }
   SI_CUDA_TRY(cudaStreamSynchronize(st));
   int agg = 0;
-  for (int k = 0; k < b->n_scenes; ++k) agg |= b->h_status[k];
+  for (int k = 0; k < nf; ++k) agg |= b->h_status[k];
   if (h_totals)
     for (int k = 0; k < b->n_scenes; ++k) h_totals[k] = b->h_pinned[k];
+  // heavy scenes: their grids' status words
+  si_status worst = SI_OK;
+  for (const auto &h : b->heavy) {
+    const si_status hs = si_grid_sync(h.grid, st);
+    if (hs == SI_ERR_INVALID) agg |= ST_INVALID;
+    else if (hs == SI_ERR_CAPACITY) agg |= ST_CAPACITY;
+    else if (hs != SI_OK) worst = hs;
+  }
+  if (b->warm_status == SI_ERR_CAPACITY) agg |= ST_CAPACITY;
+  b->warm_status = 0;
   if (agg & ST_INVALID) return fail(SI_ERR_INVALID, "a scene has a point outside a cyclic box or not finite");
   if (agg & ST_INTERNAL) return fail(SI_ERR_INTERNAL, "device-side consistency check failed");
+  if (worst != SI_OK) return worst;
   if (agg & ST_CAPACITY) return fail(SI_ERR_CAPACITY, "a scene's id buffer is too small");
   return SI_OK;
 }

@@ -1,5 +1,6 @@
-"""Parity of the batched persistent path (all scenes in one set of launches,
-optionally replayed from a CUDA graph) with the FP64 oracle, scene by scene."""
+"""Parity of the batched path (short-list scenes in one fused set of launches,
+long-list scenes through their own pipelines, optionally replayed from a CUDA
+graph) with the FP64 oracle and the single-scene path, scene by scene."""
 import numpy as np
 import pytest
 import torch
@@ -62,3 +63,28 @@ def test_batch_capacity_overflow_is_reported():
     with pytest.raises(_native.SIError) as ei:
         b.sync()
     assert ei.value.status == _native.SI_ERR_CAPACITY
+
+
+@pytest.mark.parametrize("kind", ["long_lists_only", "short_lists_only"])
+def test_batch_with_a_single_kind_of_scene(kind):
+    # long lists: every scene runs its own pipeline on a graph branch, the
+    # fused launches have nothing to do; short lists: the reverse
+    if kind == "long_lists_only":
+        scenes = [synth.Scene(synth.uniform_points(30_000, 61 + k), (0, 0, 0), 1 / 16, (4, 4, 4), 7 - k,
+                              2.0 / 16) for k in range(3)]
+    else:
+        scenes = [synth.Scene(synth.uniform_points(5_000, 71 + k), (0, 0, 0), 1 / 32, (5, 5, 5), k,
+                              1.0 / 32) for k in range(3)]
+    plain = [gpu_radius(sc) for sc in scenes]
+    b, offs, ids = make_batch(scenes, caps=[int(o[-1]) + 1 for o, _ in plain])
+    for _ in range(3):
+        for t in ids:
+            t.fill_(-7)
+        b.run(use_graph=True)
+        totals = b.sync()
+        for k, sc in enumerate(scenes):
+            off_p, ids_p = plain[k]
+            o = offs[k].cpu().numpy()
+            assert totals[k] == off_p[-1]
+            assert np.array_equal(o, off_p)
+            assert np.array_equal(ids[k].cpu().numpy()[: o[-1]], ids_p)
