@@ -5,11 +5,24 @@
 //
 // Order is (canonical FP64 D2, index).  Candidates are compared in FP32; two
 // FP32 values closer than the proven FP32 error bound are compared again in
-// FP64 (values cached per held entry), so the kept set and its order are
-// exact while almost every comparison stays in FP32.
+// FP64, so the kept set and its order are exact while almost every
+// comparison stays in FP32.
+//
+// Two kernels.  With a bounded r_max, k_knn_warp serves a query with one
+// warp: the x-rows of the r_max sphere (rows of cells whose y-z bound is
+// within r_max, each cut to the x-interval the query's exact y-z distance
+// allows) are decoded by the lanes in parallel, every candidate within r_max
+// (the exact predicate) goes to the warp's shared buffer as an FP32 key, and
+// a warp bitonic sort orders the buffer; runs of adjacent keys closer than
+// the FP32 error bound are then put in canonical order.  r_max is the cut
+// here from the start: on these workloads it is close to the K-th distance,
+// so shrinking it saves little.  k_knn, one thread per query with the
+// shrinking cut described above, serves unbounded r_max, query points outside
+// the region and queries whose candidates overflow the warp's buffer.
 #include <cmath>
 
 #include "si_host.h"
+#include "si_sort.cuh"
 #include "si_walk.cuh"
 
 namespace si {
@@ -52,11 +65,13 @@ __device__ __forceinline__ bool cand_less(Cand &a, const KnnList &L, int kb, con
   return __ldg(g.perm + a.j) < __ldg(g.perm + jb);
 }
 
+// list (nullable): [0] = count, then the sorted slots to serve; else every slot.
 __global__ void __launch_bounds__(kKnnThreads) k_knn(GridDev g, int K, float dmax_g, int n_query,
                                                      Band B, PairBand pb, unsigned flags,
                                                      int *__restrict__ out_ids,
                                                      float *__restrict__ out_d2,
-                                                     int *__restrict__ out_counts) {
+                                                     int *__restrict__ out_counts,
+                                                     const int *__restrict__ list) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x;
   KnnList L;
@@ -64,8 +79,9 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(GridDev g, int K, float dma
   L.j = (int *)(L.d + (size_t)K * T);
   L.T = T;
   L.t = threadIdx.x;
-  const int s = blockIdx.x * T + threadIdx.x;
-  if (s >= g.n) return;
+  const int ti = blockIdx.x * T + threadIdx.x;
+  if (ti >= (list ? list[0] : g.n)) return;
+  const int s = list ? list[1 + ti] : ti;
   const QueryGeom Q = make_geom(g.spos[s], g);
   const int self = (flags & SI_INCLUDE_SELF) ? -1 : s;
   int cnt = 0;
@@ -203,6 +219,221 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(GridDev g, int K, float dma
   out_counts[orig] = cnt;
 }
 
+constexpr int kKnnWarps = 8;      // warps per block of k_knn_warp
+constexpr int kKnnCap = 512;      // candidates a warp holds
+
+struct KnnRuns {                  // up to two runs per row of a 32-row batch
+  int b[64];
+  int len[64];
+  float qx[64], qy[64], qz[64];
+  unsigned char wrapped[64];
+  int pre[33];
+};
+
+__global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, float dmax_g, int n_query,
+                                                            Band B, PairBand pb, unsigned flags,
+                                                            int *__restrict__ out_ids,
+                                                            float *__restrict__ out_d2,
+                                                            int *__restrict__ out_counts,
+                                                            int *__restrict__ fallq) {
+  __shared__ unsigned long long keys[kKnnWarps][kKnnCap];
+  __shared__ KnnRuns runs[kKnnWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int s = blockIdx.x * kKnnWarps + w;   // the warp's query (sorted slot)
+  if (s >= g.n) return;
+  unsigned long long *key = keys[w];
+  KnnRuns &R = runs[w];
+  const unsigned lt = (1u << lane) - 1u;
+  const QueryGeom Q = make_geom(g.spos[s], g);
+  if (Q.outside) {   // the bounding-cube walk of the per-thread kernel
+    if (lane == 0) fallq[1 + atomicAdd(fallq, 1)] = s;
+    return;
+  }
+  const int self = (flags & SI_INCLUDE_SELF) ? -1 : s;
+  const float cut2 = dmax_g * dmax_g;
+  const int Gx = 1 << g.wx;
+  const bool cyc_x = g.cyc & 1u;
+  int cnt = 0;
+  bool overflow = false, out_any = false;
+  // every candidate within r_max, decided exactly, into the buffer
+  auto add = [&](bool in, float d, int j) {
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    const int at = cnt + __popc(m & lt);
+    if (in && at < kKnnCap) key[at] = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)j;
+    cnt += __popc(m);
+  };
+  for (int base = 0; base < g.n_rows && !overflow; base += 32) {
+    const int r = base + lane;
+    int b0 = 0, l0 = 0, b1 = 0, l1 = 0;
+    float qx0 = 0.f, qy0 = 0.f, qz0 = 0.f, qx1 = 0.f;
+    bool w0 = false, out = false, live = false;
+    if (r < g.n_rows) {
+      const RowEntry E = g.rows[r];
+      live = E.b2 <= n_query && (float)E.b2 <= cut2;   // rows are sorted by b2
+      if (live) {
+        const float ty = E.oy > 0 ? (float)(E.oy - 1) + Q.zp[1] : (E.oy < 0 ? (float)(-E.oy - 1) + Q.zn[1] : 0.f);
+        const float tz = E.oz > 0 ? (float)(E.oz - 1) + Q.zp[2] : (E.oz < 0 ? (float)(-E.oz - 1) + Q.zn[2] : 0.f);
+        const float rem = cut2 - fmaf(ty, ty, tz * tz);
+        if (rem >= 0.f) {
+          const float h = sqrtf(rem) + g.eps;
+          const int lo = max((int)floorf(Q.u[0] - h) - Q.c[0], -g.row_lim_x);
+          const int hi = min((int)floorf(Q.u[0] + h) - Q.c[0], g.row_lim_x);
+          if (lo <= hi) {
+            const Target tg = translate_raw(E.unp, Q, g);
+            if (tg.outside) {
+              out = true;
+            } else {
+              const unsigned row = tg.key - (unsigned)Q.c[0];
+              int x0 = Q.c[0] + lo, x1 = Q.c[0] + hi;
+              qx0 = tg.qx;
+              qy0 = tg.qy;
+              qz0 = tg.qz;
+              w0 = tg.wrapped;
+              if (!cyc_x) {
+                if (x0 < 0 || x1 >= Gx) out = true;
+                x0 = max(x0, 0);
+                x1 = min(x1, Gx - 1);
+              } else if (x0 < 0 || x1 >= Gx) {
+                const int wa = x0 < 0 ? x0 + Gx : 0, wb = x0 < 0 ? Gx - 1 : x1 - Gx;
+                b1 = __ldg(g.cell_start + row + wa);
+                l1 = __ldg(g.cell_start + row + wb + 1) - b1;
+                qx1 = Q.q.x + (x0 < 0 ? g.Lx : -g.Lx);
+                x0 = max(x0, 0);
+                x1 = min(x1, Gx - 1);
+              }
+              if (x0 <= x1) {
+                b0 = __ldg(g.cell_start + row + x0);
+                l0 = __ldg(g.cell_start + row + x1 + 1) - b0;
+              }
+            }
+          }
+        }
+      }
+    }
+    out_any |= __any_sync(0xffffffffu, out);
+    const bool more = __any_sync(0xffffffffu, live);
+    R.b[2 * lane] = b0;
+    R.len[2 * lane] = l0;
+    R.qx[2 * lane] = qx0;
+    R.qy[2 * lane] = qy0;
+    R.qz[2 * lane] = qz0;
+    R.wrapped[2 * lane] = w0 ? 1 : 0;
+    R.b[2 * lane + 1] = b1;
+    R.len[2 * lane + 1] = l1;
+    R.qx[2 * lane + 1] = qx1;
+    R.qy[2 * lane + 1] = qy0;
+    R.qz[2 * lane + 1] = qz0;
+    R.wrapped[2 * lane + 1] = 1;
+    int inc = l0 + l1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    R.pre[lane + 1] = inc;
+    if (lane == 0) R.pre[0] = 0;
+    __syncwarp();
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    for (int f = lane; f - lane < total; f += 32) {
+      bool in = false;
+      float d = 0.f;
+      int j = 0;
+      if (f < total) {
+        int L = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (R.pre[L + step] <= f) L += step;
+        int off = f - R.pre[L];
+        int slot = 2 * L;
+        if (off >= R.len[slot]) {
+          off -= R.len[slot];
+          ++slot;
+        }
+        j = R.b[slot] + off;
+        if (j != self) {
+          const float4 p = g.spos[j];
+          const float dx = p.x - R.qx[slot], dy = p.y - R.qy[slot], dz = p.z - R.qz[slot];
+          d = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+          const bool wr = R.wrapped[slot];
+          const float blo = wr ? B.lo_w : B.lo, bhi = wr ? B.hi_w : B.hi;
+          in = d <= blo || (!(d > bhi) && canon_d2(Q.q, p, g) <= B.r2);
+        }
+      }
+      add(in, d, j);
+    }
+    __syncwarp();   // the next batch rewrites R
+    if (cnt > kKnnCap) overflow = true;
+    if (!more) break;   // every later row lies beyond r_max
+  }
+  if (out_any && !overflow) {   // the outside cell: every pair in FP64
+    const int b = __ldg(g.cell_start + g.outside), e = __ldg(g.cell_start + g.outside + 1);
+    for (int j0 = b; j0 < e; j0 += 32) {
+      const int j = j0 + lane;
+      bool in = false;
+      float d = 0.f;
+      if (j < e && j != self) {
+        const double D = canon_d2(Q.q, g.spos[j], g);
+        in = D <= B.r2;
+        d = (float)D;
+      }
+      add(in, d, j);
+    }
+    if (cnt > kKnnCap) overflow = true;
+  }
+  if (overflow) {   // the per-thread kernel takes it
+    if (lane == 0) fallq[1 + atomicAdd(fallq, 1)] = s;
+    return;
+  }
+  __syncwarp();
+  bitonic_padded(key, cnt, lane, 32, WarpSync());
+  // runs of keys closer than the FP32 error bound, up to the K-th (and the
+  // first one past it, which decides who is in), in canonical order
+  const int top = min(cnt, K + 1);
+  if (lane == 0) {
+    int a = 0;
+    while (a < top) {
+      int e = a + 1;
+      while (e < cnt) {
+        const float da = __uint_as_float((unsigned)(key[e - 1] >> 32));
+        const float db = __uint_as_float((unsigned)(key[e] >> 32));
+        const float m = db * 1.000001f;
+        if (db - da > fmaf(pb.c2, m, pb.c1 * sqrtf(m)) + 1e-37f) break;
+        ++e;
+      }
+      if (e - a > 1) {   // insertion sort of [a, e) by (D2, index)
+        for (int i = a + 1; i < e; ++i) {
+          const unsigned long long x = key[i];
+          const int jx = (int)(x & 0xffffffffu);
+          const double Dx = canon_d2(Q.q, g.spos[jx], g);
+          const int ix = __ldg(g.perm + jx);
+          int p = i;
+          while (p > a) {
+            const int jy = (int)(key[p - 1] & 0xffffffffu);
+            const double Dy = canon_d2(Q.q, g.spos[jy], g);
+            if (Dy < Dx || (Dy == Dx && __ldg(g.perm + jy) < ix)) break;
+            key[p] = key[p - 1];
+            --p;
+          }
+          key[p] = x;
+        }
+      }
+      a = e;
+    }
+  }
+  __syncwarp();
+  const int kept = min(cnt, K);
+  const int orig = __ldg(g.perm + s);
+  int *oi = out_ids + (size_t)orig * K;
+  float *od = out_d2 ? out_d2 + (size_t)orig * K : nullptr;
+  for (int k = lane; k < K; k += 32) {
+    const bool have = k < kept;
+    const unsigned long long x = have ? key[k] : 0ull;
+    oi[k] = have ? __ldg(g.perm + (int)(x & 0xffffffffu)) : -1;
+    if (od) od[k] = have ? __uint_as_float((unsigned)(x >> 32)) : __int_as_float(0x7f800000);
+  }
+  if (lane == 0) out_counts[orig] = kept;
+}
+
 }  // namespace si
 
 using namespace si;
@@ -241,8 +472,22 @@ extern "C" si_status si_query_knn(si_grid *g, const float *d_centers, int64_t m,
   const PairBand pb = make_pair_band(lat);
   const size_t smem = (size_t)k * kKnnThreads * 8;
   SI_CUDA_TRY(cudaFuncSetAttribute(k_knn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const unsigned blocks = (unsigned)((m + kKnnThreads - 1) / kKnnThreads);
-  SI_KLAUNCH("k_knn", st, k_knn<<<blocks, kKnnThreads, smem, st>>>(g->dev(), k, dmax_g, n_query, B, pb, flags, d_ids, d_d2,
-                                           d_counts));
+  if (unb) {
+    // no bound: the per-thread walk with the shrinking cut
+    const unsigned blocks = (unsigned)((m + kKnnThreads - 1) / kKnnThreads);
+    SI_KLAUNCH("k_knn", st, k_knn<<<blocks, kKnnThreads, smem, st>>>(g->dev(), k, dmax_g, n_query, B, pb, flags,
+                                                                     d_ids, d_d2, d_counts, nullptr));
+    return SI_OK;
+  }
+  // a warp per query; the queries it hands back go to the per-thread kernel
+  int *fallq = g->longq;   // idle during a K-nearest call
+  SI_CUDA_TRY(cudaMemsetAsync(fallq, 0, sizeof(int), st));
+  const unsigned wblocks = (unsigned)((m + kKnnWarps - 1) / kKnnWarps);
+  SI_KLAUNCH("k_knn_warp", st, k_knn_warp<<<wblocks, kKnnWarps * 32, 0, st>>>(g->dev(), k, dmax_g, n_query, B, pb,
+                                                                              flags, d_ids, d_d2, d_counts, fallq));
+  // sized for every query; blocks past the queue's length exit at once
+  const unsigned fblocks = (unsigned)((m + kKnnThreads - 1) / kKnnThreads);
+  SI_KLAUNCH("k_knn", st, k_knn<<<fblocks, kKnnThreads, smem, st>>>(g->dev(), k, dmax_g, n_query, B, pb, flags,
+                                                                   d_ids, d_d2, d_counts, fallq));
   return SI_OK;
 }

@@ -10,8 +10,8 @@ namespace si {
 // sync() separates the stages.  Every compare-exchange puts the smaller value
 // at the lower index (first step of each merge compares mirrored pairs), so
 // a pair whose upper index is past n never moves anything.
-template <class Sync>
-__device__ __forceinline__ void bitonic_padded(int *a, int n, int rank, int lanes, Sync sync) {
+template <class T, class Sync>
+__device__ __forceinline__ void bitonic_padded(T *a, int n, int rank, int lanes, Sync sync) {
   int lg = 0;
   while ((1 << lg) < n) ++lg;
   const int half = (1 << lg) >> 1;
@@ -22,7 +22,7 @@ __device__ __forceinline__ void bitonic_padded(int *a, int n, int rank, int lane
       const int lo = ((i >> (ks - 1)) << ks) + (i & ((k >> 1) - 1));
       const int hi = (lo & ~(k - 1)) + (k - 1 - (lo & (k - 1)));
       if (hi < n && a[hi] < a[lo]) {
-        const int t = a[lo];
+        const T t = a[lo];
         a[lo] = a[hi];
         a[hi] = t;
       }
@@ -34,7 +34,7 @@ __device__ __forceinline__ void bitonic_padded(int *a, int n, int rank, int lane
         const int lo = ((i >> hs) << (hs + 1)) + (i & (h - 1));
         const int hi = lo + h;
         if (hi < n && a[hi] < a[lo]) {
-          const int t = a[lo];
+          const T t = a[lo];
           a[lo] = a[hi];
           a[hi] = t;
         }

@@ -78,3 +78,15 @@ def test_full_size_4m_config_sampled(k):
     if k == 64:
         # about half the points have fewer than 64 neighbors within 4 cells
         assert 0.3 < (cnt < 64).mean() < 0.7
+
+
+def test_crowded_queries_overflowing_the_warp_buffer():
+    # a tight cluster: its points have ~2000 candidates within r_max, more
+    # than a warp buffers, and are served by the per-thread kernel instead
+    clu = synth.gaussian_mixture_points(2000, 13, n_comp=1, sigma=0.004)
+    uni = synth.uniform_points(3000, 14)
+    pos = np.concatenate([clu, uni]).astype(np.float32)
+    scene = synth.Scene(pos, (0, 0, 0), 1 / 16, (4, 4, 4), 7, 2 / 16)
+    for k in (16, 64):
+        ids, d2, cnt = run_knn(scene, k, scene.r)
+        check(scene, k, scene.r, ids, d2, cnt, np.arange(scene.n))
