@@ -230,8 +230,13 @@ struct KnnRuns {                  // up to two runs per row of a 32-row batch
   int pre[33];
 };
 
+// First pass within dmax1 (n1, B1: its table bound and guard band), a radius
+// expected to hold about 1.5 K points: exact whenever it holds at least K
+// (the K nearest then all lie within it); else a second pass within r_max
+// (dmax_g, n_query, B).  dmax1 == dmax_g: one pass.
 __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, float dmax_g, int n_query,
-                                                            Band B, PairBand pb, unsigned flags,
+                                                            Band B, float dmax1, int n1, Band B1,
+                                                            PairBand pb, unsigned flags,
                                                             int *__restrict__ out_ids,
                                                             float *__restrict__ out_d2,
                                                             int *__restrict__ out_counts,
@@ -250,18 +255,22 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, f
     return;
   }
   const int self = (flags & SI_INCLUDE_SELF) ? -1 : s;
-  const float cut2 = dmax_g * dmax_g;
   const int Gx = 1 << g.wx;
   const bool cyc_x = g.cyc & 1u;
   int cnt = 0;
   bool overflow = false, out_any = false;
-  // every candidate within r_max, decided exactly, into the buffer
   auto add = [&](bool in, float d, int j) {
     const unsigned m = __ballot_sync(0xffffffffu, in);
     const int at = cnt + __popc(m & lt);
     if (in && at < kKnnCap) key[at] = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)j;
     cnt += __popc(m);
   };
+  // every candidate within the cut (cut2 = its square in cell units, n_q its
+  // table bound, Bc its guard band), decided exactly, into the buffer
+  auto gather = [&](float cut2, int n_query, const Band &B) {
+  cnt = 0;
+  overflow = false;
+  out_any = false;
   for (int base = 0; base < g.n_rows && !overflow; base += 32) {
     const int r = base + lane;
     int b0 = 0, l0 = 0, b1 = 0, l1 = 0;
@@ -380,6 +389,9 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, f
     }
     if (cnt > kKnnCap) overflow = true;
   }
+  };
+  gather(dmax1 * dmax1, n1, B1);
+  if (!overflow && cnt < K && dmax1 < dmax_g) gather(dmax_g * dmax_g, n_query, B);
   if (overflow) {   // the per-thread kernel takes it
     if (lane == 0) fallq[1 + atomicAdd(fallq, 1)] = s;
     return;
@@ -389,7 +401,19 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, f
   // runs of keys closer than the FP32 error bound, up to the K-th (and the
   // first one past it, which decides who is in), in canonical order
   const int top = min(cnt, K + 1);
-  if (lane == 0) {
+  bool ties = false;   // an adjacent pair within the bound, up to the (K+1)-th
+  for (int e0 = 1; e0 < min(top + 1, cnt); e0 += 32) {
+    const int e = e0 + lane;
+    bool t = false;
+    if (e < min(top + 1, cnt)) {
+      const float da = __uint_as_float((unsigned)(key[e - 1] >> 32));
+      const float db = __uint_as_float((unsigned)(key[e] >> 32));
+      const float m = db * 1.000001f;
+      t = !(db - da > fmaf(pb.c2, m, pb.c1 * sqrtf(m)) + 1e-37f);
+    }
+    ties |= __any_sync(0xffffffffu, t);
+  }
+  if (ties && lane == 0) {
     int a = 0;
     while (a < top) {
       int e = a + 1;
@@ -479,12 +503,28 @@ extern "C" si_status si_query_knn(si_grid *g, const float *d_centers, int64_t m,
                                                                      d_ids, d_d2, d_counts, nullptr));
     return SI_OK;
   }
+  // first cut: the radius expected to hold 1.5 K + 8 points at the mean load
+  // (exact when it holds K; the kernel widens it to r_max otherwise)
+  float dmax1 = dmax_g;
+  int n1 = n_query;
+  Band B1 = B;
+  const double load = (double)g->n / (double)std::max<int64_t>(g->n_cells - 1, 1);
+  if (load > 0.0) {
+    const double want = 1.5 * k + 8.0;
+    const double r1 = std::cbrt(3.0 * want / (4.0 * M_PI * load)) / (double)lat.inv_s;   // world units
+    if (r1 < 0.9 * (double)r_max_query) {
+      B1 = make_band(lat, (float)r1);
+      dmax1 = (float)r1 * lat.inv_s + (float)lat.eps;
+      n1 = std::min((int)std::floor(dmax1 * dmax1), g->tables.n_max);
+    }
+  }
   // a warp per query; the queries it hands back go to the per-thread kernel
   int *fallq = g->longq;   // idle during a K-nearest call
   SI_CUDA_TRY(cudaMemsetAsync(fallq, 0, sizeof(int), st));
   const unsigned wblocks = (unsigned)((m + kKnnWarps - 1) / kKnnWarps);
-  SI_KLAUNCH("k_knn_warp", st, k_knn_warp<<<wblocks, kKnnWarps * 32, 0, st>>>(g->dev(), k, dmax_g, n_query, B, pb,
-                                                                              flags, d_ids, d_d2, d_counts, fallq));
+  SI_KLAUNCH("k_knn_warp", st, k_knn_warp<<<wblocks, kKnnWarps * 32, 0, st>>>(g->dev(), k, dmax_g, n_query, B, dmax1,
+                                                                              n1, B1, pb, flags, d_ids, d_d2,
+                                                                              d_counts, fallq));
   // sized for every query; blocks past the queue's length exit at once
   const unsigned fblocks = (unsigned)((m + kKnnThreads - 1) / kKnnThreads);
   SI_KLAUNCH("k_knn", st, k_knn<<<fblocks, kKnnThreads, smem, st>>>(g->dev(), k, dmax_g, n_query, B, pb, flags,
