@@ -644,6 +644,7 @@ static void grid_free(si_grid *g) {
   cudaFree(g->over);
   cudaFree(g->denseq);
   cudaFree(g->lightq);
+  cudaFree(g->lstage);
   cudaFree(g->cell_rec);
   cudaFree(g->scr_top);
   cudaFree(g->scratch);

@@ -145,6 +145,7 @@ struct si_grid {
   int *over = nullptr;           // [0] = count, then sorted slots of queries the cell kernel handed back
   int *denseq = nullptr;         // [0] = count, then sorted slots of the queries of dense cells (set by build)
   int *lightq = nullptr;         // [0] = count, then sorted slots of the queries of light cells (set by build)
+  int *lstage = nullptr;         // kInlineSort x cap: short lists kept by the count pass (allocated on first use)
   unsigned char *cell_cls = nullptr;   // per cell: kCellLight / kCellHeavy / kCellDense (set by build)
   unsigned char *slot_cls = nullptr;   // per sorted slot: its cell's class (set by build)
   long long *cell_rec = nullptr; // per heavy cell: its record in the scratch buffer (-1: per-query path)

@@ -76,6 +76,42 @@ struct WriteVisitor {
   }
 };
 
+// Count pass that also keeps a short list: hits are counted, and the first
+// kInlineSort ids are kept sorted in the thread's shared slots (`stride`
+// apart), so that the write pass can copy a list of up to kInlineSort ids
+// instead of walking the cells again.
+struct StageVisitor {
+  const GridDev &g;
+  const QueryGeom &Q;
+  const Band &B;
+  int self;
+  int *out;
+  int stride;
+  int k;           // hits so far
+  __device__ __forceinline__ void hit(int id) {
+    if (k < kInlineSort) {
+      int p = k;
+      while (p > 0) {
+        const int prev = out[(p - 1) * stride];
+        if (prev <= id) break;
+        out[p * stride] = prev;
+        --p;
+      }
+      out[p * stride] = id;
+    }
+    ++k;
+  }
+  __device__ __forceinline__ void operator()(const Target &t, bool full, int b, int e) {
+    for (int j = b; j < e; ++j) {
+      if (j == self) continue;
+      if (full || pair_hit(g, Q, t, B, g.spos[j])) hit(__ldg(g.perm + j));
+    }
+  }
+  __device__ __forceinline__ void operator()(const Target &t, bool full) {
+    (*this)(t, full, __ldg(g.cell_start + t.key), __ldg(g.cell_start + t.key + 1));
+  }
+};
+
 // Cell walks of the per-query kernels.
 enum Walk : int { kWalkPaper = 0, kWalkClasses = 1, kWalkCube = 2 };
 
@@ -92,10 +128,14 @@ __device__ __forceinline__ void walk_one(const GridDev &g, const QueryGeom &Q, c
 // stage (nullable): this thread's kInlineSort shared slots, `stride` apart;
 // short lists are sorted there and stored once.
 template <bool WRITE, int WALK>
+// lstage (nullable, with stage): the short-list staging area, column
+// `column` of kInlineSort rows `lstride` apart; the count pass stores lists of
+// up to kInlineSort ids there, sorted, and the write pass copies them.
 __device__ __forceinline__ void radius_one(const GridDev &g, const WalkParams &P, const Band &B,
                                            unsigned flags, int s, unsigned skip, long long *counts,
                                            const long long *offsets, int *ids, long long cap,
-                                           int *longq, int *stage = nullptr, int stride = 0) {
+                                           int *longq, int *stage = nullptr, int stride = 0,
+                                           int *lstage = nullptr, long long lstride = 0, int column = 0) {
   if (skip) {
     const int c = g.slot_cls[s];
     if (((c == kCellHeavy || c == kCellHeavyBig) && (skip & 1u)) || (c == kCellDense && (skip & 2u))) return;
@@ -104,15 +144,27 @@ __device__ __forceinline__ void radius_one(const GridDev &g, const WalkParams &P
   const int self = (flags & SI_INCLUDE_SELF) ? -1 : s;
   const int orig = __ldg(g.perm + s);
   if (!WRITE) {
-    CountVisitor v{g, Q, B, self, 0};
-    walk_one<WALK>(g, Q, P, v);
-    counts[orig] = v.count;
+    if (lstage && stage) {
+      StageVisitor v{g, Q, B, self, stage, stride, 0};
+      walk_one<WALK>(g, Q, P, v);
+      counts[orig] = v.k;
+      if (v.k <= kInlineSort)
+        for (int i = 0; i < v.k; ++i) lstage[i * lstride + column] = stage[i * stride];
+    } else {
+      CountVisitor v{g, Q, B, self, 0};
+      walk_one<WALK>(g, Q, P, v);
+      counts[orig] = v.count;
+    }
   } else {
     const long long base = offsets[orig];
     const int len = (int)(offsets[orig + 1] - base);
     if (len == 0) return;
     if (base + len > cap) {
       atomicOr(g.status, ST_CAPACITY);
+      return;
+    }
+    if (lstage && len <= kInlineSort) {   // kept, sorted, by the count pass
+      for (int i = 0; i < len; ++i) ids[base + i] = lstage[i * lstride + column];
       return;
     }
     const bool sort_all = !(flags & SI_NO_SORT);
@@ -150,12 +202,14 @@ __global__ void __launch_bounds__(kClassThreads) k_radius_cls(GridDev g, WalkPar
                                                               int n_entries, long long *counts,
                                                               const long long *offsets, int *ids,
                                                               long long cap, int *longq,
-                                                              const int *__restrict__ list) {
+                                                              const int *__restrict__ list, int *lstage,
+                                                              long long lstride) {
   extern __shared__ __align__(16) unsigned long long cls_smem[];
   const int nbeg = g.cls_q * g.cls_q * g.cls_q + 1;
   int *beg_smem = reinterpret_cast<int *>(cls_smem + n_entries);
-  // write pass: short lists are sorted in shared slots, column-interleaved
-  int *stage = WRITE ? beg_smem + ((nbeg + 3) & ~3) + threadIdx.x : nullptr;
+  // short lists are sorted in shared slots, column-interleaved (write pass;
+  // with lstage, the count pass, which keeps them for the write pass)
+  int *stage = (WRITE || lstage) ? beg_smem + ((nbeg + 3) & ~3) + threadIdx.x : nullptr;
   for (int i = threadIdx.x; i < n_entries; i += blockDim.x) cls_smem[i] = __ldg(g.cls + i);
   for (int i = threadIdx.x; i < nbeg; i += blockDim.x) beg_smem[i] = __ldg(g.cls_begin + i);
   __syncthreads();
@@ -167,7 +221,7 @@ __global__ void __launch_bounds__(kClassThreads) k_radius_cls(GridDev g, WalkPar
   const int nl = list ? list[0] : g.n;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nl; t += gridDim.x * blockDim.x)
     radius_one<WRITE, kWalkClasses>(gs, P, B, flags, list ? list[1 + t] : t, list ? 0u : skip, counts, offsets,
-                                    ids, cap, longq, stage, kClassThreads);
+                                    ids, cap, longq, stage, kClassThreads, lstage, lstride, t);
 }
 
 // Queries of dense cells (queued at binning): one warp per query.
@@ -527,7 +581,7 @@ static si_status launch_light(int walk, const si_grid *gr, const GridDev &dv, co
     const int nbeg = gr->cls_q * gr->cls_q * gr->cls_q + 1;
     const size_t smem = gr->cls_host.size() * sizeof(unsigned long long) +
                         (size_t)((nbeg + 3) & ~3) * sizeof(int) +
-                        (WRITE ? (size_t)kInlineSort * kClassThreads * sizeof(int) : 0);
+                        ((WRITE || gr->lstage) ? (size_t)kInlineSort * kClassThreads * sizeof(int) : 0);
     SI_CUDA_TRY(cudaFuncSetAttribute(k_radius_cls<WRITE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     int per_sm = 0;
@@ -537,7 +591,7 @@ static si_status launch_light(int walk, const si_grid *gr, const GridDev &dv, co
     SI_KLAUNCH(WRITE ? "k_radius_write" : "k_radius_count", st,
                k_radius_cls<WRITE><<<grid, kClassThreads, smem, st>>>(
                    dv, P, B, flags, skip, (int)gr->cls_host.size(), counts, off, ids, cap, longq,
-                   skip == 3u ? gr->lightq : nullptr));
+                   skip == 3u ? gr->lightq : nullptr, gr->lstage, (long long)gr->cap));
   } else if (walk == kWalkClasses) {
     SI_KLAUNCH(WRITE ? "k_radius_write_cls_l2" : "k_radius_count_cls_l2", st,
                k_radius<WRITE, kWalkClasses><<<blocks, kQueryThreads, 0, st>>>(
@@ -594,6 +648,14 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   // the cell path holds the runs of the whole cell-level sphere (rows of
   // cells with b^2 <= floor(d^2), at most two runs per row and the outside cell)
   const bool heavy = !cube && g->ensure_cell_rows(P.dg, st) && 2 * g->n_crow + 1 <= kCellTCap;
+  // the count pass keeps short lists for the write pass in a staging area
+  // (allocated on first use; without it the write pass walks every list again)
+  if (walk == kWalkClasses && g->cls_smem_bytes > 0 && !g->lstage && g->cap > 0) {
+    if (cudaMalloc((void **)&g->lstage, (size_t)kInlineSort * (size_t)g->cap * sizeof(int)) != cudaSuccess) {
+      g->lstage = nullptr;
+      cudaGetLastError();
+    }
+  }
   const GridDev dv = g->dev();
   const unsigned skip = (heavy ? 1u : 0u) | (dense_path(walk, g) ? 2u : 0u);
   long long *off = (long long *)d_offsets;
