@@ -405,6 +405,23 @@ def make_work(name):
     raise SystemExit(f"unknown workload {name}")
 
 
+def slowest_rank_ms(ms_step: float, device: str = "cuda") -> float:
+    """The job's step time: the slowest rank's (max over ranks; the rank's own
+    time when there is one rank or no process group)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms_step
+    t = torch.tensor([ms_step], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(queries_per_rank: int, world: int, ms_step: float) -> float:
+    """Whole-job throughput: every rank serves its own replica of the workload."""
+    return queries_per_rank * world / (ms_step * 1e-3)
+
+
 def time_steps(work, steps, warmup, flush):
     import torch
     st = torch.cuda.current_stream()
@@ -543,12 +560,8 @@ def main():
         ms = time_steps(work, args.steps, args.warmup, flush)
     launches = (launch_count() - l0) // (args.steps + args.warmup)
     work.check()
-    ms_step = float(np.mean(ms))
-    if world > 1:
-        t = torch.tensor([ms_step], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = work.queries * world / (ms_step * 1e-3)
+    ms_step = slowest_rank_ms(float(np.mean(ms)))
+    value = job_value(work.queries, world, ms_step)
     # per-kernel timing pass (CUDA events around each launch, same stream)
     lib.si_kernel_timing_enable(1)
     kernel_report(lib)
