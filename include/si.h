@@ -117,10 +117,19 @@ si_status si_grid_sync(si_grid *g, void *stream);
 si_status si_grid_get_info(const si_grid *g, si_grid_info *info);
 si_status si_grid_destroy(si_grid *g);
 
-/* All-agents fixed-radius query (Sec. I: every agent queries its
- * neighborhood; Sec. II.A: x <= d).  Query k is point k of the last build;
- * its own index is excluded unless SI_INCLUDE_SELF.
- * d_centers must be NULL (all agents) and m must equal the grid's n.
+/* Fixed-radius query (Sec. I: every agent queries its neighborhood;
+ * Sec. II.A: x <= d).
+ * d_centers NULL: all agents; query k is point k of the last build, m must
+ * equal the grid's n, and a point's own index is excluded unless
+ * SI_INCLUDE_SELF.
+ * d_centers non-NULL: m query centers (m * 4 floats, device, 16-byte
+ * aligned, the fourth lane unread); no index is excluded (SI_INCLUDE_SELF
+ * has no effect).  A center outside the region on a non-cyclic axis is
+ * answered like any other.  A center with a non-finite coordinate, or
+ * outside its box on a cyclic axis, gets an empty list and makes the grid
+ * record SI_ERR_INVALID (returned by the next si_grid_sync).  The first call
+ * with more centers than any before allocates the grid's center buffers
+ * (about 44 bytes per center, plus 128 with the class tables in use).
  * Output: CSR in input order, d_offsets[m + 1] (int64, device) and d_ids
  * (int32, device, capacity ids_capacity); ids ascending per query unless
  * SI_NO_SORT.  r must satisfy 0 <= r <= r_max.
@@ -132,8 +141,11 @@ si_status si_query_radius(si_grid *g, const float *d_centers, int64_t m, float r
                           uint32_t flags, int64_t *d_offsets, int32_t *d_ids,
                           int64_t ids_capacity, int64_t *h_total, void *stream);
 
-/* All-agents K-nearest query (Sec. II.A, last paragraph: once K neighbors are
- * found the search radius shrinks to the K-th distance; Sec. IV.B).
+/* K-nearest query (Sec. II.A, last paragraph: once K neighbors are found
+ * the search radius shrinks to the K-th distance; Sec. IV.B), for all agents
+ * (d_centers NULL, m = the grid's n; own index excluded unless
+ * SI_INCLUDE_SELF) or for m query centers (as in si_query_radius; a center
+ * with invalid coordinates gets count 0, ids -1 and d2 +inf).
  * Up to k (1 <= k <= 64) nearest points within r_max_query (inclusive), ordered
  * by (canonical D2, index); d_ids[m * k] int32 padded with -1, d_d2[m * k]
  * float (nullable; FP32 rounding of the canonical D2, +inf padding), and

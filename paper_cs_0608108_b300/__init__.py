@@ -31,6 +31,16 @@ def _check_points(pos: torch.Tensor) -> torch.Tensor:
     return pos.contiguous()
 
 
+def _centers(centers):
+    """(tensor whose pointer is passed, m) for a centers argument.  A NULL
+    pointer means all agents, so an empty centers tensor passes a one-row
+    buffer (never read) with m = 0."""
+    c = _check_points(centers)
+    if c.shape[0] == 0:
+        return torch.zeros((1, 4), dtype=torch.float32, device=c.device), 0
+    return c, c.shape[0]
+
+
 class _CudaArray:
     def __init__(self, ptr, shape, typestr):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
@@ -121,26 +131,31 @@ class Grid:
     # -- queries -------------------------------------------------------------
     def query_radius(self, r: float, include_self: bool = False, method: str = "sphere",
                      sort: bool = True, out_offsets=None, out_ids=None, sync_total: bool = True,
-                     walk: str = "classes"):
-        """All-agents radius query.  Returns (offsets int64[n+1], ids int32[total]).
-        method "sphere" (spherical index) or "cube" (bin-lattice scan); walk
-        "classes" (sub-cell class tables) or "paper" (Sec. III.A 64 tables)."""
+                     walk: str = "classes", centers=None):
+        """Radius query.  Returns (offsets int64[m+1], ids int32[total]).
+        centers None: all agents (query k is point k, m = n); else a CUDA
+        float32 (m, 4) tensor of query centers.  method "sphere" (spherical
+        index) or "cube" (bin-lattice scan); walk "classes" (sub-cell class
+        tables) or "paper" (Sec. III.A 64 tables)."""
         flags = (N.SI_INCLUDE_SELF if include_self else 0) | \
                 (N.SI_METHOD_CUBE if method == "cube" else 0) | (0 if sort else N.SI_NO_SORT) | \
                 (N.SI_WALK_PAPER if walk == "paper" else 0)
         dev = self._pos.device
-        off = out_offsets if out_offsets is not None else torch.empty(self.n + 1, dtype=torch.int64, device=dev)
+        m = self.n
+        if centers is not None:
+            centers, m = _centers(centers)
+        off = out_offsets if out_offsets is not None else torch.empty(m + 1, dtype=torch.int64, device=dev)
         ids = out_ids
         if ids is None:
-            cap = self._ids_cap or max(16 * self.n, 1024)
+            cap = self._ids_cap or max(16 * m, 1024)
             ids = torch.empty(cap, dtype=torch.int32, device=dev)
         total = ctypes.c_int64(0)
-        st = self._lib.si_query_radius(self._h, None, self.n, float(r), flags, _ptr(off), _ptr(ids),
+        st = self._lib.si_query_radius(self._h, _ptr(centers), m, float(r), flags, _ptr(off), _ptr(ids),
                                        ids.numel(), ctypes.byref(total) if sync_total else None,
                                        _stream())
         if st == N.SI_ERR_CAPACITY and out_ids is None:
             ids = torch.empty(max(int(total.value), 1), dtype=torch.int32, device=dev)
-            st = self._lib.si_query_radius(self._h, None, self.n, float(r), flags, _ptr(off),
+            st = self._lib.si_query_radius(self._h, _ptr(centers), m, float(r), flags, _ptr(off),
                                            _ptr(ids), ids.numel(), ctypes.byref(total), _stream())
         N.check(st, "si_query_radius")
         if sync_total:
@@ -149,19 +164,24 @@ class Grid:
         return off, ids
 
     def query_knn(self, k: int, r_max=None, include_self: bool = False, with_d2: bool = True,
-                  out=None):
-        """All-agents K nearest within r_max (None = grid's whole region).
-        Returns (ids int32[n,k] padded -1, d2 float32[n,k] or None, counts int32[n])."""
+                  out=None, centers=None):
+        """K nearest within r_max (None = grid's whole region), for every point
+        (centers None) or for each row of a CUDA float32 (m, 4) tensor of
+        query centers.  Returns (ids int32[m,k] padded -1, d2 float32[m,k]
+        or None, counts int32[m])."""
         dev = self._pos.device
+        m = self.n
+        if centers is not None:
+            centers, m = _centers(centers)
         if out is None:
-            ids = torch.empty((self.n, k), dtype=torch.int32, device=dev)
-            d2 = torch.empty((self.n, k), dtype=torch.float32, device=dev) if with_d2 else None
-            cnt = torch.empty(self.n, dtype=torch.int32, device=dev)
+            ids = torch.empty((m, k), dtype=torch.int32, device=dev)
+            d2 = torch.empty((m, k), dtype=torch.float32, device=dev) if with_d2 else None
+            cnt = torch.empty(m, dtype=torch.int32, device=dev)
         else:
             ids, d2, cnt = out
         rm = float("inf") if r_max is None else float(r_max)
         flags = N.SI_INCLUDE_SELF if include_self else 0
-        N.check(self._lib.si_query_knn(self._h, None, self.n, int(k), rm, flags, _ptr(ids), _ptr(d2),
+        N.check(self._lib.si_query_knn(self._h, _ptr(centers), m, int(k), rm, flags, _ptr(ids), _ptr(d2),
                                        _ptr(cnt), _stream()), "si_query_knn")
         return ids, d2, cnt
 

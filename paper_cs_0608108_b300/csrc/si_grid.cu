@@ -326,6 +326,9 @@ void fill_griddev(const Lattice &lat, const DevTables &t, GridDev &g) {
   g.W = lat.W;
   g.cyc = lat.cyc;
   g.outside = 1u << lat.W;
+  g.qpos = nullptr;   // set with the arrays (si_grid::dev, or the query-center path)
+  g.qid = nullptr;
+  g.q_agents = 1;
   const int pos[3] = {0, lat.W + lat.w[0], lat.w[0] + lat.w[1]};
   unsigned long long valid = 0, guard[3], non = 0;
   for (int a = 0; a < 3; ++a) {
@@ -621,6 +624,9 @@ si::GridDev si_grid::dev() const {
   g.cls_q = cls_q;
   g.crow = crow;
   g.n_crow = n_crow;
+  g.qpos = spos;
+  g.qid = perm;
+  g.q_agents = 1;
   return g;
 }
 
@@ -653,6 +659,17 @@ static void grid_free(si_grid *g) {
   cudaFree(g->cls);
   cudaFree(g->cls_begin);
   cudaFree(g->crow);
+  cudaFree(g->cpos);
+  cudaFree(g->cid);
+  cudaFree(g->ckey);
+  cudaFree(g->cbuck);
+  cudaFree(g->cscan);
+  cudaFree(g->cscan64);
+  cudaFree(g->clist0);
+  cudaFree(g->clist1);
+  cudaFree(g->clong);
+  cudaFree(g->chuge);
+  cudaFree(g->cstage);
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
   free_tables(g->tables);
   delete g;

@@ -120,6 +120,23 @@ int64_t class_capacity(const Lattice &lat, int64_t table_entries);
 void build_class_tables(const Lattice &lat, double dg, int q, std::vector<unsigned long long> &ent,
                         std::vector<int> &begin);
 
+// Outputs a query-center call gives a center it cannot query (a non-finite
+// coordinate, or one outside its box on a cyclic axis): an empty result.
+struct CenterOut {
+  long long *rad_counts = nullptr;   // radius: per-center counts (offsets + 1)
+  int K = 0;                         // K nearest: ids (-1), d2 (+inf, nullable), counts (0)
+  int *ids = nullptr;
+  float *d2 = nullptr;
+  int *counts = nullptr;
+};
+
+// Query centers (si_centers.cu): sort the m centers (device float4) by
+// coarse cell into the grid's center buffers and list them (clist0: the
+// centers of light cells, or every valid center unless `split`; clist1: the
+// rest), then set dv to the grid's view with that query set.
+si_status prepare_centers(si_grid *g, const float *d_centers, int64_t m, bool split, bool stage,
+                          const CenterOut &out, GridDev &dv, cudaStream_t st);
+
 }  // namespace si
 
 struct si_grid {
@@ -173,5 +190,20 @@ struct si_grid {
   double *partial = nullptr;     // reduce partial sums
   int64_t partial_len = 0;
   long long *h_pinned = nullptr; // pinned host scratch (2 values)
+  // query centers in coarse cell order (si_centers.cu), grown on demand
+  int64_t ccap = 0;
+  float4 *cpos = nullptr;        // ccap: positions
+  int *cid = nullptr;            // ccap: input index of each
+  uint2 *ckey = nullptr;         // ccap: (bucket, rank in bucket)
+  int *cbuck = nullptr;          // bucket starts ([0] = 0, then inclusive counts)
+  int *cscan = nullptr;          // their scan scratch
+  long long *cscan64 = nullptr;  // scan scratch for ccap per-center counts
+  int *clist0 = nullptr;         // ccap + 1: [0] = count, then slots (light group)
+  int *clist1 = nullptr;         // ccap + 1: the warp-per-center group
+  int *clong = nullptr;          // ccap + 1: long lists to sort; K nearest: the per-thread fallback queue
+  int *chuge = nullptr;          // ccap + 1: lists too long for a warp sort
+  int *cstage = nullptr;         // kInlineSort x cstage_cap: short lists kept by the count pass
+  int64_t cstage_cap = 0;
+  si_status ensure_centers(int64_t m, bool stage);
   si::GridDev dev() const;
 };

@@ -73,9 +73,21 @@ struct GridDev {
   const RowEntry *rows;            // x-rows sorted by b2 (K-nearest walk)
   int n_rows;
   int row_lim_x;                   // |ox| bound of the rows' x extent
+  // the query set: positions in walk order and the output row of each; the
+  // grid's own sorted points (all-agents mode, q_agents = 1: query s is
+  // point s and leaves itself out of its list unless SI_INCLUDE_SELF) or
+  // caller-given centers sorted by cell (q_agents = 0)
+  const float4 *qpos;
+  const int *qid;
+  int q_agents;
 };
 
 enum : int { ST_INVALID = 1, ST_CAPACITY = 2, ST_INTERNAL = 4, ST_TIMEOUT = 8 };
+
+// The sorted slot query s must leave out of its own list, or -1.
+__device__ __forceinline__ int query_self(const GridDev &g, unsigned flags, int s) {
+  return (g.q_agents && !(flags & SI_INCLUDE_SELF)) ? s : -1;
+}
 
 // Inclusive warp scan of one int per lane (all 32 lanes take part).
 __device__ __forceinline__ int warp_incl_scan_i(int v) {

@@ -82,8 +82,8 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(GridDev g, int K, float dma
   const int ti = blockIdx.x * T + threadIdx.x;
   if (ti >= (list ? list[0] : g.n)) return;
   const int s = list ? list[1 + ti] : ti;
-  const QueryGeom Q = make_geom(g.spos[s], g);
-  const int self = (flags & SI_INCLUDE_SELF) ? -1 : s;
+  const QueryGeom Q = make_geom(g.qpos[s], g);
+  const int self = query_self(g, flags, s);
   int cnt = 0;
   float cut2 = dmax_g * dmax_g;          // cell units: walk cut on b2 and t2
   float kth_hi = fmaxf(B.hi, B.hi_w);    // world units: candidate filter
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(GridDev g, int K, float dma
     walk_cube(g, Q, dmax_g, v);
   }
 
-  const int orig = __ldg(g.perm + s);
+  const int orig = __ldg(g.qid + s);
   int *oi = out_ids + (size_t)orig * K;
   for (int k = 0; k < K; ++k) oi[k] = k < cnt ? __ldg(g.perm + L.j[L.at(k)]) : -1;
   if (out_d2) {
@@ -233,28 +233,31 @@ struct KnnRuns {                  // up to two runs per row of a 32-row batch
 // First pass within dmax1 (n1, B1: its table bound and guard band), a radius
 // expected to hold about 1.5 K points: exact whenever it holds at least K
 // (the K nearest then all lie within it); else a second pass within r_max
-// (dmax_g, n_query, B).  dmax1 == dmax_g: one pass.
+// (dmax_g, n_query, B).  dmax1 == dmax_g: one pass.  list (nullable): [0] =
+// count, then the sorted slots to serve; else every slot.
 __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, float dmax_g, int n_query,
                                                             Band B, float dmax1, int n1, Band B1,
                                                             PairBand pb, unsigned flags,
                                                             int *__restrict__ out_ids,
                                                             float *__restrict__ out_d2,
                                                             int *__restrict__ out_counts,
-                                                            int *__restrict__ fallq) {
+                                                            int *__restrict__ fallq,
+                                                            const int *__restrict__ list) {
   __shared__ unsigned long long keys[kKnnWarps][kKnnCap];
   __shared__ KnnRuns runs[kKnnWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int s = blockIdx.x * kKnnWarps + w;   // the warp's query (sorted slot)
-  if (s >= g.n) return;
+  const int item = blockIdx.x * kKnnWarps + w;
+  if (item >= (list ? list[0] : g.n)) return;
+  const int s = list ? list[1 + item] : item;   // the warp's query (sorted slot)
   unsigned long long *key = keys[w];
   KnnRuns &R = runs[w];
   const unsigned lt = (1u << lane) - 1u;
-  const QueryGeom Q = make_geom(g.spos[s], g);
+  const QueryGeom Q = make_geom(g.qpos[s], g);
   if (Q.outside) {   // the bounding-cube walk of the per-thread kernel
     if (lane == 0) fallq[1 + atomicAdd(fallq, 1)] = s;
     return;
   }
-  const int self = (flags & SI_INCLUDE_SELF) ? -1 : s;
+  const int self = query_self(g, flags, s);
   const int Gx = 1 << g.wx;
   const bool cyc_x = g.cyc & 1u;
   int cnt = 0;
@@ -446,7 +449,7 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, f
   }
   __syncwarp();
   const int kept = min(cnt, K);
-  const int orig = __ldg(g.perm + s);
+  const int orig = __ldg(g.qid + s);
   int *oi = out_ids + (size_t)orig * K;
   float *od = out_d2 ? out_d2 + (size_t)orig * K : nullptr;
   for (int k = lane; k < K; k += 32) {
@@ -466,8 +469,12 @@ extern "C" si_status si_query_knn(si_grid *g, const float *d_centers, int64_t m,
                                   float r_max_query, uint32_t flags, int32_t *d_ids, float *d_d2,
                                   int32_t *d_counts, void *stream) {
   if (!g) return fail(SI_ERR_INVALID, "null grid");
-  if (d_centers) return fail(SI_ERR_INVALID, "only the all-agents mode is supported (centers must be NULL)");
-  if (m != g->n) return fail(SI_ERR_INVALID, "all-agents mode: m must equal the grid's point count");
+  if (d_centers) {
+    if (m < 0 || m > (int64_t)INT32_MAX - 1) return fail(SI_ERR_INVALID, "m out of range");
+    if ((uintptr_t)d_centers & 15u) return fail(SI_ERR_INVALID, "centers must be a 16-byte aligned float4 array");
+  } else if (m != g->n) {
+    return fail(SI_ERR_INVALID, "all-agents mode: m must equal the grid's point count");
+  }
   if (k < 1 || k > 64) return fail(SI_ERR_INVALID, "k must be in [1, 64]");
   if (!d_ids || !d_counts) return fail(SI_ERR_INVALID, "null output");
   if (flags & ~(SI_INCLUDE_SELF)) return fail(SI_ERR_INVALID, "unknown flags");
@@ -496,11 +503,27 @@ extern "C" si_status si_query_knn(si_grid *g, const float *d_centers, int64_t m,
   const PairBand pb = make_pair_band(lat);
   const size_t smem = (size_t)k * kKnnThreads * 8;
   SI_CUDA_TRY(cudaFuncSetAttribute(k_knn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // the query set: the grid's points, or the caller's centers in coarse
+  // cell order (listed; those with invalid coordinates get empty results)
+  GridDev dv = g->dev();
+  const int *list = nullptr;
+  int *fallq = g->longq;   // idle during a K-nearest call
+  if (d_centers) {
+    CenterOut eo;
+    eo.K = k;
+    eo.ids = d_ids;
+    eo.d2 = d_d2;
+    eo.counts = d_counts;
+    si_status s = prepare_centers(g, d_centers, m, false, false, eo, dv, st);
+    if (s != SI_OK) return s;
+    list = g->clist0;
+    fallq = g->clong;
+  }
   if (unb) {
     // no bound: the per-thread walk with the shrinking cut
     const unsigned blocks = (unsigned)((m + kKnnThreads - 1) / kKnnThreads);
-    SI_KLAUNCH("k_knn", st, k_knn<<<blocks, kKnnThreads, smem, st>>>(g->dev(), k, dmax_g, n_query, B, pb, flags,
-                                                                     d_ids, d_d2, d_counts, nullptr));
+    SI_KLAUNCH("k_knn", st, k_knn<<<blocks, kKnnThreads, smem, st>>>(dv, k, dmax_g, n_query, B, pb, flags,
+                                                                     d_ids, d_d2, d_counts, list));
     return SI_OK;
   }
   // first cut: the radius expected to hold 1.5 K + 8 points at the mean load
@@ -519,15 +542,14 @@ extern "C" si_status si_query_knn(si_grid *g, const float *d_centers, int64_t m,
     }
   }
   // a warp per query; the queries it hands back go to the per-thread kernel
-  int *fallq = g->longq;   // idle during a K-nearest call
   SI_CUDA_TRY(cudaMemsetAsync(fallq, 0, sizeof(int), st));
   const unsigned wblocks = (unsigned)((m + kKnnWarps - 1) / kKnnWarps);
-  SI_KLAUNCH("k_knn_warp", st, k_knn_warp<<<wblocks, kKnnWarps * 32, 0, st>>>(g->dev(), k, dmax_g, n_query, B, dmax1,
+  SI_KLAUNCH("k_knn_warp", st, k_knn_warp<<<wblocks, kKnnWarps * 32, 0, st>>>(dv, k, dmax_g, n_query, B, dmax1,
                                                                               n1, B1, pb, flags, d_ids, d_d2,
-                                                                              d_counts, fallq));
+                                                                              d_counts, fallq, list));
   // sized for every query; blocks past the queue's length exit at once
   const unsigned fblocks = (unsigned)((m + kKnnThreads - 1) / kKnnThreads);
-  SI_KLAUNCH("k_knn", st, k_knn<<<fblocks, kKnnThreads, smem, st>>>(g->dev(), k, dmax_g, n_query, B, pb, flags,
+  SI_KLAUNCH("k_knn", st, k_knn<<<fblocks, kKnnThreads, smem, st>>>(dv, k, dmax_g, n_query, B, pb, flags,
                                                                    d_ids, d_d2, d_counts, fallq));
   return SI_OK;
 }

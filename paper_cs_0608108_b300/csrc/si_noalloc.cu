@@ -183,6 +183,8 @@ extern "C" si_status si_neighbor_energy_noalloc(const si_grid_desc *desc, const 
   fill_griddev(lat, none, g);
   g.spos = spos;
   g.perm = perm;
+  g.qpos = spos;
+  g.qid = perm;
   g.cell_start = start;
   g.n = (int)n;
   g.status = status;

@@ -140,9 +140,9 @@ __device__ __forceinline__ void radius_one(const GridDev &g, const WalkParams &P
     const int c = g.slot_cls[s];
     if (((c == kCellHeavy || c == kCellHeavyBig) && (skip & 1u)) || (c == kCellDense && (skip & 2u))) return;
   }
-  const QueryGeom Q = make_geom(g.spos[s], g);
-  const int self = (flags & SI_INCLUDE_SELF) ? -1 : s;
-  const int orig = __ldg(g.perm + s);
+  const QueryGeom Q = make_geom(g.qpos[s], g);
+  const int self = query_self(g, flags, s);
+  const int orig = __ldg(g.qid + s);
   if (!WRITE) {
     if (lstage && stage) {
       StageVisitor v{g, Q, B, self, stage, stride, 0};
@@ -182,14 +182,16 @@ __device__ __forceinline__ void radius_one(const GridDev &g, const WalkParams &P
   }
 }
 
+// list (nullable): [0] = count, then the sorted slots to serve; else every slot.
 template <bool WRITE, int WALK>
 __global__ void __launch_bounds__(kQueryThreads) k_radius(GridDev g, WalkParams P, Band B, unsigned flags,
                                                           unsigned skip, long long *counts,
                                                           const long long *offsets, int *ids,
-                                                          long long cap, int *longq) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= g.n) return;
-  radius_one<WRITE, WALK>(g, P, B, flags, s, skip, counts, offsets, ids, cap, longq);
+                                                          long long cap, int *longq,
+                                                          const int *__restrict__ list) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (list ? list[0] : g.n)) return;
+  radius_one<WRITE, WALK>(g, P, B, flags, list ? list[1 + t] : t, skip, counts, offsets, ids, cap, longq);
 }
 
 // Per-query kernel with the class tables staged in shared memory: a
@@ -431,9 +433,9 @@ __global__ void __launch_bounds__(kClassThreads, 4) k_radius_dense(GridDev g, Wa
   FlatRuns &R = runs[w];
   for (int item = blockIdx.x * nwb + w; item < nq; item += gridDim.x * nwb) {
     const int s = denseq[1 + item];
-    const QueryGeom Q = make_geom(g.spos[s], g);
-    const int self = (flags & SI_INCLUDE_SELF) ? -1 : s;
-    const int orig = __ldg(g.perm + s);
+    const QueryGeom Q = make_geom(g.qpos[s], g);
+    const int self = query_self(g, flags, s);
+    const int orig = __ldg(g.qid + s);
     if (!WRITE) {
       long long count = 0;
       if (Q.outside) {
@@ -568,20 +570,24 @@ static WalkParams walk_params(const Lattice &lat, float r, bool inclusion) {
 // warp-per-query kernels for dense cells.
 static bool dense_path(int walk, const si_grid *gr) { return walk == kWalkClasses && gr->cls_smem_bytes > 0; }
 
+// The per-thread query kernels.  list (nullable): [0] = count, then the
+// slots to serve; else every slot of dv's query set, skipping by class byte.
+// lstage (nullable): the short-list staging area, lstride slots per row.
 template <bool WRITE>
 static si_status launch_light(int walk, const si_grid *gr, const GridDev &dv, const WalkParams &P,
                               const Band &B, unsigned flags, unsigned skip, long long *counts,
                               const long long *off, int *ids, long long cap, int *longq,
-                              unsigned blocks, cudaStream_t st) {
+                              unsigned blocks, const int *list, int *lstage, long long lstride,
+                              cudaStream_t st) {
   if (walk == kWalkCube) {
     SI_KLAUNCH(WRITE ? "k_radius_write_cube" : "k_radius_count_cube", st,
                k_radius<WRITE, kWalkCube><<<blocks, kQueryThreads, 0, st>>>(dv, P, B, flags, 0, counts,
-                                                                            off, ids, cap, longq));
+                                                                            off, ids, cap, longq, list));
   } else if (walk == kWalkClasses && gr->cls_smem_bytes > 0) {
     const int nbeg = gr->cls_q * gr->cls_q * gr->cls_q + 1;
     const size_t smem = gr->cls_host.size() * sizeof(unsigned long long) +
                         (size_t)((nbeg + 3) & ~3) * sizeof(int) +
-                        ((WRITE || gr->lstage) ? (size_t)kInlineSort * kClassThreads * sizeof(int) : 0);
+                        ((WRITE || lstage) ? (size_t)kInlineSort * kClassThreads * sizeof(int) : 0);
     SI_CUDA_TRY(cudaFuncSetAttribute(k_radius_cls<WRITE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     int per_sm = 0;
@@ -591,22 +597,23 @@ static si_status launch_light(int walk, const si_grid *gr, const GridDev &dv, co
     SI_KLAUNCH(WRITE ? "k_radius_write" : "k_radius_count", st,
                k_radius_cls<WRITE><<<grid, kClassThreads, smem, st>>>(
                    dv, P, B, flags, skip, (int)gr->cls_host.size(), counts, off, ids, cap, longq,
-                   skip == 3u ? gr->lightq : nullptr, gr->lstage, (long long)gr->cap));
+                   list, lstage, lstride));
   } else if (walk == kWalkClasses) {
     SI_KLAUNCH(WRITE ? "k_radius_write_cls_l2" : "k_radius_count_cls_l2", st,
                k_radius<WRITE, kWalkClasses><<<blocks, kQueryThreads, 0, st>>>(
-                   dv, P, B, flags, skip, counts, off, ids, cap, longq));
+                   dv, P, B, flags, skip, counts, off, ids, cap, longq, list));
   } else {
     SI_KLAUNCH(WRITE ? "k_radius_write_eq2" : "k_radius_count_eq2", st,
                k_radius<WRITE, kWalkPaper><<<blocks, kQueryThreads, 0, st>>>(
-                   dv, P, B, flags, skip, counts, off, ids, cap, longq));
+                   dv, P, B, flags, skip, counts, off, ids, cap, longq, list));
   }
   return SI_OK;
 }
 
+// The warp-per-query kernels over the slots listed in q ([0] = count).
 template <bool WRITE>
 static si_status launch_dense(const si_grid *gr, const GridDev &dv, const WalkParams &P, const Band &B,
-                              unsigned flags, long long *counts, const long long *off, int *ids,
+                              unsigned flags, const int *q, long long *counts, const long long *off, int *ids,
                               long long cap, int *longq, cudaStream_t st) {
   const int nbeg = gr->cls_q * gr->cls_q * gr->cls_q + 1;
   const size_t smem = gr->cls_host.size() * sizeof(unsigned long long) +
@@ -620,7 +627,71 @@ static si_status launch_dense(const si_grid *gr, const GridDev &dv, const WalkPa
   const unsigned grid = (unsigned)std::max(1, std::min<int>(per_sm, 8) * 148);
   SI_KLAUNCH(WRITE ? "k_radius_dense_write" : "k_radius_dense_count", st,
              k_radius_dense<WRITE><<<grid, kClassThreads, smem, st>>>(
-                 dv, P, B, flags, (int)gr->cls_host.size(), gr->denseq, counts, off, ids, cap, longq));
+                 dv, P, B, flags, (int)gr->cls_host.size(), q, counts, off, ids, cap, longq));
+  return SI_OK;
+}
+
+// Sort every queued list (ids ascending): a warp per list up to
+// kSortWarpCap ids, a block per longer one.
+static si_status launch_sorts(const long long *off, int *ids, int *longq, int *hugeq, cudaStream_t st) {
+  const size_t wsm = (size_t)kSortWarps * kSortWarpCap * sizeof(int);
+  SI_CUDA_TRY(cudaFuncSetAttribute(k_sort_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
+  SI_KLAUNCH("k_sort_warp", st, k_sort_warp<<<148 * 2, kSortWarps * 32, wsm, st>>>(off, ids, longq, hugeq));
+  const size_t bsm = (size_t)kSortBlockCap * sizeof(int);
+  SI_CUDA_TRY(cudaFuncSetAttribute(k_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+  SI_KLAUNCH("k_sort_block", st, k_sort_block<<<148, 512, bsm, st>>>(off, ids, hugeq));
+  return SI_OK;
+}
+
+// Radius query from caller-given centers (sorted by coarse cell first; see
+// si_centers.cu): the per-thread kernel for centers in light cells, the
+// warp-per-query kernel for the rest; no self exclusion.
+static si_status query_radius_centers(si_grid *g, const float *d_centers, int64_t m, float r, uint32_t flags,
+                                      int64_t *d_offsets, int32_t *d_ids, int64_t ids_capacity, int64_t *h_total,
+                                      cudaStream_t st) {
+  const bool cube = flags & SI_METHOD_CUBE;
+  const double load = g->n_cells > 1 ? (double)g->n / (double)(g->n_cells - 1) : 0.0;
+  const WalkParams P = walk_params(g->lat, r, load >= 4.0);
+  const Band B = make_band(g->lat, r);
+  const int walk = cube ? kWalkCube
+                        : ((!(flags & SI_WALK_PAPER) && g->ensure_classes(P.dg, st)) ? kWalkClasses
+                                                                                    : kWalkPaper);
+  const bool split = dense_path(walk, g);
+  long long *off = (long long *)d_offsets;
+  CenterOut eo;
+  eo.rad_counts = off + 1;
+  GridDev dv;
+  si_status s = prepare_centers(g, d_centers, m, split, split, eo, dv, st);
+  if (s != SI_OK) return s;
+  int *lstage = split ? g->cstage : nullptr;
+  const long long lstride = g->cstage_cap;
+  const unsigned blocks = (unsigned)((std::max<int64_t>(m, 1) + kQueryThreads - 1) / kQueryThreads);
+  SI_CUDA_TRY(cudaMemsetAsync(off, 0, sizeof(long long), st));
+  if (m > 0) {
+    if ((s = launch_light<false>(walk, g, dv, P, B, flags, 0u, off + 1, nullptr, nullptr, 0, nullptr, blocks,
+                                 g->clist0, lstage, lstride, st)) != SI_OK)
+      return s;
+    if (split && (s = launch_dense<false>(g, dv, P, B, flags, g->clist1, off + 1, nullptr, nullptr, 0, nullptr,
+                                          st)) != SI_OK)
+      return s;
+    if ((s = scan_inclusive_i64(off + 1, off + 1, m, g->cscan64, st)) != SI_OK) return s;
+  }
+  if (h_total) {
+    SI_CUDA_TRY(cudaMemcpyAsync(g->h_pinned, off + m, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    SI_CUDA_TRY(cudaStreamSynchronize(st));
+    *h_total = g->h_pinned[0];
+    if (*h_total > ids_capacity) return fail(SI_ERR_CAPACITY, "neighbor id buffer too small");
+  }
+  if (m == 0) return SI_OK;
+  SI_CUDA_TRY(cudaMemsetAsync(g->clong, 0, sizeof(int), st));
+  SI_CUDA_TRY(cudaMemsetAsync(g->chuge, 0, sizeof(int), st));
+  if ((s = launch_light<true>(walk, g, dv, P, B, flags, 0u, nullptr, off, d_ids, ids_capacity, g->clong, blocks,
+                              g->clist0, lstage, lstride, st)) != SI_OK)
+    return s;
+  if (split && (s = launch_dense<true>(g, dv, P, B, flags, g->clist1, nullptr, off, d_ids, ids_capacity, g->clong,
+                                       st)) != SI_OK)
+    return s;
+  if (!(flags & SI_NO_SORT)) return launch_sorts(off, d_ids, g->clong, g->chuge, st);
   return SI_OK;
 }
 
@@ -628,8 +699,12 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
                                      uint32_t flags, int64_t *d_offsets, int32_t *d_ids,
                                      int64_t ids_capacity, int64_t *h_total, void *stream) {
   if (!g) return fail(SI_ERR_INVALID, "null grid");
-  if (d_centers) return fail(SI_ERR_INVALID, "only the all-agents mode is supported (centers must be NULL)");
-  if (m != g->n) return fail(SI_ERR_INVALID, "all-agents mode: m must equal the grid's point count");
+  if (d_centers) {
+    if (m < 0 || m > (int64_t)INT32_MAX - 1) return fail(SI_ERR_INVALID, "m out of range");
+    if ((uintptr_t)d_centers & 15u) return fail(SI_ERR_INVALID, "centers must be a 16-byte aligned float4 array");
+  } else if (m != g->n) {
+    return fail(SI_ERR_INVALID, "all-agents mode: m must equal the grid's point count");
+  }
   if (!(r >= 0.f) || !std::isfinite(r)) return fail(SI_ERR_INVALID, "radius must be finite and >= 0");
   if (!g->lat.unbounded && (double)r > (double)g->desc.r_max)
     return fail(SI_ERR_INVALID, "radius exceeds the grid's r_max");
@@ -638,6 +713,7 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   if (flags & ~(SI_METHOD_CUBE | SI_INCLUDE_SELF | SI_NO_SORT | SI_WALK_PAPER))
     return fail(SI_ERR_INVALID, "unknown flags");
   cudaStream_t st = (cudaStream_t)stream;
+  if (d_centers) return query_radius_centers(g, d_centers, m, r, flags, d_offsets, d_ids, ids_capacity, h_total, st);
   const bool cube = flags & SI_METHOD_CUBE;
   const double load = g->n_cells > 1 ? (double)g->n / (double)(g->n_cells - 1) : 0.0;
   const WalkParams P = walk_params(g->lat, r, load >= 4.0);
@@ -658,6 +734,8 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   }
   const GridDev dv = g->dev();
   const unsigned skip = (heavy ? 1u : 0u) | (dense_path(walk, g) ? 2u : 0u);
+  // with both other paths on, the light cells' slots are listed at binning
+  const int *light_list = (walk == kWalkClasses && g->cls_smem_bytes > 0 && skip == 3u) ? g->lightq : nullptr;
   long long *off = (long long *)d_offsets;
   const unsigned blocks = (unsigned)((m + kQueryThreads - 1) / kQueryThreads);
   si_status s;
@@ -673,10 +751,11 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
     if (m == 0) return SI_OK;
     si_status r;
     if ((r = launch_light<false>(walk, g, dv, P, B, flags, skip, off + 1, nullptr, nullptr, 0,
-                                 nullptr, blocks, st)) != SI_OK)
+                                 nullptr, blocks, light_list, g->lstage, (long long)g->cap, st)) != SI_OK)
       return r;
     if (dense_path(walk, g) &&
-        (r = launch_dense<false>(g, dv, P, B, flags, off + 1, nullptr, nullptr, 0, nullptr, st)) != SI_OK)
+        (r = launch_dense<false>(g, dv, P, B, flags, g->denseq, off + 1, nullptr, nullptr, 0, nullptr, st)) !=
+            SI_OK)
       return r;
     if (heavy) {
       if ((r = launch_cell_pass(dv, P, B, flags, g->heavy, g->heavy_big, g->counters, g->over, off + 1, g->cell_rec,
@@ -717,7 +796,7 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   SI_CUDA_TRY(cudaMemsetAsync(g->longq, 0, sizeof(int), st));
   SI_CUDA_TRY(cudaMemsetAsync(g->hugeq, 0, sizeof(int), st));
   if ((s = launch_light<true>(walk, g, dv, P, B, flags, skip, nullptr, off, d_ids, ids_capacity,
-                              g->longq, blocks, st)) != SI_OK)
+                              g->longq, blocks, light_list, g->lstage, (long long)g->cap, st)) != SI_OK)
     return s;
   if (heavy) {
     if ((s = launch_cell_expand(dv, g->heavy, g->cell_rec, g->scratch, off, d_ids, ids_capacity, st)) != SI_OK)
@@ -728,16 +807,9 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
                                                                       g->longq));
   }
   if (dense_path(walk, g) &&
-      (s = launch_dense<true>(g, dv, P, B, flags, nullptr, off, d_ids, ids_capacity, g->longq, st)) != SI_OK)
+      (s = launch_dense<true>(g, dv, P, B, flags, g->denseq, nullptr, off, d_ids, ids_capacity, g->longq, st)) !=
+          SI_OK)
     return s;
-  if (!(flags & SI_NO_SORT)) {
-    const size_t wsm = (size_t)kSortWarps * kSortWarpCap * sizeof(int);
-    SI_CUDA_TRY(cudaFuncSetAttribute(k_sort_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
-    SI_KLAUNCH("k_sort_warp", st,
-               k_sort_warp<<<148 * 2, kSortWarps * 32, wsm, st>>>(off, d_ids, g->longq, g->hugeq));
-    const size_t bsm = (size_t)kSortBlockCap * sizeof(int);
-    SI_CUDA_TRY(cudaFuncSetAttribute(k_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
-    SI_KLAUNCH("k_sort_block", st, k_sort_block<<<148, 512, bsm, st>>>(off, d_ids, g->hugeq));
-  }
+  if (!(flags & SI_NO_SORT)) return launch_sorts(off, d_ids, g->longq, g->hugeq, st);
   return SI_OK;
 }
