@@ -123,6 +123,35 @@ def dist_setup():
 # ---------------------------------------------------------------------------
 # workloads (GPU arm)
 # ---------------------------------------------------------------------------
+def cell_classes(start, log2_cells):
+    """Class of every cell as the binning assigns it: heavy 1 (>= 8 points,
+    or >= 3 with >= 12 in the cell and its two x-neighbours), large heavy 3
+    (heavy with >= 768 points in the 27 cells around it), dense 2 (not heavy,
+    >= 24 points around it), light 0 (the rest); the last entry is the
+    outside cell."""
+    cnt = np.diff(start).astype(np.int64)
+    nc = len(cnt) - 1                # lattice cells; key nc is the outside cell
+    row = np.zeros(nc + 1, dtype=np.int64)
+    if nc >= 3:
+        key = np.arange(1, nc - 1)
+        row[1:nc - 1] = start[key + 2] - start[key - 1]
+    heavy = (cnt >= 8) | ((cnt >= 3) & (row >= 12))
+    heavy[-1] = False
+    wx, wy, wz = log2_cells
+    c3 = cnt[:nc].reshape(1 << wz, 1 << wy, 1 << wx)
+    xs = c3.copy()
+    xs[:, :, 1:] += c3[:, :, :-1]
+    xs[:, :, :-1] += c3[:, :, 1:]          # x clipped at the region's ends
+    n27 = np.zeros_like(c3)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            n27 += np.roll(np.roll(xs, dz, 0), dy, 1)   # y, z wrapped
+    n27 = np.append(n27.ravel(), cnt[nc])
+    cls = np.where(heavy, np.where(n27 >= 768, 3, 1), np.where(n27 >= 24, 2, 0))
+    cls[-1] = np.where(cnt[nc] >= 24, 2, 0)
+    return cls
+
+
 class RadiusWork:
     """Bin + all-agents radius query for a list of scenes."""
 
@@ -162,24 +191,7 @@ class RadiusWork:
         s = self.scenes[k]
         start, _, perm = (t.cpu().numpy() for t in self.grids[k].cell_arrays())
         cnt = np.diff(start).astype(np.int64)
-        nc = len(cnt) - 1                # lattice cells; key nc is the outside cell
-        row = np.zeros(nc + 1, dtype=np.int64)
-        if nc >= 3:
-            key = np.arange(1, nc - 1)
-            row[1:nc - 1] = start[key + 2] - start[key - 1]
-        heavy = (cnt >= 8) | ((cnt >= 3) & (row >= 12))
-        heavy[-1] = False
-        wx, wy, wz = s.log2_cells
-        c3 = cnt[:nc].reshape(1 << wz, 1 << wy, 1 << wx)
-        xs = c3.copy()
-        xs[:, :, 1:] += c3[:, :, :-1]
-        xs[:, :, :-1] += c3[:, :, 1:]          # x clipped at the region's ends
-        n27 = np.zeros_like(c3)
-        for dz in (-1, 0, 1):
-            for dy in (-1, 0, 1):
-                n27 += np.roll(np.roll(xs, dz, 0), dy, 1)   # y, z wrapped
-        n27 = np.append(n27.ravel(), cnt[nc])
-        cls = np.where(heavy, np.where(n27 >= 768, 3, 1), np.where(n27 >= 24, 2, 0))
+        cls = cell_classes(start, s.log2_cells)
         if self.method == "cube":
             cls[:] = 0
         slot_cls = np.repeat(cls, cnt.clip(min=0))[: len(perm)]
@@ -263,6 +275,70 @@ def e2e_radius(work, steps, warmup):
     bi = sum(16 * s.n for s in work.scenes)
     bo = sum(8 * (s.n + 1) + 4 * t for s, t in zip(work.scenes, work.totals))
     return ms, bi, bo
+
+
+class CentersWork:
+    """Bin + radius query from m caller-given centers (no self exclusion)."""
+
+    def __init__(self, scene, centers):
+        import torch
+        from paper_cs_0608108_b300 import Grid
+        self.scene = scene
+        self.centers_np = centers
+        self.pos = torch.from_numpy(scene.pos).cuda()
+        self.centers = torch.from_numpy(centers).cuda()
+        self.grid = Grid.for_scene(scene)
+        self.grid.build(self.pos)
+        off, _ = self.grid.query_radius(scene.r, centers=self.centers)
+        self.grid.sync()
+        self.total = int(off[-1].item())
+        self.off = off
+        self.ids = torch.empty(max(self.total, 1), dtype=torch.int32, device="cuda")
+        self.queries = centers.shape[0]
+
+    def step(self):
+        self.grid.build(self.pos)
+        self.grid.query_radius(self.scene.r, centers=self.centers, out_offsets=self.off, out_ids=self.ids,
+                               sync_total=False)
+
+    def check(self):
+        self.grid.sync()
+
+    def _split(self):
+        """(fraction of centers, fraction of hits) served per thread (light
+        cells) and per warp (the rest), from the cell classes of the centers'
+        cells."""
+        s = self.scene
+        start, _, _ = (t.cpu().numpy() for t in self.grid.cell_arrays())
+        cls = cell_classes(start, s.log2_cells)
+        u = ((self.centers_np[:, :3] - np.array(s.origin, np.float32)) *
+             np.float32(1.0 / s.cell_size)).astype(np.int64)
+        w = s.log2_cells
+        u = np.minimum(np.maximum(u, 0), [(1 << a) - 1 for a in w])
+        key = (u[:, 2] << (w[0] + w[1])) | (u[:, 1] << w[0]) | u[:, 0]
+        light = cls[key] == 0
+        lens = np.diff(self.off.cpu().numpy())
+        tot = max(lens.sum(), 1)
+        return light.mean(), lens[light].sum() / tot
+
+    def algorithmic_bytes(self):
+        s, m = self.scene, self.queries
+        n, C = s.n, (1 << sum(s.log2_cells)) + 1
+        fl, tl = self._split()
+        q_b = 16 * m + 4 * m + 8 * m   # the center, its input index, its count or offset
+        return {"k_bin_key": 16 * n + 8 * n + 8 * C,
+                "k_bin_scatter": 8 * n + 16 * n + 4 * C + 16 * n + 4 * n,
+                "k_center_key": 16 * m + 8 * m,
+                "k_center_scatter": 16 * m + 8 * m + 16 * m + 4 * m + 4 * m,
+                "k_radius_count": fl * q_b + 4 * C,
+                "k_radius_write": fl * q_b + 4 * C + tl * 4 * self.total,
+                "k_radius_dense_count": (1 - fl) * q_b + 4 * C,
+                "k_radius_dense_write": (1 - fl) * q_b + 4 * C + (1 - tl) * 4 * self.total}
+
+    def step_bytes(self):
+        s, m = self.scene, self.queries
+        n, C = s.n, (1 << sum(s.log2_cells)) + 1
+        return 36 * n + 4 * C + 20 * n + 4 * C + 64 * m + 2 * 28 * m + 4 * C + 4 * self.total
 
 
 class KnnWork:
@@ -402,7 +478,22 @@ def make_work(name):
         return LoopWork(synth.batched_scenes()), "256 uneven scenes, plain path looped per scene"
     if name == "tiny":
         return RadiusWork([synth.tiny_scene()]), "20k-point radius, 32^3 non-cyclic, r=0.96 cells"
+    if name == "radius_centers_1m":
+        return CentersWork(synth.mixture_1m_scene(), centers_1m()), \
+            "1M Gaussian-mixture points, 128^3 cyclic, r=1.5 cells; 1M query centers, half from the " \
+            "same mixture (another seed), half uniform"
     raise SystemExit(f"unknown workload {name}")
+
+
+def centers_1m():
+    """Query centers of the centers workload: 500k drawn from the points'
+    mixture with another seed, 500k uniform, interleaved."""
+    from paper_cs_0608108_b300 import synth
+    a = synth.gaussian_mixture_points(500_000, synth.SEEDS["mixture_1m"] + 0x100)
+    b = synth.uniform_points(500_000, synth.SEEDS["mixture_1m"] + 0x101)
+    c = np.empty((1_000_000, 4), np.float32)
+    c[0::2], c[1::2] = a, b
+    return c
 
 
 def slowest_rank_ms(ms_step: float, device: str = "cuda") -> float:
@@ -455,7 +546,7 @@ def _oracle_scene(name):
     from paper_cs_0608108_b300 import synth
     if name in ("radius_1m", "radius_1m_cube", "walk_1m", "radius_uniform", "radius_uniform_cube"):
         return synth.uniform_1m_scene()
-    if name in ("radius_mixture", "radius_mixture_cube"):
+    if name in ("radius_mixture", "radius_mixture_cube", "radius_centers_1m"):
         return synth.mixture_1m_scene()
     if name == "knn_4m":
         return synth.knn_4m_scene()
@@ -475,12 +566,15 @@ class OracleRunner:
         self.sc = _oracle_scene(name)
         self.threads = oracle.max_threads()
         self.rng = np.random.default_rng(0)
+        self.centers = centers_1m() if name == "radius_centers_1m" else None
 
     def run(self, m):
         sc, o = self.sc, self.oracle
         q = self.rng.choice(sc.n, m, replace=False)
         t = time.perf_counter()
-        if self.name == "knn_4m":
+        if self.centers is not None:
+            o.radius(sc.pos, self.centers[q], sc.box, sc.cyclic_mask, sc.r, None)
+        elif self.name == "knn_4m":
             o.knn(sc.pos, sc.pos[q], sc.box, sc.cyclic_mask, 16, sc.r, q)
         elif self.name == "walk_1m":
             o.reduce(sc.pos, q, sc.box, sc.cyclic_mask, sc.r)
@@ -495,7 +589,8 @@ class OracleRunner:
         return int(min(self.sc.n, max(m, m * seconds / max(dt, 1e-4))))
 
     def describe(self, m, total_s, steps):
-        return (f"{steps} x {m} random query points of the {self.sc.n}-point workload, "
+        what = "query centers" if self.centers is not None else "query points"
+        return (f"{steps} x {m} random {what} of the {self.sc.n}-point workload, "
                 f"FP64 brute force over all points, {self.threads} threads, {total_s:.1f} s")
 
 
