@@ -496,6 +496,45 @@ def centers_1m():
     return c
 
 
+SWEEPS = {
+    # the paper's sizes (Sec. IV.A, Fig. 9 and 10): 20,480 objects, 16^3 / 32^3 / 64^3
+    "paper_20k": dict(n=20_480, m=100_000, log2=4, shifts=(0, 1, 2), d=(0.5, 1, 2, 3, 4, 6)),
+    # the same loads on a 64x larger problem: 64^3 / 128^3 / 256^3
+    "b300_1m": dict(n=1_310_720, m=250_000, log2=6, shifts=(0, 1, 2), d=(0.5, 1, 2, 3, 4)),
+}
+
+
+def run_sweep(reps=3):
+    """Discretization sweep: for each problem size, cyclic mask (xyz, none),
+    mode (all neighbors within d; the nearest within d) and distance d (in
+    cells of the coarsest lattice), the time of binning + one query of m
+    uniform centers on each lattice, and the fastest lattice (the tuner of
+    the library)."""
+    import torch
+    from paper_cs_0608108_b300 import synth, tune_lattice
+    out, total_q, total_ms, launches = {}, 0, 0.0, 0
+    for name, S in SWEEPS.items():
+        pos = torch.from_numpy(synth.uniform_points(S["n"], 0x51D00100 + S["log2"])).cuda()
+        cen = torch.from_numpy(synth.uniform_points(S["m"], 0x51D00200 + S["log2"])).cuda()
+        rows = []
+        for mask in (7, 0):
+            for mode, k in (("radius", 0), ("nearest", 1)):
+                for d in S["d"]:
+                    s0 = 1.0 / (1 << S["log2"])
+                    ms, best = tune_lattice((0, 0, 0), s0, (S["log2"],) * 3, mask, pos, d * s0, S["shifts"],
+                                            centers=cen, k=k, reps=reps)
+                    rows.append({"mask": mask, "mode": mode, "d": d,
+                                 "lattices": [1 << (S["log2"] + x) for x in S["shifts"]],
+                                 "ms": [round(t, 4) if np.isfinite(t) else None for t in ms],
+                                 "best": 1 << (S["log2"] + S["shifts"][best]),
+                                 "queries_per_s_best": S["m"] / (ms[best] * 1e-3)})
+                    total_q += S["m"]
+                    total_ms += ms[best]
+        out[name] = {"n": S["n"], "m": S["m"], "loads": [S["n"] / (1 << 3 * (S["log2"] + x)) for x in S["shifts"]],
+                     "rows": rows}
+    return out, total_q, total_ms
+
+
 def slowest_rank_ms(ms_step: float, device: str = "cuda") -> float:
     """The job's step time: the slowest rank's (max over ranks; the rank's own
     time when there is one rank or no process group)."""
@@ -639,6 +678,23 @@ def main():
 
     import torch
     torch.cuda.set_device(local)
+    if args.workload == "sweep":
+        if rank != 0:
+            return
+        from paper_cs_0608108_b300 import launch_count
+        l0 = launch_count()
+        with ClockSampler(local) as clk:
+            table, q, ms_tot = run_sweep()
+        line = {"metric": "discretization sweep: queries/s of the fastest lattice per point (Fig. 9/10 shape)",
+                "value": q / (ms_tot * 1e-3), "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+                "ms_per_step": ms_tot, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": "sweep", "description": "uniform objects and centers in the unit cube; "
+                           "binning + one query per timed round, median of 3 rounds", "l2": "not flushed"},
+                "gpu_launches": int(launch_count() - l0), "clocks": clk.summary(), "roofline": None,
+                "e2e": None, "sweep": table}
+        print(json.dumps(line))
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")

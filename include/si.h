@@ -191,6 +191,25 @@ si_status si_neighbor_reduce(si_grid *g, float r, int kernel, double *d_energy,
 si_status si_neighbor_energy_noalloc(const si_grid_desc *desc, const float *d_pos, int64_t n,
                                      float r, double *d_energy, void *stream);
 
+/* Discretization tuning (Sec. IV.A, Fig. 9 and 10: for a fixed region, fixed
+ * objects and fixed query centers there is a best cell size, which depends on
+ * the number of objects, the query distance and on K).  Candidate i cuts the
+ * region of *desc into 2^(log2_cells[a] + h_shifts[i]) cells on every axis
+ * (cell side cell_size * 2^-h_shifts[i], same origin and box); for each, a
+ * grid is created for the n points (d_pos, device) and `reps` rounds of
+ * si_grid_build plus one query are timed with CUDA events on `stream`: the
+ * radius query of radius r when k == 0, else the k nearest within r
+ * (1 <= k <= 64), from d_centers (m centers, device; NULL = all agents,
+ * m = n) with default flags.  h_ms[i] (host, n_cand floats) receives the
+ * median milliseconds per round, +inf for a candidate that is not a valid
+ * lattice (log2 out of [2, 10], or tables that would wrap a cyclic axis);
+ * *h_best (host) the index of the fastest.  One warm-up round per candidate
+ * is not timed.  Synchronises; allocates and frees its own grids and
+ * buffers.  SI_ERR_INVALID when no candidate is valid. */
+si_status si_tune_lattice(const si_grid_desc *desc, const float *d_pos, int64_t n, const float *d_centers,
+                          int64_t m, float r, int k, const int32_t *h_shifts, int n_cand, int reps,
+                          float *h_ms, int32_t *h_best, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Batched scenes: many independent grids served together.
  * Each scene has its own lattice, cyclic mask, radius and points.  Scenes

@@ -14,7 +14,7 @@ import torch
 
 from . import _native as N
 
-__all__ = ["Grid", "NeighborEnergy", "neighbor_energy", "Batch", "launch_count"]
+__all__ = ["Grid", "NeighborEnergy", "neighbor_energy", "Batch", "launch_count", "tune_lattice"]
 
 
 def _stream() -> ctypes.c_void_p:
@@ -68,6 +68,27 @@ def make_desc(origin, cell_size, log2_cells, cyclic_mask, r_max) -> N.GridDesc:
     d.cyclic_mask = int(cyclic_mask)
     d.r_max = float("inf") if r_max is None else float(r_max)
     return d
+
+
+def tune_lattice(origin, cell_size, log2_cells, cyclic_mask, pos: torch.Tensor, r: float, shifts,
+                 centers=None, k: int = 0, reps: int = 5):
+    """Time binning + one query (radius r, or the k nearest within r) on the
+    region cut 2^shift times finer per axis, for each shift.  Returns
+    (milliseconds per round for each shift, inf where invalid; index of the
+    fastest)."""
+    pos = _check_points(pos)
+    d = make_desc(origin, cell_size, log2_cells, cyclic_mask, r)
+    m = pos.shape[0]
+    c = None
+    if centers is not None:
+        c, m = _centers(centers)
+    sh = (ctypes.c_int32 * len(shifts))(*[int(x) for x in shifts])
+    ms = (ctypes.c_float * len(shifts))()
+    best = ctypes.c_int32(-1)
+    N.check(N.lib().si_tune_lattice(ctypes.byref(d), _ptr(pos), pos.shape[0], _ptr(c), m, float(r), int(k),
+                                    sh, len(shifts), int(reps), ms, ctypes.byref(best), _stream()),
+            "si_tune_lattice")
+    return [float(x) for x in ms], int(best.value)
 
 
 class Grid:

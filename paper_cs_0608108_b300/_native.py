@@ -51,6 +51,7 @@ SIGNATURES = {
     "si_query_knn": (I32, [P, P, I64, I32, F, U32, P, P, P, P]),
     "si_neighbor_reduce": (I32, [P, F, I32, P, P, P, P]),
     "si_neighbor_energy_noalloc": (I32, [ctypes.POINTER(GridDesc), P, I64, F, P, P]),
+    "si_tune_lattice": (I32, [ctypes.POINTER(GridDesc), P, I64, P, I64, F, I32, P, I32, I32, P, P, P]),
     "si_batch_create": (I32, [ctypes.POINTER(SceneDesc), I32, U32, ctypes.POINTER(P)]),
     "si_batch_run": (I32, [P, I32, P]),
     "si_batch_sync": (I32, [P, P, P]),
