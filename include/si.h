@@ -54,6 +54,11 @@ typedef enum {
 #define SI_WALK_PAPER      8u  /* radius: walk the 64 direction-bit tables of
                                   Sec. III.A with the run-time test (Eq. 1)
                                   instead of the sub-cell class tables         */
+#define SI_METHOD_LIST    16u  /* radius: the non-empty cell list method of
+                                  Sec. III.B / IV.A: every object tested      */
+#define SI_SPHERE_ONLY    32u  /* radius: the spherical index without the volume
+                                  comparison (Sec. IV.A, Fig. 8): never switch
+                                  to the list method                           */
 
 /* Region, lattice and table extent (Sec. II.B).  The box side on axis a is
  * L_a = cell_size * 2^log2_cells[a] (exact in float32).  A cyclic axis wraps
@@ -119,6 +124,12 @@ si_status si_grid_destroy(si_grid *g);
 
 /* Fixed-radius query (Sec. I: every agent queries its neighborhood;
  * Sec. II.A: x <= d).
+ * Method: with SI_METHOD_SPHERE (0) the call compares volumes as the paper
+ * does (Sec. III.B, Sec. IV.A): when the estimated cost of walking the query
+ * sphere's cells exceeds that of testing every object of the region (large
+ * radius, low load), it uses the non-empty list method (SI_METHOD_LIST)
+ * instead; SI_SPHERE_ONLY disables the comparison.  Every method returns the
+ * same lists.
  * d_centers NULL: all agents; query k is point k of the last build, m must
  * equal the grid's n, and a point's own index is excluded unless
  * SI_INCLUDE_SELF.

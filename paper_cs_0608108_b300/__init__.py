@@ -156,10 +156,15 @@ class Grid:
         """Radius query.  Returns (offsets int64[m+1], ids int32[total]).
         centers None: all agents (query k is point k, m = n); else a CUDA
         float32 (m, 4) tensor of query centers.  method "sphere" (spherical
-        index) or "cube" (bin-lattice scan); walk "classes" (sub-cell class
-        tables) or "paper" (Sec. III.A 64 tables)."""
-        flags = (N.SI_INCLUDE_SELF if include_self else 0) | \
-                (N.SI_METHOD_CUBE if method == "cube" else 0) | (0 if sort else N.SI_NO_SORT) | \
+        index, switching to the list method when the volume comparison says
+        it is cheaper), "sphere_only" (never switching), "cube" (bin-lattice
+        scan) or "list" (non-empty list: every object tested); walk "classes"
+        (sub-cell class tables) or "paper" (Sec. III.A 64 tables)."""
+        if method not in ("sphere", "sphere_only", "cube", "list"):
+            raise ValueError(f"unknown method {method!r}")
+        flags = (N.SI_INCLUDE_SELF if include_self else 0) | (0 if sort else N.SI_NO_SORT) | \
+                {"sphere": 0, "sphere_only": N.SI_SPHERE_ONLY, "cube": N.SI_METHOD_CUBE,
+                 "list": N.SI_METHOD_LIST}[method] | \
                 (N.SI_WALK_PAPER if walk == "paper" else 0)
         dev = self._pos.device
         m = self.n

@@ -670,6 +670,7 @@ static void grid_free(si_grid *g) {
   cudaFree(g->clong);
   cudaFree(g->chuge);
   cudaFree(g->cstage);
+  cudaFree(g->ipos);
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
   free_tables(g->tables);
   delete g;

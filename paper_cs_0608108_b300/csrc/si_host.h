@@ -205,5 +205,6 @@ struct si_grid {
   int *cstage = nullptr;         // kInlineSort x cstage_cap: short lists kept by the count pass
   int64_t cstage_cap = 0;
   si_status ensure_centers(int64_t m, bool stage);
+  float4 *ipos = nullptr;        // cap: points in input order (non-empty list method; allocated on first use)
   si::GridDev dev() const;
 };

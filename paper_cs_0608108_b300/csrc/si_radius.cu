@@ -643,6 +643,76 @@ static si_status launch_sorts(const long long *off, int *ids, int *longq, int *h
   return SI_OK;
 }
 
+// The non-empty list method (si_list.cu) for all agents or for centers:
+// every (query, point) pair tested, points in input order, so the lists come
+// out ascending without a sort.
+static si_status query_radius_list(si_grid *g, const float *d_centers, int64_t m, float r, uint32_t flags,
+                                   int64_t *d_offsets, int32_t *d_ids, int64_t ids_capacity, int64_t *h_total,
+                                   cudaStream_t st) {
+  if (!g->ipos) {
+    if (cudaMalloc((void **)&g->ipos, (size_t)std::max<int64_t>(g->cap, 1) * sizeof(float4)) != cudaSuccess) {
+      g->ipos = nullptr;
+      cudaGetLastError();
+      return fail(SI_ERR_OOM, "input-order point buffer");
+    }
+  }
+  const Band B = make_band(g->lat, r);
+  long long *off = (long long *)d_offsets;
+  GridDev dv = g->dev();
+  const int *list = nullptr;
+  long long *scan = g->scan_i64;
+  si_status s;
+  if (d_centers) {
+    CenterOut eo;
+    eo.rad_counts = off + 1;
+    if ((s = prepare_centers(g, d_centers, m, false, false, eo, dv, st)) != SI_OK) return s;
+    list = g->clist0;
+    scan = g->cscan64;
+  }
+  if ((s = gather_input(g, dv, g->ipos, st)) != SI_OK) return s;
+  SI_CUDA_TRY(cudaMemsetAsync(off, 0, sizeof(long long), st));
+  if (m > 0) {
+    if ((s = launch_list(dv, B, flags, list, m, g->ipos, off + 1, nullptr, nullptr, 0, false, st)) != SI_OK) return s;
+    if ((s = scan_inclusive_i64(off + 1, off + 1, m, scan, st)) != SI_OK) return s;
+  }
+  if (h_total) {
+    SI_CUDA_TRY(cudaMemcpyAsync(g->h_pinned, off + m, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    SI_CUDA_TRY(cudaStreamSynchronize(st));
+    *h_total = g->h_pinned[0];
+    if (*h_total > ids_capacity) return fail(SI_ERR_CAPACITY, "neighbor id buffer too small");
+  }
+  if (m == 0) return SI_OK;
+  return launch_list(dv, B, flags, list, m, g->ipos, nullptr, off, d_ids, ids_capacity, true, st);
+}
+
+// Volume comparison (Sec. III.B, Sec. IV.A): the paper walks the sphere
+// unless its list of non-empty cells is shorter.  Here the two methods'
+// estimated costs per query are compared, in nanoseconds on B300 (a fit to
+// both methods measured on 20k to 1.3M uniform points, 16^3 to 128^3
+// lattices, d = 0.7 to 24 cells, 100k centers):
+//   sphere: 0.019 per x-row run of the class walk (0.015 per cell of the
+//           table walk) + 0.0041 per candidate + 0.069 per hit + 0.85
+//   list:   0.0019 per point + 0.0028 per hit + 1.2
+// with candidates = load x the Steiner volume 1 + 6d + 3 pi d^2 + 4/3 pi d^3
+// (cells meeting the sphere around a random center) and hits = load x
+// 4/3 pi d^3.  The list is taken when estimated 1.2x cheaper.
+static bool list_cheaper(const si_grid *g, float r, int walk) {
+  if (g->n <= 0 || g->n_cells <= 1) return false;
+  const double d = (double)r * (double)g->lat.inv_s;
+  const double load = (double)g->n / (double)(g->n_cells - 1);
+  const double steiner = 1.0 + 6.0 * d + 3.0 * M_PI * d * d + 4.0 / 3.0 * M_PI * d * d * d;
+  const double hits = load * 4.0 / 3.0 * M_PI * d * d * d;
+  double sphere = 0.0041 * load * steiner + 0.069 * hits + 0.85;
+  if (walk == kWalkClasses && g->cls_q > 0) {
+    const double q3 = (double)g->cls_q * g->cls_q * g->cls_q;
+    sphere += 0.019 * (double)g->cls_host.size() / q3;
+  } else {
+    sphere += 0.015 * steiner;
+  }
+  const double list = 0.0019 * (double)g->n + 0.0028 * hits + 1.2;
+  return 1.2 * list < sphere;
+}
+
 // Radius query from caller-given centers (sorted by coarse cell first; see
 // si_centers.cu): the per-thread kernel for centers in light cells, the
 // warp-per-query kernel for the rest; no self exclusion.
@@ -710,9 +780,21 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
     return fail(SI_ERR_INVALID, "radius exceeds the grid's r_max");
   if (!d_offsets) return fail(SI_ERR_INVALID, "null offsets");
   if (ids_capacity < 0 || (ids_capacity > 0 && !d_ids)) return fail(SI_ERR_INVALID, "bad ids buffer");
-  if (flags & ~(SI_METHOD_CUBE | SI_INCLUDE_SELF | SI_NO_SORT | SI_WALK_PAPER))
+  if (flags & ~(SI_METHOD_CUBE | SI_INCLUDE_SELF | SI_NO_SORT | SI_WALK_PAPER | SI_METHOD_LIST | SI_SPHERE_ONLY))
     return fail(SI_ERR_INVALID, "unknown flags");
+  if ((flags & SI_METHOD_CUBE) && (flags & SI_METHOD_LIST))
+    return fail(SI_ERR_INVALID, "SI_METHOD_CUBE and SI_METHOD_LIST are exclusive");
   cudaStream_t st = (cudaStream_t)stream;
+  if (flags & SI_METHOD_LIST)
+    return query_radius_list(g, d_centers, m, r, flags, d_offsets, d_ids, ids_capacity, h_total, st);
+  if (!(flags & (SI_METHOD_CUBE | SI_WALK_PAPER | SI_SPHERE_ONLY))) {
+    // the walk the sphere method would take (class tables when they can be
+    // built for this radius), then the volume comparison
+    const WalkParams P0 = walk_params(g->lat, r, false);
+    const int walk0 = g->ensure_classes(P0.dg, st) ? kWalkClasses : kWalkPaper;
+    if (list_cheaper(g, r, walk0))
+      return query_radius_list(g, d_centers, m, r, flags, d_offsets, d_ids, ids_capacity, h_total, st);
+  }
   if (d_centers) return query_radius_centers(g, d_centers, m, r, flags, d_offsets, d_ids, ids_capacity, h_total, st);
   const bool cube = flags & SI_METHOD_CUBE;
   const double load = g->n_cells > 1 ? (double)g->n / (double)(g->n_cells - 1) : 0.0;

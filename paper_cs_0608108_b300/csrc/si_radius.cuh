@@ -27,4 +27,10 @@ si_status launch_cell_pass(const GridDev &g, const WalkParams &P, const Band &B,
 si_status launch_cell_expand(const GridDev &g, const int *heavy, const long long *cell_rec, const int *scratch,
                              const long long *offsets, int *ids, long long cap, cudaStream_t st);
 
+// Non-empty list method (si_list.cu): every (query, point) pair tested.
+si_status launch_list(const GridDev &dv, const Band &B, unsigned flags, const int *list, int64_t m,
+                      const float4 *ipos, long long *counts, const long long *off, int *ids, long long cap,
+                      bool write, cudaStream_t st);
+si_status gather_input(const si_grid *g, const GridDev &dv, float4 *ipos, cudaStream_t st);
+
 }  // namespace si

@@ -220,3 +220,74 @@ def test_full_size_uniform_1m_with_random_centers_sampled():
     mean = (off[-1] / c.shape[0])
     expect = 4 / 3 * np.pi * 1.5 ** 3 * scene.n / 128 ** 3
     assert abs(mean - expect) < 0.02 * expect
+
+
+# ---------------------------------------------------------------------------
+# The non-empty list method (Sec. III.B, Sec. IV.A) and the volume comparison
+# that switches to it.
+
+def kernels_run(fn):
+    """Names of the library kernels launched by fn()."""
+    from paper_cs_0608108_b300 import _native as N
+    import ctypes
+    L = N.lib()
+    L.si_kernel_timing_enable(1)
+    buf = ctypes.create_string_buffer(1 << 16)
+    L.si_kernel_timing_report(buf, len(buf))
+    fn()
+    L.si_kernel_timing_report(buf, len(buf))
+    L.si_kernel_timing_enable(0)
+    return {line.rsplit(" ", 2)[0] for line in buf.value.decode().splitlines() if line}
+
+
+@pytest.mark.parametrize("mask", [7, 0, 6])
+@pytest.mark.parametrize("include_self", [False, True])
+def test_list_method_all_agents_exact(mask, include_self):
+    pos = synth.uniform_points(9000, 500 + mask)
+    pos[:6, 0] = np.float32(-0.2) if not (mask & 1) else pos[:6, 0]   # outside on a non-cyclic x
+    pos[10:30] = pos[3]                                               # coincident points
+    scene = synth.Scene(pos, (0, 0, 0), 1 / 16, (4, 4, 4), mask, 2.3 / 16)
+    g = gpu_grid(scene)
+    off, ids = g.query_radius(scene.r, method="list", include_self=include_self)
+    g.sync()
+    q = np.arange(scene.n)
+    off_o, ids_o = oracle.radius(scene.pos, scene.pos, scene.box, scene.cyclic_mask, scene.r,
+                                 None if include_self else q)
+    assert_csr_equal(off.cpu().numpy(), ids.cpu().numpy(), off_o, ids_o)
+
+
+def test_list_method_from_centers_exact():
+    scene = synth.Scene(synth.uniform_points(7000, 511), (0, 0, 0), 1 / 16, (4, 4, 4), 5, 3.1 / 16)
+    c = mixed_centers(scene, 5000, 3)
+    c[7, 1] = np.float32(-0.3)       # outside on the non-cyclic y
+    c[8, 0] = np.float32(2.0)        # outside the cyclic x box: invalid
+    g = gpu_grid(scene)
+    off, ids = g.query_radius(scene.r, method="list", centers=to_dev(c))
+    with pytest.raises(_native.SIError):
+        g.sync()
+    off, ids = off.cpu().numpy(), ids.cpu().numpy()
+    assert off[9] == off[8]
+    good = np.setdiff1d(np.arange(c.shape[0]), [8])
+    off_o, ids_o = oracle_centers(scene, c[good])
+    for t, i in enumerate(good):
+        assert np.array_equal(ids[off[i]:off[i + 1]], ids_o[off_o[t]:off_o[t + 1]])
+
+
+def test_volume_comparison_picks_the_list_at_low_load_and_large_radius():
+    # 64^3 cells for 20,480 points (load 0.08), r = 20 cells: the sphere holds
+    # ~40k cells, more than the region has points
+    far = synth.Scene(synth.uniform_points(20_480, 521), (0, 0, 0), 1 / 64, (6, 6, 6), 7, 20 / 64)
+    g = gpu_grid(far)
+    c = to_dev(mixed_centers(far, 3000, 4))
+    names = kernels_run(lambda: g.query_radius(far.r, centers=c))
+    assert "k_radius_all_count" in names and "k_radius_all_write" in names
+    names = kernels_run(lambda: g.query_radius(far.r, centers=c, method="sphere_only"))
+    assert "k_radius_all_count" not in names
+    off_a, ids_a = radius_centers(g, c.cpu().numpy(), far.r)
+    off_s, ids_s = radius_centers(g, c.cpu().numpy(), far.r, method="sphere_only")
+    assert_csr_equal(off_a, ids_a, off_s, ids_s)
+    # the 1M uniform configuration keeps the sphere
+    near = synth.uniform_1m_scene()
+    gn = gpu_grid(near)
+    names = kernels_run(lambda: gn.query_radius(near.r))
+    assert "k_radius_all_count" not in names
