@@ -152,6 +152,52 @@ def cell_classes(start, log2_cells):
     return cls
 
 
+# ALU roofline of the pair tests: FP32 lanes x 2 (packed FP32x2 arithmetic) per SM
+# and clock, over the 6 arithmetic operations of one test (3 differences, one
+# square, two fused multiply-adds); the comparison runs on another pipe.
+SMS, FP32_LANES, SM_GHZ, OPS_PER_PAIR = 148, 128, 2.032, 6
+PAIR_PEAK = SMS * FP32_LANES * 2 * SM_GHZ * 1e9 / OPS_PER_PAIR
+
+
+def candidate_pairs(scene, start, cls, sample=131_072):
+    """Algorithmic pair tests of the spherical index, by query class: for
+    each query point, the points of every cell that meets its sphere (exact
+    per-query cell culling, cyclic wrap; cells leaving a non-cyclic region
+    skipped), summed over a fixed sample of queries and scaled to all."""
+    pos = scene.pos
+    n = len(pos)
+    if n == 0:
+        return {c: 0.0 for c in range(4)}
+    step = max(1, n // sample)
+    q = pos[::step, :3].astype(np.float64)
+    w = np.array(scene.log2_cells)
+    G = 1 << w
+    u = (q - np.array(scene.origin)) / scene.cell_size
+    c = np.clip(np.floor(u).astype(np.int64), 0, G - 1)
+    f = u - c
+    d = scene.r / scene.cell_size
+    D = int(np.ceil(d))
+    cnt = np.diff(start).astype(np.int64)
+    qcls = cls[(c[:, 2] << (w[0] + w[1])) | (c[:, 1] << w[0]) | c[:, 0]]
+    tot = np.zeros(len(q))
+    for oz in range(-D, D + 1):
+        for oy in range(-D, D + 1):
+            for ox in range(-D, D + 1):
+                o = np.array([ox, oy, oz])
+                gap = np.where(o > 0, o - f, np.where(o < 0, f - o - 1, 0.0))
+                ok = (gap * gap).sum(axis=1) <= d * d
+                t = c + o
+                for a in range(3):
+                    if (scene.cyclic_mask >> a) & 1:
+                        t[:, a] %= G[a]
+                    else:
+                        ok &= (t[:, a] >= 0) & (t[:, a] < G[a])
+                t = np.clip(t, 0, G - 1)
+                key = (t[:, 2] << (w[0] + w[1])) | (t[:, 1] << w[0]) | t[:, 0]
+                tot += np.where(ok, cnt[key], 0)
+    return {k: float(tot[qcls == k].sum()) * step for k in range(4)}
+
+
 class RadiusWork:
     """Bin + all-agents radius query for a list of scenes."""
 
@@ -243,6 +289,20 @@ class RadiusWork:
             n, C = s.n, (1 << sum(s.log2_cells)) + 1
             tot += (16 + 20) * n + 4 * C + (16 + 4) * n + 4 * C + 8 * n + 4 * t
         return tot
+
+    def algorithmic_pairs(self):
+        """Per pair-testing kernel, the algorithmic pair tests of one launch
+        (candidate_pairs of the queries it serves), averaged over the scenes."""
+        if self.method == "cube":
+            return {}
+        out = {}
+        for k, s in enumerate(self.scenes):
+            start, _, _ = (t.cpu().numpy() for t in self.grids[k].cell_arrays())
+            p = candidate_pairs(s, start, cell_classes(start, s.log2_cells))
+            for name, c in (("k_radius_count", 0), ("k_radius_write", 0), ("k_radius_dense_count", 2),
+                            ("k_radius_dense_write", 2), ("k_cell", 1), ("k_cell_large", 3)):
+                out.setdefault(name, []).append(p[c])
+        return {kk: float(np.mean(v)) for kk, v in out.items()}
 
 
 def e2e_radius(work, steps, warmup):
@@ -728,12 +788,24 @@ def main():
         avg_ms = tot / max(cnt, 1)
         a_bytes = alg.get(dom)
         achieved = (a_bytes / (avg_ms * 1e-3) / 1e9) if a_bytes else None
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-                "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": a_bytes,
-                "traffic": ncu_traffic(dom, args.workload),
-                "kernel_share": {k: round(v[1] / sum(x[1] for x in rows.values()), 4)
-                                 for k, v in sorted(rows.items(), key=lambda kv: -kv[1][1])}}
+        share = {k: round(v[1] / sum(x[1] for x in rows.values()), 4)
+                 for k, v in sorted(rows.items(), key=lambda kv: -kv[1][1])}
+        hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+               "peak_kind": peak_kind, "algorithmic_bytes_per_launch": a_bytes,
+               "traffic": ncu_traffic(dom, args.workload)}
+        pairs = work.algorithmic_pairs().get(dom) if hasattr(work, "algorithmic_pairs") else None
+        # the binding roofline: the larger of the two minimum times (bytes at
+        # the HBM peak, pair tests at the ALU peak)
+        t_hbm = (a_bytes / (peak * 1e9)) if a_bytes else 0.0
+        t_alu = (pairs / PAIR_PEAK) if pairs else 0.0
+        if pairs and t_alu > t_hbm:
+            ach = pairs / (avg_ms * 1e-3)
+            roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": PAIR_PEAK, "unit": "pair tests/s",
+                    "frac": ach / PAIR_PEAK, "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 (FP32x2) x "
+                    "2.032 GHz / 6 operations per pair test", "algorithmic_pairs_per_launch": pairs,
+                    "traffic": hbm["traffic"], "avg_launch_ms": avg_ms, "hbm": hbm, "kernel_share": share}
+        else:
+            roof = dict(bound="hbm", kernel=dom, avg_launch_ms=avg_ms, kernel_share=share, **hbm)
     step_gbs = work.step_bytes() / (ms_step * 1e-3) / 1e9
     e2e = None
     if not args.no_e2e and isinstance(work, RadiusWork):
