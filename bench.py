@@ -381,6 +381,11 @@ class CentersWork:
         tot = max(lens.sum(), 1)
         return light.mean(), lens[light].sum() / tot
 
+    def algorithmic_pairs(self):
+        """The list method tests every (center, point) pair."""
+        p = float(self.scene.n) * self.queries
+        return {"k_radius_all_count": p, "k_radius_all_write": p}
+
     def algorithmic_bytes(self):
         s, m = self.scene, self.queries
         n, C = s.n, (1 << sum(s.log2_cells)) + 1
@@ -393,7 +398,10 @@ class CentersWork:
                 "k_radius_count": fl * q_b + 4 * C,
                 "k_radius_write": fl * q_b + 4 * C + tl * 4 * self.total,
                 "k_radius_dense_count": (1 - fl) * q_b + 4 * C,
-                "k_radius_dense_write": (1 - fl) * q_b + 4 * C + (1 - tl) * 4 * self.total}
+                "k_radius_dense_write": (1 - fl) * q_b + 4 * C + (1 - tl) * 4 * self.total,
+                # list method: the points once, each center, its count or offset, the lists
+                "k_radius_all_count": 16 * n + 16 * m + 4 * m + 8 * m,
+                "k_radius_all_write": 16 * n + 16 * m + 4 * m + 8 * m + 4 * self.total}
 
     def step_bytes(self):
         s, m = self.scene, self.queries
@@ -538,11 +546,21 @@ def make_work(name):
         return LoopWork(synth.batched_scenes()), "256 uneven scenes, plain path looped per scene"
     if name == "tiny":
         return RadiusWork([synth.tiny_scene()]), "20k-point radius, 32^3 non-cyclic, r=0.96 cells"
+    if name == "radius_far_20k":
+        return CentersWork(make_work_scene_far(), synth.uniform_points(100_000, 0x51D00301)), \
+            "20,480 uniform points, 64^3 cyclic (load 0.078), r = 24 cells, 100k uniform centers: " \
+            "the volume comparison takes the non-empty list method"
     if name == "radius_centers_1m":
         return CentersWork(synth.mixture_1m_scene(), centers_1m()), \
             "1M Gaussian-mixture points, 128^3 cyclic, r=1.5 cells; 1M query centers, half from the " \
             "same mixture (another seed), half uniform"
     raise SystemExit(f"unknown workload {name}")
+
+
+def make_work_scene_far():
+    from paper_cs_0608108_b300 import synth
+    return synth.Scene(synth.uniform_points(20_480, 0x51D00300), (0.0, 0.0, 0.0), 1.0 / 64, (6, 6, 6), 7,
+                       24.0 / 64, "far_20k")
 
 
 def centers_1m():
@@ -649,6 +667,8 @@ def _oracle_scene(name):
         return synth.mixture_1m_scene()
     if name == "knn_4m":
         return synth.knn_4m_scene()
+    if name == "radius_far_20k":
+        return make_work_scene_far()
     if name == "tiny":
         return synth.tiny_scene()
     return synth.batched_scenes()[0]
@@ -666,6 +686,9 @@ class OracleRunner:
         self.threads = oracle.max_threads()
         self.rng = np.random.default_rng(0)
         self.centers = centers_1m() if name == "radius_centers_1m" else None
+        if name == "radius_far_20k":
+            from paper_cs_0608108_b300 import synth
+            self.centers = synth.uniform_points(100_000, 0x51D00301)
 
     def run(self, m):
         sc, o = self.sc, self.oracle
