@@ -16,6 +16,10 @@
  *     only the opaque objects it returns (si_grid, si_batch).
  *   - Every call is ordered on `stream` (a cudaStream_t; NULL = legacy
  *     default stream) and returns without synchronising unless stated.
+ *   - A grid's calls share its device work buffers (queues, scratch, the
+ *     center buffers): calls on one grid must not overlap on the GPU (issue
+ *     them on one stream, or order the streams); different grids are
+ *     independent.  A grid is not safe to use from two host threads at once.
  *   - Errors are returned as si_status; no call aborts or throws.
  *     si_last_error() gives a one-line message for the calling host thread.
  *   - Distances follow one canonical predicate, identical on every path:
