@@ -630,11 +630,34 @@ def job_value(queries_per_rank: int, world: int, ms_step: float) -> float:
     return queries_per_rank * world / (ms_step * 1e-3)
 
 
-def time_steps(work, steps, warmup, flush):
+def capture_step(work):
+    """The step captured once in a CUDA graph (every call of the step is
+    asynchronous once its tables and buffers are sized); returns the graph
+    and the number of library kernels it holds."""
+    import torch
+    from paper_cs_0608108_b300 import launch_count
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        work.step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    l0 = launch_count()
+    with torch.cuda.graph(graph):
+        work.step()
+    torch.cuda.synchronize()
+    return graph, launch_count() - l0
+
+
+def time_steps(work, steps, warmup, flush, graph=None):
+    """Per-step device times (CUDA events on the launching stream, L2 flushed
+    before each step); graph: replay it instead of calling the step."""
     import torch
     st = torch.cuda.current_stream()
+    run = graph.replay if graph is not None else work.step
     for _ in range(warmup):
-        work.step()
+        run()
     work.check()
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -642,7 +665,7 @@ def time_steps(work, steps, warmup, flush):
     for a, b in evs:
         flush.zero_()                        # evict L2 between timed steps
         a.record(st)
-        work.step()
+        run()
         b.record(st)
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in evs]
@@ -734,6 +757,7 @@ def main():
     ap.add_argument("--workload", default="radius_1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="call the step eagerly instead of replaying its graph")
     args = ap.parse_args()
     rank, world, local = dist_setup()
     if args.warmup < 3:
@@ -789,10 +813,19 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    # radius workloads replay the step as one CUDA graph (the batched path does
+    # the same inside the library); the plain-path loop stays eager
+    use_graph = (not args.no_graph and isinstance(work, RadiusWork) and not isinstance(work, LoopWork))
+    graph, graph_launches = None, 0
+    if use_graph:
+        for _ in range(2):
+            work.step()
+        work.check()
+        graph, graph_launches = capture_step(work)
     l0 = launch_count()
     with ClockSampler(local) as clk:
-        ms = time_steps(work, args.steps, args.warmup, flush)
-    launches = (launch_count() - l0) // (args.steps + args.warmup)
+        ms = time_steps(work, args.steps, args.warmup, flush, graph)
+    launches = graph_launches if use_graph else (launch_count() - l0) // (args.steps + args.warmup)
     work.check()
     ms_step = slowest_rank_ms(float(np.mean(ms)))
     value = job_value(work.queries, world, ms_step)
@@ -840,6 +873,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "l2": "flushed between steps",
+                       "step": "one CUDA graph replay of the library calls" if use_graph else "library calls",
                        "queries_per_step": work.queries, "parallelism": f"replicas x{world}"},
             "step_algorithmic_gbs": step_gbs, "step_hbm_frac": step_gbs / peak,
             "roofline": roof, "gpu_launches": int(launches), "clocks": clk.summary(), "e2e": e2e,
