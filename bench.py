@@ -813,9 +813,10 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    # radius workloads replay the step as one CUDA graph (the batched path does
-    # the same inside the library); the plain-path loop stays eager
-    use_graph = (not args.no_graph and isinstance(work, RadiusWork) and not isinstance(work, LoopWork))
+    # the query workloads replay the step as one CUDA graph (the batched path
+    # does the same inside the library); the plain-path loop stays eager
+    use_graph = (not args.no_graph and isinstance(work, (RadiusWork, CentersWork, KnnWork))
+                 and not isinstance(work, LoopWork))
     graph, graph_launches = None, 0
     if use_graph:
         for _ in range(2):
