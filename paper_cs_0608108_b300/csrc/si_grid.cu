@@ -551,7 +551,8 @@ __global__ void __launch_bounds__(kOrderWarps * 32) k_cell_order_big(const int *
     }
     for (int i = lane; i < m; i += 32) buf[i] = perm[b + i];
     __syncwarp();
-    bitonic_padded(buf, m, lane, 32, WarpSync());
+    warp_sort(buf, m, lane, 0x7fffffff);
+    __syncwarp();
     for (int i = lane; i < m; i += 32) {
       perm[b + i] = buf[i];
       spos[b + i] = __ldg(pos + buf[i]);

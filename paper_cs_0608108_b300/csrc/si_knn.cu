@@ -400,7 +400,8 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, f
     return;
   }
   __syncwarp();
-  bitonic_padded(key, cnt, lane, 32, WarpSync());
+  warp_sort(key, cnt, lane, ~0ull);
+  __syncwarp();
   // runs of keys closer than the FP32 error bound, up to the K-th (and the
   // first one past it, which decides who is in), in canonical order
   const int top = min(cnt, K + 1);

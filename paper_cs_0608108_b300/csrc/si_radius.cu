@@ -467,7 +467,8 @@ __global__ void __launch_bounds__(kClassThreads, 4) k_radius_dense(GridDev g, Wa
       const bool sort_all = !(flags & SI_NO_SORT);
       if (staged) {
         __syncwarp();
-        if (sort_all) bitonic_padded(buf, len, lane, 32, WarpSync());
+        if (sort_all) warp_sort(buf, len, lane, 0x7fffffff);
+        __syncwarp();
         for (int i = lane; i < len; i += 32) ids[base + i] = buf[i];
         __syncwarp();
       } else if (sort_all && lane == 0) {
@@ -514,7 +515,8 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_warp(const long long *
     }
     for (int i = lane; i < len; i += 32) buf[i] = list[i];
     __syncwarp();
-    bitonic_padded(buf, len, lane, 32, WarpSync());
+    warp_sort(buf, len, lane, 0x7fffffff);
+    __syncwarp();
     for (int i = lane; i < len; i += 32) list[i] = buf[i];
     __syncwarp();
   }

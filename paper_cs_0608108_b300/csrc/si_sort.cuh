@@ -44,9 +44,69 @@ __device__ __forceinline__ void bitonic_padded(T *a, int n, int rank, int lanes,
   }
 }
 
+// Ascending sort of a[0..n), n <= 32 E, by one warp with the keys in
+// registers: element e = r * 32 + lane sits in lane `lane`, slot r; keys past
+// n are padded with the largest value.  The bitonic network is unrolled at
+// compile time: a stage whose partner distance j is below 32 exchanges with
+// lane ^ j by shuffle, a larger one between the lane's own slots, so no index
+// arithmetic, shared-memory round trip or barrier sits between stages.  All
+// 32 lanes must call it; a[] is read before and written after (callers order
+// those accesses with __syncwarp).
+template <int E, class T>
+__device__ __forceinline__ void warp_sort_regs(T *a, int n, int lane, T pad) {
+  constexpr int N = 32 * E;
+  T v[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) v[r] = (r * 32 + lane < n) ? a[r * 32 + lane] : pad;
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+        const int rj = j >> 5;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          if (r & rj) continue;
+          const bool asc = ((r * 32) & k) == 0;   // k >= 64 here: the lane bits do not reach k
+          const T x = v[r], y = v[r | rj];
+          const bool sw = asc ? (y < x) : (x < y);
+          v[r] = sw ? y : x;
+          v[r | rj] = sw ? x : y;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const T o = __shfl_xor_sync(0xffffffffu, v[r], j);
+          const int e = r * 32 + lane;
+          const bool asc = (e & k) == 0;
+          const bool lower = (lane & j) == 0;
+          const bool take_min = lower == asc;
+          const T x = v[r];
+          v[r] = take_min ? (o < x ? o : x) : (x < o ? o : x);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < E; ++r)
+    if (r * 32 + lane < n) a[r * 32 + lane] = v[r];
+}
+
 struct WarpSync {
   __device__ __forceinline__ void operator()() const { __syncwarp(); }
 };
+
+// One warp sorts a[0..n) ascending: up to 128 keys in registers, more with
+// the shared-memory network.  pad must exceed every key.  Callers order the
+// accesses to a[] around it with __syncwarp.
+template <class T>
+__device__ __forceinline__ void warp_sort(T *a, int n, int lane, T pad) {
+  if (n <= 1) return;
+  if (n <= 32) warp_sort_regs<1>(a, n, lane, pad);
+  else if (n <= 64) warp_sort_regs<2>(a, n, lane, pad);
+  else if (n <= 128) warp_sort_regs<4>(a, n, lane, pad);
+  else bitonic_padded(a, n, lane, 32, WarpSync());
+}
 struct BlockSync {
   __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
