@@ -231,7 +231,7 @@ struct KnnRuns {                  // up to two runs per row of a 32-row batch
 };
 
 // First pass within dmax1 (n1, B1: its table bound and guard band), a radius
-// expected to hold about 1.5 K points: exact whenever it holds at least K
+// expected to hold about K + 2 sqrt(K) + 4 points: exact whenever it holds at least K
 // (the K nearest then all lie within it); else a second pass within r_max
 // (dmax_g, n_query, B).  dmax1 == dmax_g: one pass.  list (nullable): [0] =
 // count, then the sorted slots to serve; else every slot.
@@ -527,14 +527,15 @@ extern "C" si_status si_query_knn(si_grid *g, const float *d_centers, int64_t m,
                                                                      d_ids, d_d2, d_counts, list));
     return SI_OK;
   }
-  // first cut: the radius expected to hold 1.5 K + 8 points at the mean load
-  // (exact when it holds K; the kernel widens it to r_max otherwise)
+  // first cut: the radius expected to hold K + 2 sqrt(K) + 4 points at the
+  // mean load, two standard deviations of a Poisson count above K (exact when
+  // it holds K; the kernel widens it to r_max otherwise)
   float dmax1 = dmax_g;
   int n1 = n_query;
   Band B1 = B;
   const double load = (double)g->n / (double)std::max<int64_t>(g->n_cells - 1, 1);
   if (load > 0.0) {
-    const double want = 1.5 * k + 8.0;
+    const double want = k + 2.0 * std::sqrt((double)k) + 4.0;
     const double r1 = std::cbrt(3.0 * want / (4.0 * M_PI * load)) / (double)lat.inv_s;   // world units
     if (r1 < 0.9 * (double)r_max_query) {
       B1 = make_band(lat, (float)r1);
