@@ -211,3 +211,34 @@ def test_reduce_invariants():
     # every pair within r contributes: e_i > 0 exactly when i has a neighbor
     off, _ = oracle.radius(pos, pos, UNIT, 7, float(np.nextafter(0.1, 0)), np.arange(1500))
     assert np.array_equal(e > 0, np.diff(off) > 0)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_queries_from_arbitrary_centers_match_scipy_kdtree(periodic):
+    """Caller-given centers (nothing excluded; a center on a point finds it):
+    radius lists and K nearest against an independent k-d tree."""
+    pos = synth.uniform_points(3000, 31 if periodic else 32)
+    cen = synth.uniform_points(1500, 33)
+    cen[:10] = pos[:10]                          # centers on top of points
+    mask = 7 if periodic else 0
+    tp = cKDTree(pos[:, :3].astype(np.float64), boxsize=UNIT if periodic else None)
+    tc = cKDTree(cen[:, :3].astype(np.float64), boxsize=UNIT if periodic else None)
+    r = 0.06
+    for _ in range(50):                          # a radius no center-point distance sits on
+        dd = tc.sparse_distance_matrix(tp, r * 1.000001, output_type="ndarray")["v"]
+        if not np.any(np.abs(dd - r) < 1e-9 * r):
+            break
+        r *= 1.0001
+    off, ids = oracle.radius(pos, cen, UNIT, mask, r, None)
+    for k, lst in enumerate(_lists(off, ids)):
+        want = sorted(tp.query_ball_point(cen[k, :3].astype(np.float64), r))
+        assert lst.tolist() == want
+    assert all(k in _lists(off, ids)[k].tolist() for k in range(10))
+    kk = 6
+    kid, kd2, kcnt = oracle.knn(pos, cen, UNIT, mask, kk, None, None)
+    dist, nbr = tp.query(cen[:, :3].astype(np.float64), k=kk)
+    assert np.all(kcnt == kk)
+    assert np.allclose(np.sqrt(kd2), dist, rtol=1e-12, atol=1e-15)
+    distinct = np.all(np.diff(dist, axis=1) > 1e-12, axis=1)
+    assert np.array_equal(kid[distinct], nbr[distinct])
+    assert np.all(kid[:10, 0] == np.arange(10))   # distance 0 first
