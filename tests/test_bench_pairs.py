@@ -62,3 +62,31 @@ def test_candidate_pairs_split_by_class_and_scaled_sample():
     assert sum(full.values()) > 0 and full[1] + full[3] > 0
     # a quarter sample scaled up estimates the total within a few percent
     assert abs(sum(half.values()) - sum(full.values())) < 0.05 * sum(full.values())
+
+
+def test_cell_classes_follow_the_binning_rule():
+    """Heavy: >= 8 points, or >= 3 with >= 12 in the cell and its two packed
+    neighbours; large heavy: heavy with >= 768 in the 27 cells around it (y, z
+    wrapped, x clipped); dense: not heavy, >= 24 around it; the outside cell
+    dense with >= 24 points."""
+    scene = synth.Scene(synth.gaussian_mixture_points(30_000, 9, n_comp=6, sigma=0.02), (0, 0, 0), 1 / 16,
+                        (4, 4, 4), 7, 1.5 / 16)
+    start = cell_start(scene)
+    cls = bench.cell_classes(start, scene.log2_cells)
+    cnt = np.diff(start)
+    G = 16
+    nc = G ** 3
+    for key in range(nc):
+        x, y, z = key % G, (key // G) % G, key // (G * G)
+        row = start[min(key + 2, nc)] - start[max(key - 1, 0)] if 1 <= key <= nc - 2 else 0
+        heavy = cnt[key] >= 8 or (cnt[key] >= 3 and row >= 12)
+        n27 = 0
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    xx = x + dx
+                    if 0 <= xx < G:
+                        n27 += cnt[((z + dz) % G) * G * G + ((y + dy) % G) * G + xx]
+        want = (3 if n27 >= 768 else 1) if heavy else (2 if n27 >= 24 else 0)
+        assert cls[key] == want, key
+    assert cls[nc] == (2 if cnt[nc] >= 24 else 0)
