@@ -201,17 +201,18 @@ def candidate_pairs(scene, start, cls, sample=131_072):
 class RadiusWork:
     """Bin + all-agents radius query for a list of scenes."""
 
-    def __init__(self, scenes, method="sphere"):
+    def __init__(self, scenes, method="sphere", walk="classes"):
         import torch
         from paper_cs_0608108_b300 import Grid
         self.scenes = scenes
         self.method = method
+        self.walk = walk
         self.pos = [torch.from_numpy(s.pos).cuda() for s in scenes]
         self.grids = [Grid.for_scene(s) for s in scenes]
         self.off, self.ids, self.totals = [], [], []
         for g, p, s in zip(self.grids, self.pos, scenes):
             g.build(p)
-            off, ids = g.query_radius(s.r, method=method)
+            off, ids = g.query_radius(s.r, method=method, walk=walk)
             g.sync()
             self.totals.append(int(off[-1].item()))
             self.off.append(off)
@@ -221,7 +222,8 @@ class RadiusWork:
     def step(self):
         for g, p, s, off, ids in zip(self.grids, self.pos, self.scenes, self.off, self.ids):
             g.build(p)
-            g.query_radius(s.r, method=self.method, out_offsets=off, out_ids=ids, sync_total=False)
+            g.query_radius(s.r, method=self.method, walk=self.walk, out_offsets=off, out_ids=ids,
+                           sync_total=False)
 
     def check(self):
         for g in self.grids:
@@ -278,6 +280,8 @@ class RadiusWork:
                 "k_cell_expand": (fs + fb) * (4 * n + 8 * n) + (ts + tb) * 4 * tot,
                 "k_radius_count_cube": 16 * n + 4 * n + 4 * C + 8 * n,
                 "k_radius_write_cube": 16 * n + 4 * n + 4 * C + 8 * n + 4 * tot,
+                "k_radius_count_planes": 16 * n + 4 * n + 4 * C + 8 * n,
+                "k_radius_write_planes": 16 * n + 4 * n + 4 * C + 8 * n + 4 * tot,
             }
             for kk, v in per.items():
                 out.setdefault(kk, []).append(v)
@@ -299,6 +303,8 @@ class RadiusWork:
         for k, s in enumerate(self.scenes):
             start, _, _ = (t.cpu().numpy() for t in self.grids[k].cell_arrays())
             p = candidate_pairs(s, start, cell_classes(start, s.log2_cells))
+            out.setdefault("k_radius_count_planes", []).append(sum(p.values()))
+            out.setdefault("k_radius_write_planes", []).append(sum(p.values()))
             for name, c in (("k_radius_count", 0), ("k_radius_write", 0), ("k_radius_dense_count", 2),
                             ("k_radius_dense_write", 2), ("k_cell", 1), ("k_cell_large", 3)):
                 out.setdefault(name, []).append(p[c])
@@ -330,7 +336,7 @@ def e2e_radius(work, steps, warmup):
             g.build(dpos[k])
             if done[b][k] is not None:
                 comp.wait_event(done[b][k])     # the output set's previous copy has landed
-            g.query_radius(s.r, out_offsets=offs[b][k], out_ids=idss[b][k], sync_total=False)
+            g.query_radius(s.r, walk=work.walk, out_offsets=offs[b][k], out_ids=idss[b][k], sync_total=False)
             ready = torch.cuda.Event()
             ready.record(comp)
             copy.wait_event(ready)
@@ -571,6 +577,13 @@ def make_work(name):
         return LoopWork(synth.batched_scenes()), "256 uneven scenes, plain path looped per scene"
     if name == "tiny":
         return RadiusWork([synth.tiny_scene()]), "20k-point radius, 32^3 non-cyclic, r=0.96 cells"
+    if name in ("terrain_1m", "terrain_1m_planes"):
+        sc = synth.Scene(synth.terrain_points(1_000_000, 0x51D00400), (0.0, 0.0, 0.0), 1.0 / 128, (7, 7, 7), 3,
+                         1.5 / 128, "terrain_1m")
+        walk = "planes" if name.endswith("planes") else "classes"
+        return RadiusWork([sc], walk=walk), \
+            f"1M agents on a bumpy terrain (z = 0.5 + 0.01 sin sin), 2% flying, 128^3, cyclic x, y, r = 1.5 cells, " \
+            f"{walk} walk"
     if name == "radius_far_20k":
         return CentersWork(make_work_scene_far(), synth.uniform_points(100_000, 0x51D00301)), \
             "20,480 uniform points, 64^3 cyclic (load 0.078), r = 24 cells, 100k uniform centers: " \
@@ -717,6 +730,9 @@ def _oracle_scene(name):
         return synth.knn_4m_scene()
     if name == "radius_far_20k":
         return make_work_scene_far()
+    if name in ("terrain_1m", "terrain_1m_planes"):
+        return synth.Scene(synth.terrain_points(1_000_000, 0x51D00400), (0.0, 0.0, 0.0), 1.0 / 128, (7, 7, 7), 3,
+                           1.5 / 128, "terrain_1m")
     if name == "tiny":
         return synth.tiny_scene()
     return synth.batched_scenes()[0]

@@ -63,6 +63,10 @@ typedef enum {
 #define SI_SPHERE_ONLY    32u  /* radius: the spherical index without the volume
                                   comparison (Sec. IV.A, Fig. 8): never switch
                                   to the list method                           */
+#define SI_WALK_PLANES    64u  /* radius: stacked circle-indexed z-planes (Sec. V),
+                                  each plane skipped when empty, taken as its
+                                  point list when sparse, else walked by rows:
+                                  for points concentrated on a few planes      */
 
 /* Region, lattice and table extent (Sec. II.B).  The box side on axis a is
  * L_a = cell_size * 2^log2_cells[a] (exact in float32).  A cyclic axis wraps

@@ -159,13 +159,14 @@ class Grid:
         index, switching to the list method when the volume comparison says
         it is cheaper), "sphere_only" (never switching), "cube" (bin-lattice
         scan) or "list" (non-empty list: every object tested); walk "classes"
-        (sub-cell class tables) or "paper" (Sec. III.A 64 tables)."""
+        (sub-cell class tables), "paper" (Sec. III.A 64 tables) or "planes"
+        (stacked z-planes, Sec. V)."""
         if method not in ("sphere", "sphere_only", "cube", "list"):
             raise ValueError(f"unknown method {method!r}")
         flags = (N.SI_INCLUDE_SELF if include_self else 0) | (0 if sort else N.SI_NO_SORT) | \
                 {"sphere": 0, "sphere_only": N.SI_SPHERE_ONLY, "cube": N.SI_METHOD_CUBE,
                  "list": N.SI_METHOD_LIST}[method] | \
-                (N.SI_WALK_PAPER if walk == "paper" else 0)
+                (N.SI_WALK_PAPER if walk == "paper" else 0) | (N.SI_WALK_PLANES if walk == "planes" else 0)
         dev = self._pos.device
         m = self.n
         if centers is not None:

@@ -113,12 +113,13 @@ struct StageVisitor {
 };
 
 // Cell walks of the per-query kernels.
-enum Walk : int { kWalkPaper = 0, kWalkClasses = 1, kWalkCube = 2 };
+enum Walk : int { kWalkPaper = 0, kWalkClasses = 1, kWalkCube = 2, kWalkPlanes = 3 };
 
 template <int WALK, class V>
 __device__ __forceinline__ void walk_one(const GridDev &g, const QueryGeom &Q, const WalkParams &P, V &v) {
   if (WALK == kWalkCube || Q.outside) walk_cube(g, Q, P.dg, v);
   else if (WALK == kWalkClasses) walk_classes_in(g, Q, g.cls, g.cls_begin, g.cls_q, v);
+  else if (WALK == kWalkPlanes) walk_planes(g, Q, P.dg, v);
   else walk_sphere(g, Q, P, v);
 }
 
@@ -600,6 +601,10 @@ static si_status launch_light(int walk, const si_grid *gr, const GridDev &dv, co
                k_radius_cls<WRITE><<<grid, kClassThreads, smem, st>>>(
                    dv, P, B, flags, skip, (int)gr->cls_host.size(), counts, off, ids, cap, longq,
                    list, lstage, lstride));
+  } else if (walk == kWalkPlanes) {
+    SI_KLAUNCH(WRITE ? "k_radius_write_planes" : "k_radius_count_planes", st,
+               k_radius<WRITE, kWalkPlanes><<<blocks, kQueryThreads, 0, st>>>(
+                   dv, P, B, flags, skip, counts, off, ids, cap, longq, list));
   } else if (walk == kWalkClasses) {
     SI_KLAUNCH(WRITE ? "k_radius_write_cls_l2" : "k_radius_count_cls_l2", st,
                k_radius<WRITE, kWalkClasses><<<blocks, kQueryThreads, 0, st>>>(
@@ -726,8 +731,9 @@ static si_status query_radius_centers(si_grid *g, const float *d_centers, int64_
   const WalkParams P = walk_params(g->lat, r, load >= 4.0);
   const Band B = make_band(g->lat, r);
   const int walk = cube ? kWalkCube
-                        : ((!(flags & SI_WALK_PAPER) && g->ensure_classes(P.dg, st)) ? kWalkClasses
-                                                                                    : kWalkPaper);
+                        : ((flags & SI_WALK_PLANES) ? kWalkPlanes
+                           : ((!(flags & SI_WALK_PAPER) && g->ensure_classes(P.dg, st)) ? kWalkClasses
+                                                                                       : kWalkPaper));
   const bool split = dense_path(walk, g);
   long long *off = (long long *)d_offsets;
   CenterOut eo;
@@ -782,14 +788,15 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
     return fail(SI_ERR_INVALID, "radius exceeds the grid's r_max");
   if (!d_offsets) return fail(SI_ERR_INVALID, "null offsets");
   if (ids_capacity < 0 || (ids_capacity > 0 && !d_ids)) return fail(SI_ERR_INVALID, "bad ids buffer");
-  if (flags & ~(SI_METHOD_CUBE | SI_INCLUDE_SELF | SI_NO_SORT | SI_WALK_PAPER | SI_METHOD_LIST | SI_SPHERE_ONLY))
+  if (flags & ~(SI_METHOD_CUBE | SI_INCLUDE_SELF | SI_NO_SORT | SI_WALK_PAPER | SI_METHOD_LIST | SI_SPHERE_ONLY |
+                SI_WALK_PLANES))
     return fail(SI_ERR_INVALID, "unknown flags");
   if ((flags & SI_METHOD_CUBE) && (flags & SI_METHOD_LIST))
     return fail(SI_ERR_INVALID, "SI_METHOD_CUBE and SI_METHOD_LIST are exclusive");
   cudaStream_t st = (cudaStream_t)stream;
   if (flags & SI_METHOD_LIST)
     return query_radius_list(g, d_centers, m, r, flags, d_offsets, d_ids, ids_capacity, h_total, st);
-  if (!(flags & (SI_METHOD_CUBE | SI_WALK_PAPER | SI_SPHERE_ONLY))) {
+  if (!(flags & (SI_METHOD_CUBE | SI_WALK_PAPER | SI_SPHERE_ONLY | SI_WALK_PLANES))) {
     // the walk the sphere method would take (class tables when they can be
     // built for this radius), then the volume comparison
     const WalkParams P0 = walk_params(g->lat, r, false);
@@ -802,12 +809,15 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   const double load = g->n_cells > 1 ? (double)g->n / (double)(g->n_cells - 1) : 0.0;
   const WalkParams P = walk_params(g->lat, r, load >= 4.0);
   const Band B = make_band(g->lat, r);
+  const bool planes = !cube && (flags & SI_WALK_PLANES);
   const int walk = cube ? kWalkCube
-                        : ((!(flags & SI_WALK_PAPER) && g->ensure_classes(P.dg, st)) ? kWalkClasses
-                                                                                    : kWalkPaper);
+                        : (planes ? kWalkPlanes
+                                  : ((!(flags & SI_WALK_PAPER) && g->ensure_classes(P.dg, st)) ? kWalkClasses
+                                                                                              : kWalkPaper));
   // the cell path holds the runs of the whole cell-level sphere (rows of
-  // cells with b^2 <= floor(d^2), at most two runs per row and the outside cell)
-  const bool heavy = !cube && g->ensure_cell_rows(P.dg, st) && 2 * g->n_crow + 1 <= kCellTCap;
+  // cells with b^2 <= floor(d^2), at most two runs per row and the outside cell);
+  // the stacked-plane walk serves every query itself
+  const bool heavy = !cube && !planes && g->ensure_cell_rows(P.dg, st) && 2 * g->n_crow + 1 <= kCellTCap;
   // the count pass keeps short lists for the write pass in a staging area
   // (allocated on first use; without it the write pass walks every list again)
   if (walk == kWalkClasses && g->cls_smem_bytes > 0 && !g->lstage && g->cap > 0) {

@@ -193,6 +193,111 @@ __device__ __forceinline__ void walk_cube(const GridDev &g, const QueryGeom &Q, 
   }
 }
 
+// Stacked planes (Sec. V: circle-indexed planes stacked to make the sphere,
+// each plane choosing between its circle and its non-empty list).  For each
+// z-plane the sphere reaches (its minimum z-distance from the query, with the
+// shrunk zetas, within d), the plane's points are one contiguous range of
+// the sorted array (consecutive packed indices): an empty plane costs its two
+// bounds; a plane holding fewer points than half its circle's x-rows is
+// visited as that one range, every pair tested in FP64 (any image may be
+// nearest, as for the outside cell); otherwise the circle of radius
+// sqrt(d^2 - gz^2) is walked row by row, each row's x-interval from the
+// query's exact y-distance to it, one contiguous range per row (two where it
+// crosses the cyclic x boundary).  Points agents concentrate on a few planes
+// skip the empty ones wholesale.  Query centers outside the region take the
+// bounding-cube walk (walk_one).
+template <class V>
+__device__ __forceinline__ void walk_planes(const GridDev &g, const QueryGeom &Q, float dg, V &visit) {
+  const int Gx = 1 << g.wx, Gy = 1 << g.wy, Gz = 1 << g.wz;
+  const bool cyc_x = g.cyc & 1u, cyc_y = (g.cyc >> 1) & 1u, cyc_z = (g.cyc >> 2) & 1u;
+  const int pshift = g.wx + g.wy;
+  bool out_seen = false;
+  auto outside = [&]() {
+    if (out_seen) return;
+    out_seen = true;
+    Target t;
+    t.key = g.outside;
+    t.outside = true;
+    t.wrapped = false;
+    t.qx = Q.q.x;
+    t.qy = Q.q.y;
+    t.qz = Q.q.z;
+    visit(t, false, __ldg(g.cell_start + g.outside), __ldg(g.cell_start + g.outside + 1));
+  };
+  const int R = (int)dg + 1;
+  for (int dz = -R; dz <= R; ++dz) {
+    const float gz = dz > 0 ? (float)(dz - 1) + Q.zp[2] : (dz < 0 ? (float)(-dz - 1) + Q.zn[2] : 0.f);
+    if (gz > dg) continue;
+    int z = Q.c[2] + dz;
+    float sz = 0.f;
+    if (z < 0 || z >= Gz) {
+      if (!cyc_z) {
+        outside();
+        continue;
+      }
+      sz = z < 0 ? -g.Lz : g.Lz;   // the plane's image: compare against q - sz
+      z = z < 0 ? z + Gz : z - Gz;
+    }
+    const int ps = __ldg(g.cell_start + ((unsigned)z << pshift));
+    const int pe = __ldg(g.cell_start + ((unsigned)(z + 1) << pshift));
+    if (pe == ps) continue;
+    const float rc2 = fmaxf(dg * dg - gz * gz, 0.f);
+    const float rc = sqrtf(rc2);
+    if (2 * (pe - ps) <= 2 * (int)rc + 1) {   // fewer points than half the circle's rows
+      Target t;
+      t.key = 0u;
+      t.outside = true;
+      t.wrapped = false;
+      t.qx = Q.q.x;
+      t.qy = Q.q.y;
+      t.qz = Q.q.z;
+      visit(t, false, ps, pe);
+      continue;
+    }
+    const int Ry = (int)rc + 1;
+    for (int dy = -Ry; dy <= Ry; ++dy) {
+      const float gy = dy > 0 ? (float)(dy - 1) + Q.zp[1] : (dy < 0 ? (float)(-dy - 1) + Q.zn[1] : 0.f);
+      if (gy > rc) continue;
+      int y = Q.c[1] + dy;
+      float sy = 0.f;
+      if (y < 0 || y >= Gy) {
+        if (!cyc_y) {
+          outside();
+          continue;
+        }
+        sy = y < 0 ? -g.Ly : g.Ly;
+        y = y < 0 ? y + Gy : y - Gy;
+      }
+      const float h = sqrtf(fmaxf(rc2 - gy * gy, 0.f)) + g.eps;
+      int x0 = (int)floorf(Q.u[0] - h), x1 = (int)floorf(Q.u[0] + h);
+      const unsigned row = ((unsigned)z << pshift) | ((unsigned)y << g.wx);
+      Target tg;
+      tg.key = row;
+      tg.outside = false;
+      tg.wrapped = (sy != 0.f) || (sz != 0.f);
+      tg.qx = Q.q.x;
+      tg.qy = Q.q.y - sy;
+      tg.qz = Q.q.z - sz;
+      if (!cyc_x) {
+        if (x0 < 0 || x1 >= Gx) outside();
+        x0 = max(x0, 0);
+        x1 = min(x1, Gx - 1);
+        if (x0 > x1) continue;
+      } else if (x0 < 0 || x1 >= Gx) {
+        const int wa = x0 < 0 ? x0 + Gx : 0;
+        const int wb = x0 < 0 ? Gx - 1 : x1 - Gx;
+        Target tw = tg;
+        tw.qx = Q.q.x + (x0 < 0 ? g.Lx : -g.Lx);
+        tw.wrapped = true;
+        visit(tw, false, __ldg(g.cell_start + row + wa), __ldg(g.cell_start + row + wb + 1));
+        x0 = max(x0, 0);
+        x1 = min(x1, Gx - 1);
+      }
+      visit(tg, false, __ldg(g.cell_start + row + x0), __ldg(g.cell_start + row + x1 + 1));
+    }
+  }
+}
+
 // FP32 candidate test with FP64 recheck inside the guard band.  The outside
 // cell holds arbitrary positions (any image may be nearest), so its
 // candidates always take the FP64 path.

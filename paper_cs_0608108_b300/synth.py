@@ -88,6 +88,22 @@ def gaussian_mixture_points(n: int, seed: int, n_comp: int = 64, sigma: float = 
     return out
 
 
+def terrain_points(n: int, seed: int, flying: float = 0.02, z0: float = 0.5, amp: float = 0.01,
+                   waves: int = 3) -> np.ndarray:
+    """Agents on a bumpy terrain with a few flying objects: x, y uniform in the
+    unit square, z = z0 + amp * sin(2 pi waves x) * sin(2 pi waves y) for all
+    but a fraction `flying`, whose z is uniform in [0, 1)."""
+    u = splitmix64(seed, 4 * n).reshape(n, 4)
+    x, y, f, zf = (unit24(u[:, k]) for k in range(4))
+    z = z0 + amp * np.sin(2 * np.pi * waves * x) * np.sin(2 * np.pi * waves * y)
+    z = np.where(f < flying, zf, z)
+    out = np.zeros((n, 4), dtype=np.float32)
+    out[:, 0] = _to_box_f32(x, 1.0, 0.0)
+    out[:, 1] = _to_box_f32(y, 1.0, 0.0)
+    out[:, 2] = _to_box_f32(z, 1.0, 0.0)
+    return out
+
+
 def normal_steps(n: int, seed: int, step: int) -> np.ndarray:
     """Standard normal (n, 3) float64 increments for time step `step`."""
     u = splitmix64(seed + 0x5DEECE66D * (step + 1), 4 * n).reshape(n, 4)
