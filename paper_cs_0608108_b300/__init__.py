@@ -31,6 +31,13 @@ def _check_points(pos: torch.Tensor) -> torch.Tensor:
     return pos.contiguous()
 
 
+def _check_out(t, dtype, numel, what):
+    """A caller-given output buffer must be a contiguous CUDA tensor of the
+    right type holding at least `numel` elements (the library writes there)."""
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous() and t.numel() >= numel):
+        raise ValueError(f"{what} must be a contiguous CUDA {dtype} tensor with at least {numel} elements")
+
+
 def _centers(centers):
     """(tensor whose pointer is passed, m) for a centers argument.  A NULL
     pointer means all agents, so an empty centers tensor passes a one-row
@@ -172,6 +179,9 @@ class Grid:
         if centers is not None:
             centers, m = _centers(centers)
         off = out_offsets if out_offsets is not None else torch.empty(m + 1, dtype=torch.int64, device=dev)
+        _check_out(off, torch.int64, m + 1, "out_offsets")
+        if out_ids is not None:
+            _check_out(out_ids, torch.int32, 0, "out_ids")
         ids = out_ids
         if ids is None:
             cap = self._ids_cap or max(16 * m, 1024)
@@ -206,6 +216,10 @@ class Grid:
             cnt = torch.empty(m, dtype=torch.int32, device=dev)
         else:
             ids, d2, cnt = out
+            _check_out(ids, torch.int32, m * k, "out ids")
+            _check_out(cnt, torch.int32, m, "out counts")
+            if d2 is not None:
+                _check_out(d2, torch.float32, m * k, "out d2")
         rm = float("inf") if r_max is None else float(r_max)
         flags = N.SI_INCLUDE_SELF if include_self else 0
         N.check(self._lib.si_query_knn(self._h, _ptr(centers), m, int(k), rm, flags, _ptr(ids), _ptr(d2),
@@ -215,6 +229,12 @@ class Grid:
     def neighbor_reduce(self, r: float, energy=None, grad=None, grad_scale=None):
         """Fused smooth-kernel sum over radius neighbors: energy (float64[1]) and,
         when `grad` is given (float32[n,4]), dE/dx in input order."""
+        if energy is not None:
+            _check_out(energy, torch.float64, 1, "energy")
+        if grad is not None:
+            _check_out(grad, torch.float32, 4 * self.n, "grad")
+        if grad_scale is not None:
+            _check_out(grad_scale, torch.float32, 1, "grad_scale")
         N.check(self._lib.si_neighbor_reduce(self._h, float(r), N.SI_KERNEL_POLY6_CUBED, _ptr(energy),
                                              _ptr(grad), _ptr(grad_scale), _stream()),
                 "si_neighbor_reduce")

@@ -94,3 +94,22 @@ def test_k_above_the_number_of_points():
     oi, od, oc = oracle.knn(scene.pos, scene.pos, scene.box, 0, 64, None, np.arange(10))
     assert np.all(cnt.cpu().numpy() == 9) and np.array_equal(ids.cpu().numpy(), oi)
     assert np.all(np.isinf(d2.cpu().numpy()[:, 9:]))
+
+
+def test_caller_output_buffers_are_checked_before_the_call():
+    scene = synth.tiny_scene(2000, seed=3)
+    g = gpu_grid(scene)
+    small = torch.empty(10, dtype=torch.int64, device="cuda")
+    with pytest.raises(ValueError):
+        g.query_radius(scene.r, out_offsets=small)
+    with pytest.raises(ValueError):
+        g.query_radius(scene.r, out_offsets=torch.empty(scene.n + 1, dtype=torch.int32, device="cuda"))
+    ids = torch.empty((scene.n, 4), dtype=torch.int32, device="cuda")
+    cnt = torch.empty(scene.n, dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError):
+        g.query_knn(8, r_max=scene.r, out=(ids, None, cnt))       # room for 4 per query, not 8
+    with pytest.raises(ValueError):
+        g.neighbor_reduce(scene.r, energy=torch.empty(1, dtype=torch.float32, device="cuda"))
+    off, lst = g.query_radius(scene.r)                             # the grid is still usable
+    g.sync()
+    assert_csr_equal(off.cpu().numpy(), lst.cpu().numpy(), *oracle_radius(scene))
