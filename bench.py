@@ -908,7 +908,8 @@ def main():
     e2e = None
     if not args.no_e2e and isinstance(work, RadiusWork):
         e_ms, bi, bo = e2e_radius(work, max(3, args.steps // 2), 2)
-        e2e = {"value": work.queries * world / (e_ms * 1e-3), "unit": "queries/s",
+        e_ms = slowest_rank_ms(e_ms)
+        e2e = {"value": job_value(work.queries, world, e_ms), "unit": "queries/s",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": e_ms}
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
