@@ -688,9 +688,17 @@ def capture_step(work):
     return graph, launch_count() - l0
 
 
+def _barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
 def time_steps(work, steps, warmup, flush, graph=None):
     """Per-step device times (CUDA events on the launching stream, L2 flushed
-    before each step); graph: replay it instead of calling the step."""
+    before each step); graph: replay it instead of calling the step.  The
+    timed steps are bracketed by a device synchronisation and a barrier over
+    the ranks on both sides."""
     import torch
     st = torch.cuda.current_stream()
     run = graph.replay if graph is not None else work.step
@@ -698,6 +706,7 @@ def time_steps(work, steps, warmup, flush, graph=None):
         run()
     work.check()
     torch.cuda.synchronize()
+    _barrier()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(steps)]
     for a, b in evs:
@@ -706,6 +715,7 @@ def time_steps(work, steps, warmup, flush, graph=None):
         run()
         b.record(st)
     torch.cuda.synchronize()
+    _barrier()
     return [a.elapsed_time(b) for a, b in evs]
 
 
@@ -817,7 +827,8 @@ def main():
               "sample": r.describe(m, total, args.steps)}
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "dtype": "f64",
+                "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": {"workload": args.workload}, "cpu_baseline": cb,
                 "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
