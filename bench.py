@@ -559,6 +559,10 @@ def make_work(name):
         return RadiusWork([synth.uniform_1m_scene()]), "1M uniform all-agents radius, 128^3 cyclic, r=1.5 cells"
     if name == "radius_mixture":
         return RadiusWork([synth.mixture_1m_scene()]), "1M Gaussian-mixture all-agents radius, 128^3 cyclic, r=1.5 cells"
+    if name == "radius_mixture_250k":
+        return RadiusWork([synth.mixture_250k_scene()]), \
+            "250k Gaussian-mixture all-agents radius (16 components, the 1M mixture's density), 128^3 cyclic, " \
+            "r=1.5 cells"
     if name == "radius_uniform_cube":
         return RadiusWork([synth.uniform_1m_scene()], "cube"), "1M uniform, GPU bin-lattice cube scan"
     if name == "radius_mixture_cube":
@@ -734,6 +738,8 @@ def _oracle_scene(name):
     from paper_cs_0608108_b300 import synth
     if name in ("radius_1m", "radius_1m_cube", "walk_1m", "radius_uniform", "radius_uniform_cube"):
         return synth.uniform_1m_scene()
+    if name == "radius_mixture_250k":
+        return synth.mixture_250k_scene()
     if name in ("radius_mixture", "radius_mixture_cube", "radius_centers_1m"):
         return synth.mixture_1m_scene()
     if name == "knn_4m":

@@ -67,6 +67,10 @@ typedef enum {
                                   each plane skipped when empty, taken as its
                                   point list when sparse, else walked by rows:
                                   for points concentrated on a few planes      */
+#define SI_NO_GROUPS     128u  /* radius: serve every crowded cell on its own
+                                  (by default neighbouring crowded cells of an
+                                  aligned 2x2x2 block share one candidate
+                                  gather and sort); the lists are the same     */
 
 /* Region, lattice and table extent (Sec. II.B).  The box side on axis a is
  * L_a = cell_size * 2^log2_cells[a] (exact in float32).  A cyclic axis wraps
@@ -284,6 +288,20 @@ si_status si_kernel_timing_enable(int enable);
  * and write one line per kernel, "name launches total_ms\n", into buf (host,
  * cap bytes, always NUL-terminated).  Clears the records. */
 si_status si_kernel_timing_report(char *buf, size_t cap);
+
+/* Measured pair-test rate of the current device, for the arithmetic
+ * roofline of the radius kernels (not part of the paper's method).  A pair
+ * test is the FP32 filter of the canonical predicate: three coordinate
+ * differences, a square and two fused multiply-adds, and the sign of
+ * d^2 - t moved into a hit mask, with the candidates read from shared
+ * memory by broadcast, as in the cell kernels' test phase.  variant 0:
+ * scalar FP32 operations; 1: packed f32x2 operations (two pairs per
+ * instruction).  Launches its own kernel on a stream of its own (the whole
+ * GPU, about a millisecond, six launches), synchronises, and writes the best
+ * rate in pair tests per second to *pairs_per_second (host).  Allocates and
+ * frees a small device buffer; errors: SI_ERR_INVALID (null output, unknown
+ * variant), SI_ERR_CUDA. */
+si_status si_measure_pair_rate(uint32_t variant, double *pairs_per_second);
 
 const char *si_status_string(si_status s);
 const char *si_last_error(void);

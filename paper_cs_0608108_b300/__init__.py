@@ -66,6 +66,14 @@ def launch_count() -> int:
     return int(N.lib().si_launch_count())
 
 
+def measure_pair_rate(packed: bool = True) -> float:
+    """Measured pair tests per second of the current device (the arithmetic
+    roofline of the radius kernels): packed f32x2 or scalar FP32 form."""
+    out = ctypes.c_double(0.0)
+    N.check(N.lib().si_measure_pair_rate(1 if packed else 0, ctypes.byref(out)), "si_measure_pair_rate")
+    return out.value
+
+
 def make_desc(origin, cell_size, log2_cells, cyclic_mask, r_max) -> N.GridDesc:
     d = N.GridDesc()
     for a in range(3):
@@ -159,7 +167,7 @@ class Grid:
     # -- queries -------------------------------------------------------------
     def query_radius(self, r: float, include_self: bool = False, method: str = "sphere",
                      sort: bool = True, out_offsets=None, out_ids=None, sync_total: bool = True,
-                     walk: str = "classes", centers=None):
+                     walk: str = "classes", centers=None, groups: bool = True):
         """Radius query.  Returns (offsets int64[m+1], ids int32[total]).
         centers None: all agents (query k is point k, m = n); else a CUDA
         float32 (m, 4) tensor of query centers.  method "sphere" (spherical
@@ -167,13 +175,15 @@ class Grid:
         it is cheaper), "sphere_only" (never switching), "cube" (bin-lattice
         scan) or "list" (non-empty list: every object tested); walk "classes"
         (sub-cell class tables), "paper" (Sec. III.A 64 tables) or "planes"
-        (stacked z-planes, Sec. V)."""
+        (stacked z-planes, Sec. V); groups False serves every crowded cell
+        on its own (same lists)."""
         if method not in ("sphere", "sphere_only", "cube", "list"):
             raise ValueError(f"unknown method {method!r}")
         flags = (N.SI_INCLUDE_SELF if include_self else 0) | (0 if sort else N.SI_NO_SORT) | \
                 {"sphere": 0, "sphere_only": N.SI_SPHERE_ONLY, "cube": N.SI_METHOD_CUBE,
                  "list": N.SI_METHOD_LIST}[method] | \
-                (N.SI_WALK_PAPER if walk == "paper" else 0) | (N.SI_WALK_PLANES if walk == "planes" else 0)
+                (N.SI_WALK_PAPER if walk == "paper" else 0) | (N.SI_WALK_PLANES if walk == "planes" else 0) | \
+                (0 if groups else N.SI_NO_GROUPS)
         dev = self._pos.device
         m = self.n
         if centers is not None:

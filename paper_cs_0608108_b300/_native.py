@@ -12,7 +12,7 @@ SO_PATH = os.path.join(_PKG, "libsi.so")
 
 SI_OK, SI_ERR_INVALID, SI_ERR_OOM, SI_ERR_CUDA, SI_ERR_CAPACITY, SI_ERR_TIMEOUT, SI_ERR_INTERNAL = range(7)
 SI_METHOD_SPHERE, SI_METHOD_CUBE, SI_INCLUDE_SELF, SI_NO_SORT, SI_WALK_PAPER = 0, 1, 2, 4, 8
-SI_METHOD_LIST, SI_SPHERE_ONLY, SI_WALK_PLANES = 16, 32, 64
+SI_METHOD_LIST, SI_SPHERE_ONLY, SI_WALK_PLANES, SI_NO_GROUPS = 16, 32, 64, 128
 SI_KERNEL_POLY6_CUBED = 0
 
 c_float3 = ctypes.c_float * 3
@@ -58,6 +58,7 @@ SIGNATURES = {
     "si_batch_sync": (I32, [P, P, P]),
     "si_batch_destroy": (I32, [P]),
     "si_launch_count": (I64, []),
+    "si_measure_pair_rate": (I32, [U32, ctypes.POINTER(D)]),
     "si_kernel_timing_enable": (I32, [I32]),
     "si_kernel_timing_report": (I32, [ctypes.c_char_p, ctypes.c_size_t]),
     "si_status_string": (ctypes.c_char_p, [I32]),

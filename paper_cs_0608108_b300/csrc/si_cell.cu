@@ -34,39 +34,36 @@
 // record's offset) and one record per slab.  A cell that fits neither, or
 // whose records do not fit the scratch buffer, hands its queries to the
 // per-query path.
-#include <cmath>
-
-#include "si_host.h"
-#include "si_radius.cuh"
-#include "si_walk.cuh"
+#include "si_cell.cuh"
 
 namespace si {
 
-template <int THREADS, int CAP, int MAXQ, int BUCKETS, int MINB>
-struct CellCfg {
-  static constexpr int kThreads = THREADS;   // block size
-  static constexpr int kCap = CAP;           // staged candidates
-  static constexpr int kMaxQ = MAXQ;         // queries of the cell
-  static constexpr int kBuckets = BUCKETS;   // id buckets of the sort
-  static constexpr int kMinBlocks = MINB;    // resident blocks per SM
-  static constexpr int kBucketBits = BUCKETS == 1024 ? 10 : (BUCKETS == 512 ? 9 : 8);
-  static_assert((1 << kBucketBits) == BUCKETS, "bucket count must be 256, 512 or 1024");
-};
 using CellSmall = CellCfg<256, 1280, 128, 512, 4>;
 using CellLarge = CellCfg<kCellThreads, kCellCap, kCellMaxQ, 1024, 2>;
 
 template <class C>
 struct CellSmem {
-  float4 c[C::kCap];                       // candidate in the query frame; x = NaN: outside cell; w = spos slot
-  unsigned long long key[C::kCap];         // (input index << 32) | staging slot, in bucket order
-  int sid[C::kCap];                        // input index of each staged candidate
+  static constexpr int kChunks = (C::kCap + 31) / 32;
+  float4 c[C::kCap];                       // staged candidate in the query frame; x = NaN: outside cell; w = spos slot
+  union {
+    struct {                               // sort phase
+      unsigned long long key[C::kCap];     // (input index << 32) | staging slot, in bucket order
+      int sid[C::kCap];                    // input index of each staged candidate
+    } s;
+    struct {                               // test phase, candidates in id order
+      float4 xy[kChunks * kPairRow];       // (x_2p, x_2p+1, y_2p, y_2p+1)
+      float2 z[kChunks * kPairRow];        // (z_2p, z_2p+1)
+    } t;
+  } u;
+  unsigned outb[kChunks];                  // per chunk: candidates of the outside cell (FP64 for every pair)
+  unsigned short sslot[C::kCap];           // staging slot (in c) of each candidate in id order
   int bstart[C::kBuckets];                 // bucket counts, then starts
   int bcur[C::kBuckets];                   // bucket fill pointers
   struct {                                 // gather: runs of points of the cell-level sphere
     int tbeg[kCellTCap];
     int tcnt[kCellTCap];
     int tpre[kCellTCap + 1];
-    unsigned char tcode[kCellTCap];
+    int tsh[kCellTCap];                    // bytes 0-2: image shift per axis (-1, 0, +1 box sides); byte 3: outside cell
   } t;
   float4 qa[C::kMaxQ];                     // the cell's query points as FP32x2 pairs: (x, x, y, y)
   float4 qb[C::kMaxQ];                     // (z, z, own position among the candidates, -)
@@ -74,17 +71,11 @@ struct CellSmem {
   int scan[C::kThreads / 32];
   long long base;                          // the slab's record in the scratch buffer (-1: no room)
   long long hdr;                           // the split cell's header (-1: no room)
-  int nt, nc, out_seen, item;
+  int nt, nc, out_seen, item, qs, nq, cls;
+  unsigned key;
 };
 
 size_t cell_smem_bytes() { return sizeof(CellSmem<CellLarge>); }
-
-// Packed FP32 pairs (low half = first value) for f32x2 instructions.
-__device__ __forceinline__ unsigned long long pack2(float a, float b) {
-  return ((unsigned long long)__float_as_uint(b) << 32) | (unsigned long long)__float_as_uint(a);
-}
-__device__ __forceinline__ float lo_half(unsigned long long v) { return __uint_as_float((unsigned)v); }
-__device__ __forceinline__ float hi_half(unsigned long long v) { return __uint_as_float((unsigned)(v >> 32)); }
 
 // cells: [0] = count, then cell keys; next (nullable): where cells that do
 // not fit go (else they are split into slabs, or the per-query path takes
@@ -128,17 +119,51 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
     const unsigned long long b = atomicAdd(scr_top, (unsigned long long)need);
     return (b + (unsigned long long)need <= (unsigned long long)scr_cap) ? (long long)b : -1ll;
   };
+  // the next cell is fetched while this one is processed (thread 0): its
+  // item number at the start, its key after the gather, its bounds after
+  // the sort, so that no dependent global load waits at the loop head
+  int n_item = 0, n_qs = 0, n_qe = 0, n_cls = 0;
+  unsigned n_key = 0u;
+  bool keyed = false, bounded = false;   // this iteration's fetches done
+  auto fetch_key = [&]() {
+    if (keyed) return;
+    keyed = true;
+    if (tid == 0 && n_item < nheavy) n_key = (unsigned)cells[1 + n_item];
+  };
+  auto fetch_bounds = [&]() {
+    if (bounded) return;
+    fetch_key();
+    bounded = true;
+    if (tid == 0 && n_item < nheavy) {
+      n_qs = __ldg(g.cell_start + n_key);
+      n_qe = __ldg(g.cell_start + n_key + 1);
+      n_cls = g.cell_cls[n_key];
+    }
+  };
+  if (tid == 0) n_item = atomicAdd(work, 1);
+  fetch_key();
+  fetch_bounds();
   for (;;) {
-    if (tid == 0) S.item = atomicAdd(work, 1);
+    if (tid == 0) {
+      S.item = n_item;
+      S.key = n_key;
+      S.qs = n_qs;
+      S.nq = n_qe - n_qs;
+      S.cls = n_cls;
+      if (n_item < nheavy) n_item = atomicAdd(work, 1);
+    }
+    keyed = bounded = false;
     __syncthreads();
     const int item = S.item;
     if (item >= nheavy) return;
-    const unsigned key = (unsigned)cells[1 + item];
-    if (next && g.cell_cls[key] == kCellHeavyBig) {   // listed for the large configuration
-      __syncthreads();   // every thread has read S.item before it is rewritten
+    const unsigned key = S.key;
+    if (next && S.cls == kCellHeavyBig) {   // listed for the large configuration
+      fetch_key();
+      fetch_bounds();
+      __syncthreads();   // every thread has read S before it is rewritten
       continue;
     }
-    const int qs = g.cell_start[key], nq = g.cell_start[key + 1] - qs;
+    const int qs = S.qs, nq = S.nq;
     const int cx = (int)(key & ((1u << g.wx) - 1u));
     const int cy = (int)((key >> g.wx) & ((1u << g.wy) - 1u));
     const int cz = (int)(key >> (g.wx + g.wy));
@@ -150,13 +175,6 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
     }
     for (int b = tid; b < kBuckets; b += blockDim.x) S.bstart[b] = 0;
     const bool qfit = nq <= C::kMaxQ;
-    if (qfit)
-      for (int i = tid; i < nq; i += blockDim.x) {
-        const float4 q = g.spos[qs + i];
-        S.qa[i] = make_float4(q.x, q.x, q.y, q.y);
-        S.qb[i] = make_float4(q.z, q.z, __int_as_float(-1), 0.f);
-        S.qcnt[i] = 0;
-      }
     __syncthreads();
     int nt = 0, ntot = 0;
     if (qfit) {
@@ -170,7 +188,14 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
         const int t = atomicAdd(&S.nt, 1);
         S.t.tbeg[t] = b;
         S.t.tcnt[t] = c;
-        S.t.tcode[t] = (unsigned char)code;
+        // code: bits 2a, 2a + 1 = +L, -L on axis a; bit 6 = the outside cell
+        unsigned sh = (code & 64u) ? (1u << 24) : 0u;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const unsigned c2 = (code >> (2 * a)) & 3u;
+          sh |= (c2 == 1u ? 0x01u : (c2 == 2u ? 0xffu : 0u)) << (8 * a);
+        }
+        S.t.tsh[t] = (int)sh;
       };
       for (int e = tid; e < g.n_crow; e += blockDim.x) {
         const unsigned long long E = g.crow[e];
@@ -199,6 +224,13 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
           if (x0 <= x1) add_run(row + (unsigned)x0, row + (unsigned)x1, code);
         }
         if (out && !atomicExch(&S.out_seen, 1)) add_run(g.outside, g.outside, 64u);
+      }
+      // the cell's queries as FP32x2 pairs (their loads overlap the runs')
+      for (int i = tid; i < nq; i += blockDim.x) {
+        const float4 q = g.spos[qs + i];
+        S.qa[i] = make_float4(q.x, q.x, q.y, q.y);
+        S.qb[i] = make_float4(q.z, q.z, __int_as_float(-1), 0.f);
+        S.qcnt[i] = 0;
       }
       __syncthreads();
       nt = S.nt;
@@ -260,14 +292,15 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
         for (int u = 0; u < kGather; ++u) {
           bool keep = false;
           if (cj[u] >= 0 && pid[u] >= lo && pid[u] < hi) {
-            const unsigned code = S.t.tcode[tt[u]];
-            if (code & 64u) {
+            const int sh = S.t.tsh[tt[u]];
+            if (sh >> 24) {
               p[u].x = __int_as_float(0x7fc00000);   // outside cell: FP64 test for every pair
               keep = true;
             } else {
-              if (code & 3u) p[u].x += (code & 1u) ? g.Lx : -g.Lx;
-              if (code & 12u) p[u].y += (code & 4u) ? g.Ly : -g.Ly;
-              if (code & 48u) p[u].z += (code & 16u) ? g.Lz : -g.Lz;
+              // image shift: x + k L with k in {-1, 0, 1} (the product is exact)
+              p[u].x = fmaf((float)(signed char)(sh & 0xff), g.Lx, p[u].x);
+              p[u].y = fmaf((float)(signed char)((sh >> 8) & 0xff), g.Ly, p[u].y);
+              p[u].z = fmaf((float)(signed char)((sh >> 16) & 0xff), g.Lz, p[u].z);
               const float ux = (p[u].x - g.ox) * g.inv_s - (float)cx;
               const float uy = (p[u].y - g.oy) * g.inv_s - (float)cy;
               const float uz = (p[u].z - g.oz) * g.inv_s - (float)cz;
@@ -287,13 +320,14 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
               float4 cp = p[u];
               cp.w = __int_as_float(cj[u]);
               S.c[at] = cp;
-              S.sid[at] = pid[u] - lo;
+              S.u.s.sid[at] = pid[u] - lo;
               atomicAdd(&S.bstart[(pid[u] - lo) >> bshift], 1);
             }
           }
         }
       }
       __syncthreads();
+      fetch_key();
       const int nc = S.nc;
       if (nc > kCap) {
         if (!next && !split) {
@@ -357,105 +391,59 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
       }
       __syncthreads();
       for (int p = tid; p < nc; p += blockDim.x) {
-        const int id = S.sid[p];
-        S.key[atomicAdd(&S.bcur[id >> bshift], 1)] = ((unsigned long long)(unsigned)id << 32) | (unsigned)p;
+        const int id = S.u.s.sid[p];
+        S.u.s.key[atomicAdd(&S.bcur[id >> bshift], 1)] = ((unsigned long long)(unsigned)id << 32) | (unsigned)p;
       }
       __syncthreads();
       for (int b = tid; b < kBuckets; b += blockDim.x) {
         const int blo = S.bstart[b], bhi = S.bcur[b];
         for (int i = blo + 1; i < bhi; ++i) {
-          const unsigned long long x = S.key[i];
+          const unsigned long long x = S.u.s.key[i];
           int p = i;
-          while (p > blo && S.key[p - 1] > x) {
-            S.key[p] = S.key[p - 1];
+          while (p > blo && S.u.s.key[p - 1] > x) {
+            S.u.s.key[p] = S.u.s.key[p - 1];
             --p;
           }
-          S.key[p] = x;
+          S.u.s.key[p] = x;
         }
       }
+      fetch_bounds();
       __syncthreads();
-      // permute the candidates into id order; the ordered ids go to the record,
-      // each query notes its own position (if its index is in this slab)
+      // id order: the ordered ids go to the record and each sorted position
+      // notes its staging slot (the sort's keys are read here for the last
+      // time; the staged candidates in S.c stay where the gather put them)
       const long long rec = S.base;
       int *rec_ids = scratch + rec + 1;
       unsigned *rec_masks = reinterpret_cast<unsigned *>(rec_ids + nc);
       if (tid == 0) scratch[rec] = nc;
-      constexpr int kPer = (kCap + C::kThreads - 1) / C::kThreads;
-      float4 rc[kPer];
-#pragma unroll
-      for (int r = 0; r < kPer; ++r) {
-        const int k = tid + r * C::kThreads;
-        if (k < nc) {
-          const unsigned long long kk = S.key[k];
-          rc[r] = S.c[(int)(kk & 0xffffffffull)];
-          rec_ids[k] = (int)(kk >> 32) + lo;
-        }
+      for (int k = tid; k < nc; k += blockDim.x) {
+        const unsigned long long kk = S.u.s.key[k];
+        S.sslot[k] = (unsigned short)(kk & 0xffffu);
+        rec_ids[k] = (int)(kk >> 32) + lo;
       }
-      __syncthreads();
-      if (split) {   // own positions of this slab only
+      if (split)   // own positions of this slab only
         for (int i = tid; i < nq; i += blockDim.x) S.qb[i].z = __int_as_float(-1);
-        __syncthreads();
-      }
-#pragma unroll
-      for (int r = 0; r < kPer; ++r) {
-        const int k = tid + r * C::kThreads;
-        if (k < nc) {
-          S.c[k] = rc[r];
-          const int ql = __float_as_int(rc[r].w) - qs;
+      __syncthreads();
+      // the candidates in id order as the packed pairs of the test phase
+      // (over the sort's arrays, free now); chunk k >> 5 is one warp's row of
+      // this loop, so a ballot gives its outside-cell candidates; the padding
+      // up to whole chunks is +inf (never a hit, never in the band); each
+      // query notes its own position
+      for (int k = tid; k < nchunk * 32; k += blockDim.x) {
+        const bool in = k < nc;
+        const float4 v = in ? S.c[S.sslot[k]] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+        if (in) {
+          const int ql = __float_as_int(v.w) - qs;
           if (!incl_self && ql >= 0 && ql < nq) S.qb[ql].z = __int_as_float(k);
         }
+        const unsigned ob = __ballot_sync(0xffffffffu, in && isnan(v.x));
+        put_pair(S.u.t.xy, S.u.t.z, k, v);
+        if (lane == 0) S.outb[k >> 5] = ob;
       }
       __syncthreads();
-      // 4. tests.  Items (two chunks of 32 candidates, group of at most 16
-      //    queries) are spread over all warps; a lane holds candidates k and
-      //    k + 32 and runs both distances at once with packed FP32x2 arithmetic
-      //    (the same round-to-nearest operations, in the same order, as the
-      //    scalar path).  Pairs inside the guard band are decided in FP64.  A
-      //    query's own position is never a hit.  Lanes 2i and 2i + 1 keep the
-      //    two masks of the group's i-th query and store them together.
-      const int npair = (nchunk + 1) >> 1;
-      const int qsz = max(1, min(min(nq, 16), (nq * npair + 2 * nw - 1) / (2 * nw)));
-      const int ngrp = (nq + qsz - 1) / qsz;
-      const int nitems = npair * ngrp;
-      for (int it = wid; it < nitems; it += nw) {
-        const int grp = it / npair;
-        const int cp = it - grp * npair;
-        const int k0 = cp * 64 + lane, k1 = k0 + 32;
-        const float4 c0 = k0 < nc ? S.c[k0] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-        const float4 c1 = k1 < nc ? S.c[k1] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-        const unsigned long long X = pack2(c0.x, c1.x), Y = pack2(c0.y, c1.y), Z = pack2(c0.z, c1.z);
-        const int q0 = grp * qsz, q_end = min(nq, q0 + qsz);
-        unsigned mine = 0u;
-        for (int ql = q0; ql < q_end; ++ql) {
-          const float4 qa = S.qa[ql], qb = S.qb[ql];
-          unsigned long long dx, dy, dz, D2;
-          asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(X), "l"(pack2(qa.x, qa.y)));
-          asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(Y), "l"(pack2(qa.z, qa.w)));
-          asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(Z), "l"(pack2(qb.x, qb.y)));
-          asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(D2) : "l"(dx), "l"(dx));
-          asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D2) : "l"(dy), "l"(dy), "l"(D2));
-          asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D2) : "l"(dz), "l"(dz), "l"(D2));
-          const float d0 = lo_half(D2), d1 = hi_half(D2);
-          bool h0 = d0 <= B.lo_w, h1 = d1 <= B.lo_w;
-          const bool u0 = !h0 && !(d0 > B.hi_w), u1 = !h1 && !(d1 > B.hi_w);
-          if (__any_sync(0xffffffffu, u0 || u1)) {
-            const float4 q = make_float4(qa.x, qa.z, qb.x, 0.f);
-            if (u0 && k0 < nc) h0 = canon_d2(q, g.spos[__float_as_int(c0.w)], g) <= B.r2;
-            if (u1 && k1 < nc) h1 = canon_d2(q, g.spos[__float_as_int(c1.w)], g) <= B.r2;
-          }
-          const int own = __float_as_int(qb.z);
-          const unsigned m0 = __ballot_sync(0xffffffffu, h0 && k0 != own);
-          const unsigned m1 = __ballot_sync(0xffffffffu, h1 && k1 != own);
-          const int slot = 2 * (ql - q0);
-          if (lane == slot) mine = m0;
-          if (lane == slot + 1) mine = m1;
-        }
-        const int qi = q0 + (lane >> 1), ch = 2 * cp + (lane & 1);
-        if (qi < q_end && ch < nchunk) rec_masks[qi * nchunk + ch] = mine;
-        int c = __popc(mine);
-        c += __shfl_xor_sync(0xffffffffu, c, 1);
-        if ((lane & 1) == 0 && qi < q_end && c) atomicAdd(&S.qcnt[qi], c);
-      }
+      // 4. tests: one hit mask per (query, chunk of 32 candidates)
+      cell_test_phase(g, B, nq, nchunk, S.u.t.xy, S.u.t.z, S.outb, S.c, S.sslot, S.qa, S.qb, S.qcnt, rec_masks,
+                      lane, wid, nw);
       __syncthreads();
       if (++sl < nslab) {   // the next slab starts from empty buckets
         if (tid == 0) S.nc = 0;
@@ -463,6 +451,7 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
         __syncthreads();
       }
     }
+    fetch_bounds();
     if (!ok) {
       if (next && room) {
         // the larger configuration takes this cell
@@ -613,10 +602,114 @@ si_status launch_cell_pass(const GridDev &g, const WalkParams &P, const Band &B,
                                     cell_rec, scratch, scr_cap, scr_top, st);
 }
 
+// The expansion of most cells runs a warp per item of at most kItemQ
+// queries of one cell, with no block-wide barrier, so that the latency of
+// each item's loads (its record, its queries' output positions) is hidden
+// by the other warps of the SM.  k_expand_plan lists the items: a cell
+// served by one record of at most kItemCap candidates gives ceil(nq / kItemQ)
+// of them; split cells and longer records go to k_cell_expand (a block per
+// cell).  A warp stages its item's ordered ids in its own shared rows (32
+// ids per row, rows padded to 33 words) and expands each query's masks as
+// k_cell_expand does.
+constexpr int kItemQ = 8;
+constexpr int kItemCap = 1280;
+constexpr int kItemWarps = 8;
+constexpr int kItemRows = kItemCap / 32;
+
+__global__ void __launch_bounds__(256) k_expand_plan(GridDev g, const int *__restrict__ heavy,
+                                                     const long long *__restrict__ cell_rec,
+                                                     const int *__restrict__ scratch, int4 *items, int *blocks) {
+  const int n = heavy[0];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned key = (unsigned)heavy[1 + i];
+    const long long ref = cell_rec[key];
+    if (ref == -1) continue;   // served by the per-query path
+    const int qs = __ldg(g.cell_start + key), nq = __ldg(g.cell_start + key + 1) - qs;
+    if (ref < -1 || __ldg(scratch + ref) > kItemCap) {
+      blocks[1 + atomicAdd(blocks, 1)] = (int)key;
+      continue;
+    }
+    const int nit = (nq + kItemQ - 1) / kItemQ;
+    const int at = atomicAdd(reinterpret_cast<int *>(items), nit);
+    for (int t = 0; t < nit; ++t) {
+      const int q0 = t * kItemQ;
+      items[1 + at + t] = make_int4((int)(ref & 0xffffffffll), (int)(ref >> 32), qs, q0 | (min(kItemQ, nq - q0) << 16));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kItemWarps * 32) k_expand_items(GridDev g, const int4 *__restrict__ items,
+                                                                 const int *__restrict__ scratch,
+                                                                 const long long *__restrict__ offsets,
+                                                                 int *__restrict__ ids, long long cap) {
+  extern __shared__ int item_smem[];   // per warp: kItemRows * 33 id slots, then a 1024-id buffer
+  if (offsets[g.n] > cap) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(g.status, ST_CAPACITY);
+    return;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int *rows = item_smem + wid * (kItemRows * 33 + 1024), *buf = rows + kItemRows * 33;
+  const int nitems = items[0].x;
+  for (int it = blockIdx.x * kItemWarps + wid; it < nitems; it += gridDim.x * kItemWarps) {
+    const int4 d = items[1 + it];
+    const long long rec = (long long)(unsigned)d.x | ((long long)d.y << 32);
+    const int qs = d.z, q0 = d.w & 0xffff, cnt = d.w >> 16;
+    const int nc = __ldg(scratch + rec);
+    const int nchunk = (nc + 31) >> 5;
+    const int *rec_ids = scratch + rec + 1;
+    const unsigned *rec_masks = reinterpret_cast<const unsigned *>(rec_ids + nc);
+    // output positions of the item's queries (lane t: query q0 + t)
+    const long long wp = lane < cnt ? offsets[__ldg(g.perm + qs + q0 + lane)] : 0ll;
+    unsigned mnext = lane < nchunk ? __ldg(rec_masks + (long long)q0 * nchunk + lane) : 0u;
+    __syncwarp();   // the previous item's rows are no longer read
+    for (int k = lane; k < nc; k += 32) rows[(k >> 5) * 33 + (k & 31)] = __ldg(rec_ids + k);
+    __syncwarp();
+    for (int t = 0; t < cnt; ++t) {
+      const int ql = q0 + t;
+      long long wpos = __shfl_sync(0xffffffffu, wp, t);
+      const unsigned *mk = rec_masks + (long long)ql * nchunk;
+      for (int c0 = 0; c0 < nchunk; c0 += 32) {
+        const unsigned mm = mnext;
+        // prefetch: the rest of this query's masks, else the next query's first 32
+        if (c0 + 32 < nchunk) {
+          const int ch = c0 + 32 + lane;
+          mnext = ch < nchunk ? __ldg(mk + ch) : 0u;
+        } else if (t + 1 < cnt) {
+          mnext = lane < nchunk ? __ldg(mk + nchunk + lane) : 0u;
+        }
+        const int c = __popc(mm);
+        const int inc = warp_incl_scan_i(c);
+        int o = inc - c;
+        const int *row = rows + (c0 + lane) * 33;   // read only where a bit is set
+#pragma unroll
+        for (int b = 0; b < 32; ++b) {
+          const bool set = (mm >> b) & 1u;
+          if (set) buf[o] = row[b];
+          o += set ? 1 : 0;
+        }
+        __syncwarp();
+        const int tot = __shfl_sync(0xffffffffu, inc, 31);
+        for (int i = lane; i < tot; i += 32) ids[wpos + i] = buf[i];
+        __syncwarp();
+        wpos += tot;
+      }
+    }
+  }
+}
+
 si_status launch_cell_expand(const GridDev &g, const int *heavy, const long long *cell_rec, const int *scratch,
-                             const long long *offsets, int *ids, long long cap, cudaStream_t st) {
+                             int4 *items, int *blocks, const long long *offsets, int *ids, long long cap,
+                             cudaStream_t st) {
+  SI_CUDA_TRY(cudaMemsetAsync(items, 0, sizeof(int4), st));
+  SI_CUDA_TRY(cudaMemsetAsync(blocks, 0, sizeof(int), st));
+  SI_KLAUNCH("k_expand_plan", st,
+             k_expand_plan<<<148 * 4, 256, 0, st>>>(g, heavy, cell_rec, scratch, items, blocks));
+  const size_t ism = (size_t)kItemWarps * (kItemRows * 33 + 1024) * sizeof(int);
+  SI_CUDA_TRY(cudaFuncSetAttribute(k_expand_items, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+  SI_KLAUNCH("k_expand_items", st,
+             k_expand_items<<<148 * 3, kItemWarps * 32, ism, st>>>(g, items, scratch, offsets, ids, cap));
   SI_KLAUNCH("k_cell_expand", st,
-             k_cell_expand<<<148 * 8, kExpWarps * 32, 0, st>>>(g, heavy, cell_rec, scratch, offsets, ids, cap));
+             k_cell_expand<<<148 * 8, kExpWarps * 32, 0, st>>>(g, blocks, cell_rec, scratch, offsets, ids, cap));
   return SI_OK;
 }
 

@@ -104,6 +104,53 @@ void build_class_tables(const Lattice &lat, double dg, int q, std::vector<unsign
   begin[(size_t)q * q * q] = (int)ent.size();
 }
 
+// x-row runs of the cells within d of a box of B x B x B cells (offsets
+// relative to the box's lowest cell, box [0, B)^3 grown by the binning
+// margin), in the same entry format; B = 1 gives the cell-level rows.
+void build_box_rows(const Lattice &lat, double dg, int B, std::vector<unsigned long long> &ent) {
+  const int W = lat.W;
+  const int pos[3] = {0, W + lat.w[0], lat.w[0] + lat.w[1]};
+  const int reach = (int)std::floor(dg) + 1;
+  const double m = lat.eps;
+  struct Run {
+    int b2, oy, oz, lo, len;
+  };
+  std::vector<Run> runs;
+  for (int oz = -reach; oz <= B - 1 + reach; ++oz)
+    for (int oy = -reach; oy <= B - 1 + reach; ++oy) {
+      Run r{1 << 30, oy, oz, 0, 0};
+      for (int ox = -reach; ox <= B - 1 + reach; ++ox) {
+        const int o[3] = {ox, oy, oz};
+        double g2 = 0.0;
+        int b2 = 0;
+        for (int a = 0; a < 3; ++a) {
+          const double gap = std::max(std::max((double)o[a] - ((double)B + m), -m - (double)(o[a] + 1)), 0.0);
+          g2 += gap * gap;
+          const int bb = std::max(std::max(o[a] - B, -o[a] - 1), 0);
+          b2 += bb * bb;
+        }
+        if (g2 > dg * dg) continue;
+        if (r.len == 0) r.lo = ox;
+        r.len = ox - r.lo + 1;   // convex region: the kept ox are contiguous
+        r.b2 = std::min(r.b2, b2);
+      }
+      if (r.len > 0) runs.push_back(r);
+    }
+  std::stable_sort(runs.begin(), runs.end(), [](const Run &x, const Run &y) { return x.b2 < y.b2; });
+  ent.clear();
+  for (const Run &r : runs) {
+    unsigned long long u = 0;
+    const int o[3] = {0, r.oy, r.oz};
+    for (int a = 1; a < 3; ++a) {
+      const unsigned long long fieldmask = (1ull << (lat.w[a] + 1)) - 1ull;
+      u |= ((unsigned long long)(long long)o[a] & fieldmask) << pos[a];
+    }
+    u |= (unsigned long long)(unsigned char)(signed char)r.lo << 48;
+    u |= (unsigned long long)(r.len & 127) << 56;
+    ent.push_back(u);
+  }
+}
+
 }  // namespace si
 
 using namespace si;
@@ -122,6 +169,26 @@ bool si_grid::ensure_cell_rows(float dg, cudaStream_t st) {
   if (cudaStreamSynchronize(st) != cudaSuccess) return false;
   n_crow = (int)crow_host.size();
   crow_dg = dg;
+  return true;
+}
+
+// Rows of the 2 x 2 x 2 cell groups of the heavy-cell kernel (si_group.cu);
+// false when the lattice is too small for a group's rows to stay distinct
+// (then every heavy cell is served on its own).
+bool si_grid::ensure_group_rows(float dg, cudaStream_t st) {
+  if (grow_dg == dg) return n_grow > 0;
+  grow_dg = dg;
+  n_grow = 0;
+  const int reach = (int)std::floor((double)dg) + 1;
+  for (int a = 0; a < 3; ++a)
+    if (lat.w[a] < 1 || (1 << lat.w[a]) < 2 * reach + 2) return false;
+  build_box_rows(lat, (double)dg, 2, grow_host);
+  if ((int64_t)grow_host.size() > grow_cap || 2 * (int64_t)grow_host.size() + 1 > kGroupTCap) return false;
+  if (cudaMemcpyAsync(grow, grow_host.data(), grow_host.size() * sizeof(unsigned long long),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return false;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return false;
+  n_grow = (int)grow_host.size();
   return true;
 }
 

@@ -648,6 +648,11 @@ static void grid_free(si_grid *g) {
   cudaFree(g->heavy);
   cudaFree(g->heavy_big);
   cudaFree(g->heavy_big_built);
+  cudaFree(g->groups);
+  cudaFree(g->hsolo);
+  cudaFree(g->xblock);
+  cudaFree(g->xitems);
+  cudaFree(g->grow);
   cudaFree(g->over);
   cudaFree(g->denseq);
   cudaFree(g->lightq);
@@ -723,6 +728,11 @@ extern "C" si_status si_grid_create(const si_grid_desc *desc, int64_t n_capacity
   SI_ALLOC(g->heavy, (cap1 / kHeavyMinDense + 2) * sizeof(int));
   SI_ALLOC(g->heavy_big, (cap1 / kHeavyMinDense + 2) * sizeof(int));
   SI_ALLOC(g->heavy_big_built, sizeof(int));
+  SI_ALLOC(g->groups, (cap1 / kHeavyMinDense + 2) * sizeof(int));
+  SI_ALLOC(g->hsolo, (cap1 / kHeavyMinDense + 2) * sizeof(int));
+  SI_ALLOC(g->xblock, (cap1 / kHeavyMinDense + 2) * sizeof(int));
+  // items of at most 8 queries of one heavy cell (a heavy cell holds >= 3 points)
+  SI_ALLOC(g->xitems, (cap1 / 8 + cap1 / kHeavyMinDense + 2) * sizeof(int4));
   SI_ALLOC(g->over, (cap1 + 1) * sizeof(int));
   SI_ALLOC(g->denseq, (cap1 + 1) * sizeof(int));
   SI_ALLOC(g->lightq, (cap1 + 1) * sizeof(int));
@@ -759,6 +769,8 @@ extern "C" si_status si_grid_create(const si_grid_desc *desc, int64_t n_capacity
     const int reach = (int)std::floor(std::sqrt((double)g->lat.n_max + 1.0)) + 2;
     g->crow_cap = (int64_t)(2 * reach + 1) * (2 * reach + 1);
     e = cudaMalloc((void **)&g->crow, g->crow_cap * sizeof(unsigned long long));
+    g->grow_cap = (int64_t)(2 * reach + 2) * (2 * reach + 2);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&g->grow, g->grow_cap * sizeof(unsigned long long));
     if (e != cudaSuccess) {
       grid_free(g);
       return cuda_fail(e, "cudaMalloc (cell rows)");

@@ -119,6 +119,8 @@ int class_q_for(double dmax);
 int64_t class_capacity(const Lattice &lat, int64_t table_entries);
 void build_class_tables(const Lattice &lat, double dg, int q, std::vector<unsigned long long> &ent,
                         std::vector<int> &begin);
+void build_box_rows(const Lattice &lat, double dg, int B, std::vector<unsigned long long> &ent);
+constexpr int kGroupTCap = 128;   // runs of a cell group's rows (two per row at most, and the outside cell)
 
 // Outputs a query-center call gives a center it cannot query (a non-finite
 // coordinate, or one outside its box on a cyclic axis): an empty result.
@@ -187,6 +189,16 @@ struct si_grid {
   float crow_dg = -1.f;
   std::vector<unsigned long long> crow_host;
   bool ensure_cell_rows(float dg, cudaStream_t st);
+  unsigned long long *grow = nullptr;   // x-row runs of the cells within d of a 2 x 2 x 2 cell group
+  int64_t grow_cap = 0;
+  int n_grow = 0;
+  float grow_dg = -1.f;
+  std::vector<unsigned long long> grow_host;
+  bool ensure_group_rows(float dg, cudaStream_t st);
+  int *groups = nullptr;         // [0] = count, then the lowest cell key of each group of >= 2 heavy cells
+  int *hsolo = nullptr;          // [0] = count, then heavy cells served one at a time
+  int4 *xitems = nullptr;        // expansion items ([0].x = count): record, first slot, queries of one cell
+  int *xblock = nullptr;         // [0] = count, then heavy cells expanded a block per cell
   double *partial = nullptr;     // reduce partial sums
   int64_t partial_len = 0;
   long long *h_pinned = nullptr; // pinned host scratch (2 values)

@@ -789,7 +789,7 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   if (!d_offsets) return fail(SI_ERR_INVALID, "null offsets");
   if (ids_capacity < 0 || (ids_capacity > 0 && !d_ids)) return fail(SI_ERR_INVALID, "bad ids buffer");
   if (flags & ~(SI_METHOD_CUBE | SI_INCLUDE_SELF | SI_NO_SORT | SI_WALK_PAPER | SI_METHOD_LIST | SI_SPHERE_ONLY |
-                SI_WALK_PLANES))
+                SI_WALK_PLANES | SI_NO_GROUPS))
     return fail(SI_ERR_INVALID, "unknown flags");
   if ((flags & SI_METHOD_CUBE) && (flags & SI_METHOD_LIST))
     return fail(SI_ERR_INVALID, "SI_METHOD_CUBE and SI_METHOD_LIST are exclusive");
@@ -818,6 +818,9 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   // cells with b^2 <= floor(d^2), at most two runs per row and the outside cell);
   // the stacked-plane walk serves every query itself
   const bool heavy = !cube && !planes && g->ensure_cell_rows(P.dg, st) && 2 * g->n_crow + 1 <= kCellTCap;
+  // groups of heavy cells when the lattice holds a group's rows without
+  // wrapping onto itself (SI_NO_GROUPS serves every heavy cell on its own)
+  const bool group = heavy && !(flags & SI_NO_GROUPS) && g->ensure_group_rows(P.dg, st);
   // the count pass keeps short lists for the write pass in a staging area
   // (allocated on first use; without it the write pass walks every list again)
   if (walk == kWalkClasses && g->cls_smem_bytes > 0 && !g->lstage && g->cap > 0) {
@@ -852,7 +855,19 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
             SI_OK)
       return r;
     if (heavy) {
-      if ((r = launch_cell_pass(dv, P, B, flags, g->heavy, g->heavy_big, g->counters, g->over, off + 1, g->cell_rec,
+      // groups of neighbouring heavy cells first (they share one gather and
+      // sort), then the heavy cells served one at a time
+      const int *solo = g->heavy;
+      if (group) {
+        SI_CUDA_TRY(cudaMemsetAsync(g->groups, 0, sizeof(int), st));
+        SI_CUDA_TRY(cudaMemsetAsync(g->hsolo, 0, sizeof(int), st));
+        if ((r = launch_cell_group(dv, P, B, flags, g->heavy, g->groups, g->hsolo, g->counters + 2, g->heavy_big,
+                                   g->over, off + 1, g->cell_rec, g->scratch, g->scr_cap, g->scr_top, g->grow,
+                                   g->n_grow, st)) != SI_OK)
+          return r;
+        solo = g->hsolo;
+      }
+      if ((r = launch_cell_pass(dv, P, B, flags, solo, g->heavy_big, g->counters, g->over, off + 1, g->cell_rec,
                                 g->scratch, g->scr_cap, g->scr_top, st)) != SI_OK)
         return r;
       SI_KLAUNCH("k_radius_over_count", st,
@@ -893,7 +908,8 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
                               g->longq, blocks, light_list, g->lstage, (long long)g->cap, st)) != SI_OK)
     return s;
   if (heavy) {
-    if ((s = launch_cell_expand(dv, g->heavy, g->cell_rec, g->scratch, off, d_ids, ids_capacity, st)) != SI_OK)
+    if ((s = launch_cell_expand(dv, g->heavy, g->cell_rec, g->scratch, g->xitems, g->xblock, off, d_ids, ids_capacity,
+                                st)) != SI_OK)
       return s;
     SI_KLAUNCH("k_radius_over_write", st,
                k_radius_over<true><<<148 * 4, kQueryThreads, 0, st>>>(dv, P, B, flags, g->over, nullptr,

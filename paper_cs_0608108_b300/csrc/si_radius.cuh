@@ -24,8 +24,17 @@ si_status launch_cell_pass(const GridDev &g, const WalkParams &P, const Band &B,
                            const int *heavy, int *big, int *work, int *over, long long *counts,
                            long long *cell_rec, int *scratch, long long scr_cap, unsigned long long *scr_top,
                            cudaStream_t st);
+// Groups of heavy cells (si_group.cu): splits the heavy list into 2 x 2 x 2
+// groups and the cells served one at a time (solo), and serves the groups.
+size_t group_smem_bytes();
+si_status launch_cell_group(const GridDev &g, const WalkParams &P, const Band &B, unsigned flags,
+                            const int *heavy, int *groups, int *solo, int *work, int *big, int *over,
+                            long long *counts, long long *cell_rec, int *scratch, long long scr_cap,
+                            unsigned long long *scr_top, const unsigned long long *grow, int n_grow,
+                            cudaStream_t st);
 si_status launch_cell_expand(const GridDev &g, const int *heavy, const long long *cell_rec, const int *scratch,
-                             const long long *offsets, int *ids, long long cap, cudaStream_t st);
+                             int4 *items, int *blocks, const long long *offsets, int *ids, long long cap,
+                             cudaStream_t st);
 
 // Non-empty list method (si_list.cu): every (query, point) pair tested.
 si_status launch_list(const GridDev &dv, const Band &B, unsigned flags, const int *list, int64_t m,

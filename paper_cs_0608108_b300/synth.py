@@ -187,6 +187,15 @@ def mixture_1m_scene(n: int = 1_000_000, seed: int = SEEDS["mixture_1m"]) -> Sce
                  1.5 / 128, "mixture_1m")
 
 
+def mixture_250k_scene(n: int = 250_000, seed: int = SEEDS["mixture_1m"]) -> Scene:
+    """A quarter of the 1M mixture's components at the same density: 250k
+    points, 16 components (sigma 0.02), cyclic, 128^3.  Each component holds
+    as many points as one of the 1M mixture's, so the cells are as crowded;
+    the smaller case serves profiling."""
+    return Scene(gaussian_mixture_points(n, seed, n_comp=16), (0.0, 0.0, 0.0), 1.0 / 128, (7, 7, 7), 7,
+                 1.5 / 128, "mixture_250k")
+
+
 def knn_4m_scene(n: int = 4_000_000, seed: int = SEEDS["knn_4m"]) -> Scene:
     """N=4M uniform, cyclic in x and y, non-cyclic in z, 256^3 lattice, r_max = 4 cells."""
     return Scene(uniform_points(n, seed), (0.0, 0.0, 0.0), 1.0 / 256, (8, 8, 8), 3,
