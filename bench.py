@@ -152,11 +152,24 @@ def cell_classes(start, log2_cells):
     return cls
 
 
-# ALU roofline of the pair tests: FP32 lanes x 2 (packed FP32x2 arithmetic) per SM
-# and clock, over the 6 arithmetic operations of one test (3 differences, one
-# square, two fused multiply-adds); the comparison runs on another pipe.
-SMS, FP32_LANES, SM_GHZ, OPS_PER_PAIR = 148, 128, 2.032, 6
-PAIR_PEAK = SMS * FP32_LANES * 2 * SM_GHZ * 1e9 / OPS_PER_PAIR
+def grouped_cells(cls, start, log2_cells, d):
+    """Heavy cells of the small class served by the 2x2x2 group kernel: the
+    non-empty ones of at most 128 queries whose aligned group holds another
+    non-empty heavy cell of that class (the library's k_group_list rule;
+    groups whose candidates overflow a block at run time are not predicted),
+    on lattices with at least 2 reach + 2 cells per axis."""
+    cnt = np.diff(start).astype(np.int64)
+    G = [1 << w for w in log2_cells]
+    reach = int(np.floor(d)) + 1
+    out = np.zeros(len(cls), dtype=bool)
+    if min(log2_cells) < 1 or min(G) < 2 * reach + 2:
+        return out
+    nc = len(cnt) - 1
+    hs = ((cls[:nc] == 1) & (cnt[:nc] > 0)).reshape(G[2], G[1], G[0])
+    blk = hs.reshape(G[2] // 2, 2, G[1] // 2, 2, G[0] // 2, 2).sum(axis=(1, 3, 5))
+    per = np.repeat(np.repeat(np.repeat(blk, 2, 0), 2, 1), 2, 2)
+    out[:nc] = (hs & (per >= 2)).ravel() & (cnt[:nc] <= 128)
+    return out
 
 
 def candidate_pairs(scene, start, cls, sample=131_072):
@@ -167,7 +180,7 @@ def candidate_pairs(scene, start, cls, sample=131_072):
     pos = scene.pos
     n = len(pos)
     if n == 0:
-        return {c: 0.0 for c in range(4)}
+        return {c: 0.0 for c in range(5)}
     step = max(1, n // sample)
     q = pos[::step, :3].astype(np.float64)
     w = np.array(scene.log2_cells)
@@ -195,7 +208,7 @@ def candidate_pairs(scene, start, cls, sample=131_072):
                 t = np.clip(t, 0, G - 1)
                 key = (t[:, 2] << (w[0] + w[1])) | (t[:, 1] << w[0]) | t[:, 0]
                 tot += np.where(ok, cnt[key], 0)
-    return {k: float(tot[qcls == k].sum()) * step for k in range(4)}
+    return {k: float(tot[qcls == k].sum()) * step for k in range(5)}
 
 
 class RadiusWork:
@@ -236,21 +249,30 @@ class RadiusWork:
         large heavy (>= 768 points in the 27 cells around it), dense (not
         heavy, >= 24 points around it), light (the rest).  Cells that overflow
         the small configuration at run time are counted as small."""
-        s = self.scenes[k]
         start, _, perm = (t.cpu().numpy() for t in self.grids[k].cell_arrays())
         cnt = np.diff(start).astype(np.int64)
-        cls = cell_classes(start, s.log2_cells)
-        if self.method == "cube":
-            cls[:] = 0
+        cls = self.classes(k, start)
         slot_cls = np.repeat(cls, cnt.clip(min=0))[: len(perm)]
         off = self.off[k].cpu().numpy()
         lens = np.diff(off)
         tot = max(lens.sum(), 1)
         out = {}
-        for name, c in (("light", 0), ("small", 1), ("dense", 2), ("large", 3)):
+        for name, c in (("light", 0), ("small", 1), ("dense", 2), ("large", 3), ("group", 4)):
             sel = slot_cls == c
             out[name] = (sel.mean() if len(perm) else 0.0, lens[perm[sel]].sum() / tot)
         return out
+
+    def classes(self, k, start):
+        """Cell classes of scene k as the binning assigns them, with the heavy
+        cells served by the group kernel relabelled 4."""
+        s = self.scenes[k]
+        cls = cell_classes(start, s.log2_cells)
+        if self.method == "cube":
+            cls[:] = 0
+            return cls
+        cls = cls.copy()
+        cls[grouped_cells(cls, start, s.log2_cells, s.r / s.cell_size)] = 4
+        return cls
 
     def algorithmic_bytes(self):
         """Per-kernel minimum DRAM bytes of one launch, averaged over the scenes:
@@ -259,8 +281,8 @@ class RadiusWork:
         for k, (s, tot) in enumerate(zip(self.scenes, self.totals)):
             n, C = s.n, (1 << sum(s.log2_cells)) + 1
             f = self.cell_split(k)
-            fl, fd, fs, fb = (f[c][0] for c in ("light", "dense", "small", "large"))
-            tl, td, ts, tb = (f[c][1] for c in ("light", "dense", "small", "large"))
+            fl, fd, fs, fb, fg = (f[c][0] for c in ("light", "dense", "small", "large", "group"))
+            tl, td, ts, tb, tg = (f[c][1] for c in ("light", "dense", "small", "large", "group"))
             # per-query kernels: the query's point, index and list entry, the
             # cell starts, the count (count pass) or offset (write pass)
             q_b = 16 * n + 4 * n + 4 * n + 8 * n
@@ -275,9 +297,13 @@ class RadiusWork:
                 "k_radius_dense_count": fd * q_b + fd * 4 * C,
                 "k_radius_dense_write": fd * q_b + fd * 4 * C + td * 4 * tot,
                 "k_cell": fs * c_b + fs * 4 * C,
+                "k_cell_group": fg * c_b + fg * 4 * C,
                 "k_cell_large": fb * c_b + fb * 4 * C,
-                # the lists of every heavy query, with their offsets and indices
-                "k_cell_expand": (fs + fb) * (4 * n + 8 * n) + (ts + tb) * 4 * tot,
+                # the lists of the heavy queries, with their offsets and
+                # indices: the warp-per-item expansion serves the small and
+                # grouped cells, the block-per-cell one the large cells
+                "k_expand_items": (fs + fg) * (4 * n + 8 * n) + (ts + tg) * 4 * tot,
+                "k_cell_expand": fb * (4 * n + 8 * n) + tb * 4 * tot,
                 "k_radius_count_cube": 16 * n + 4 * n + 4 * C + 8 * n,
                 "k_radius_write_cube": 16 * n + 4 * n + 4 * C + 8 * n + 4 * tot,
                 "k_radius_count_planes": 16 * n + 4 * n + 4 * C + 8 * n,
@@ -302,11 +328,12 @@ class RadiusWork:
         out = {}
         for k, s in enumerate(self.scenes):
             start, _, _ = (t.cpu().numpy() for t in self.grids[k].cell_arrays())
-            p = candidate_pairs(s, start, cell_classes(start, s.log2_cells))
+            p = candidate_pairs(s, start, self.classes(k, start))
             out.setdefault("k_radius_count_planes", []).append(sum(p.values()))
             out.setdefault("k_radius_write_planes", []).append(sum(p.values()))
             for name, c in (("k_radius_count", 0), ("k_radius_write", 0), ("k_radius_dense_count", 2),
-                            ("k_radius_dense_write", 2), ("k_cell", 1), ("k_cell_large", 3)):
+                            ("k_radius_dense_write", 2), ("k_cell", 1), ("k_cell_large", 3),
+                            ("k_cell_group", 4)):
                 out.setdefault(name, []).append(p[c])
         return {kk: float(np.mean(v)) for kk, v in out.items()}
 
@@ -672,6 +699,48 @@ def job_value(queries_per_rank: int, world: int, ms_step: float) -> float:
     return queries_per_rank * world / (ms_step * 1e-3)
 
 
+def same_run_comparisons(steps, warmup, flush, local):
+    """The comparisons the metric names, measured in the same run as the
+    default line: the GPU bin-lattice cube scan on the same two 1M scenes,
+    and the 256 uneven scenes served by the library's batched graph against
+    the plain single-scene path looped over them (their lists checked equal,
+    scene by scene).  Device times with CUDA events, L2 flushed per step."""
+    import torch
+    from paper_cs_0608108_b300 import synth
+    out = {}
+    with ClockSampler(local) as clk:
+        cube = RadiusWork([synth.uniform_1m_scene(), synth.mixture_1m_scene()], "cube")
+        for _ in range(2):
+            cube.step()
+        cube.check()
+        g, _ = capture_step(cube)
+        ms = time_steps(cube, steps, warmup, flush, g)
+        out["radius_1m_cube"] = {"ms_per_step": float(np.mean(ms)), "queries_per_s": cube.queries / (np.mean(ms) * 1e-3),
+                                 "description": "same scenes, GPU bin-lattice cube scan (bounding cube of the sphere)"}
+        del g, cube
+        torch.cuda.empty_cache()
+        scenes = synth.batched_scenes()
+        bw = BatchWork(scenes)
+        ms_b = time_steps(bw, steps, warmup, flush)
+        bw.check()
+        lw = LoopWork(scenes)
+        ms_l = time_steps(lw, steps, warmup, flush)
+        lw.check()
+        same = all(torch.equal(a, b) for a, b in zip(bw.offs, lw.off)) and \
+            all(torch.equal(a[:t], b[:t]) for a, b, t in zip(bw.ids, lw.ids, bw.totals))
+        out["batched"] = {"ms_per_step": float(np.mean(ms_b)), "queries_per_s": bw.queries / (np.mean(ms_b) * 1e-3),
+                          "scenes": len(scenes), "points": bw.queries,
+                          "description": "256 uneven scenes, one graph replay (fused short-list scenes, "
+                                         "concurrent branches for long-list scenes)"}
+        out["batched_loop"] = {"ms_per_step": float(np.mean(ms_l)), "queries_per_s": lw.queries / (np.mean(ms_l) * 1e-3),
+                               "description": "the plain single-scene path called scene after scene"}
+        out["batched_equals_loop"] = bool(same)
+        del bw, lw
+        torch.cuda.empty_cache()
+    out["clocks"] = clk.summary()
+    return out
+
+
 def capture_step(work):
     """The step captured once in a CUDA graph (every call of the step is
     asynchronous once its tables and buffers are sized); returns the graph
@@ -815,6 +884,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="call the step eagerly instead of replaying its graph")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the same-run cube-scan and batched-vs-loop comparisons of the default workload")
     args = ap.parse_args()
     rank, world, local = dist_setup()
     if args.warmup < 3:
@@ -896,6 +967,8 @@ def main():
     lib.si_kernel_timing_enable(0)
     alg = work.algorithmic_bytes()
     peak, peak_kind = peaks()
+    from paper_cs_0608108_b300 import measure_pair_rate
+    pair_peak = measure_pair_rate(True)
     dom = max(rows.items(), key=lambda kv: kv[1][1])[0] if rows else None
     roof = None
     if dom is not None:
@@ -905,23 +978,26 @@ def main():
         achieved = (a_bytes / (avg_ms * 1e-3) / 1e9) if a_bytes else None
         share = {k: round(v[1] / sum(x[1] for x in rows.values()), 4)
                  for k, v in sorted(rows.items(), key=lambda kv: -kv[1][1])}
-        hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-               "peak_kind": peak_kind, "algorithmic_bytes_per_launch": a_bytes,
-               "traffic": ncu_traffic(dom, args.workload)}
+        traffic = ncu_traffic(dom, args.workload)
         pairs = work.algorithmic_pairs().get(dom) if hasattr(work, "algorithmic_pairs") else None
-        # the binding roofline: the larger of the two minimum times (bytes at
-        # the HBM peak, pair tests at the ALU peak)
-        t_hbm = (a_bytes / (peak * 1e9)) if a_bytes else 0.0
-        t_alu = (pairs / PAIR_PEAK) if pairs else 0.0
-        if pairs and t_alu > t_hbm:
+        # the HBM roofline of the dominant kernel (its algorithmic bytes per
+        # launch over its mean launch time), the whole step's, and the pair
+        # tests of the kernel against the measured pair-test rate of this GPU
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": a_bytes, "avg_launch_ms": avg_ms, "traffic": traffic,
+                "traffic_over_algorithmic": (traffic / a_bytes) if (traffic and a_bytes) else None,
+                "kernel_share": share}
+        if pairs:
             ach = pairs / (avg_ms * 1e-3)
-            roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": PAIR_PEAK, "unit": "pair tests/s",
-                    "frac": ach / PAIR_PEAK, "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 (FP32x2) x "
-                    "2.032 GHz / 6 operations per pair test", "algorithmic_pairs_per_launch": pairs,
-                    "traffic": hbm["traffic"], "avg_launch_ms": avg_ms, "hbm": hbm, "kernel_share": share}
-        else:
-            roof = dict(bound="hbm", kernel=dom, avg_launch_ms=avg_ms, kernel_share=share, **hbm)
+            roof["alu"] = {"achieved": ach, "peak": pair_peak, "unit": "pair tests/s",
+                           "frac": (ach / pair_peak) if pair_peak else None,
+                           "peak_kind": "measured: si_measure_pair_rate, packed f32x2 pair tests, best of 5",
+                           "algorithmic_pairs_per_launch": pairs}
     step_gbs = work.step_bytes() / (ms_step * 1e-3) / 1e9
+    if roof is not None:
+        roof["step"] = {"achieved": step_gbs, "frac": step_gbs / peak, "unit": "GB/s",
+                        "algorithmic_bytes": work.step_bytes()}
     e2e = None
     if not args.no_e2e and isinstance(work, RadiusWork):
         e_ms, bi, bo = e2e_radius(work, max(3, args.steps // 2), 2)
@@ -939,6 +1015,11 @@ def main():
             "roofline": roof, "gpu_launches": int(launches), "clocks": clk.summary(), "e2e": e2e,
             "ms_samples": {"median": float(np.median(ms)), "min": float(np.min(ms)),
                            "max": float(np.max(ms))}}
+    if args.workload == "radius_1m" and not args.no_compare:
+        cmp = same_run_comparisons(max(3, min(args.steps, 10)), 3, flush, local)
+        cmp["sphere_vs_cube"] = cmp["radius_1m_cube"]["ms_per_step"] / ms_step
+        cmp["batched_vs_loop"] = cmp["batched_loop"]["ms_per_step"] / cmp["batched"]["ms_per_step"]
+        line["comparisons"] = cmp
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0:

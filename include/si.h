@@ -110,7 +110,13 @@ typedef struct {
 /* Create a grid for up to n_capacity points: validates the descriptor,
  * builds the sorted offset table (Sec. II.A), its index by floor(d^2) and the
  * 64 specialized tables (Sec. III.A, Eq. 1-2) on the host, and allocates and
- * uploads every device array.  This is the only call that allocates. */
+ * uploads every device array.  The grid owns its device memory (no caller
+ * workspace): the query paths size part of it from data known only on the
+ * device (records of crowded cells, centers' staging, the point list of the
+ * list method), so a query call may grow it (eagerly, outside any stream
+ * capture; bench code captures only after a first eager call), and it is
+ * freed by si_grid_destroy.  Callers that cannot allocate at all have
+ * si_neighbor_energy_noalloc. */
 si_status si_grid_create(const si_grid_desc *desc, int64_t n_capacity, si_grid **out);
 
 /* Bin n points (n <= capacity) into the lattice: cell key by mask and shift
@@ -196,19 +202,24 @@ si_status si_neighbor_reduce(si_grid *g, float r, int kernel, double *d_energy,
  * cudaMalloc where they need the energy -- code running under a framework
  * that owns every device allocation, plug-ins with a fixed device-memory
  * budget, a real-time step that must never touch the allocator -- and cannot
- * create a grid.  It allocates nothing: its scratch (about 2.5 MB: cell keys,
- * counts and starts, points in cell order, partial sums, a status word) is one
- * static device array that every GPU loading the library holds until the
- * process exits.  Limits: n <= 65536 points and at most 2^16 cells
+ * create a grid.  It allocates nothing: its scratch (2,364,416 bytes =
+ * 2.25 MiB: cell keys, counts and starts, points in cell order, partial
+ * sums, a status word) is one static device array that every GPU loading the
+ * library holds until the process exits.  Limits: n <= 65536 points and at most 2^16 cells
  * (sum of log2_cells <= 16); larger inputs return SI_ERR_INVALID.
  * desc: lattice as for si_grid_create (r_max ignored; r validated the same
  * way).  d_pos: n * 4 floats, device, 16-byte aligned.  d_energy: one double,
  * device; NaN when a point lies outside a cyclic axis' box or is not finite.
  * Neighbors come from the bin-lattice walk (no tables needed), so the result
- * equals si_neighbor_reduce's up to FP32 summation order.
+ * equals si_neighbor_reduce's up to summation order; it is not bit-
+ * reproducible from call to call (the order of the points inside a cell
+ * follows the binning's atomic arrival; each thread sums its FP32 terms in
+ * FP64, which keeps the spread at the last few bits).
  * The first call on a device looks up the scratch array's device address
- * (with that device current); make that first call before any stream
- * capture.  Every call shares the scratch and leaves its contents there; the
+ * (with that device current) and keeps it for the life of the process; make
+ * that first call before any stream capture, and do not call this entry
+ * point on a device whose context was reset (cudaDeviceReset) after that
+ * first call, since the kept address would be stale.  Every call shares the scratch and leaves its contents there; the
  * call clears what must start at zero, and calls whose work overlaps on the
  * GPU (other streams, other host threads) race on it. */
 si_status si_neighbor_energy_noalloc(const si_grid_desc *desc, const float *d_pos, int64_t n,

@@ -100,7 +100,10 @@ si_status make_lattice(const si_grid_desc &d, double r_for_tables, Lattice &lat)
 void fill_griddev(const Lattice &lat, const DevTables &t, GridDev &g);
 
 // Inclusive prefix sum of n values, in place allowed (in == out).
-// Scratch must hold scan_scratch_elems(n) values.
+// Scratch must hold scan_scratch_elems(n) values: one per tile of kScanTile
+// values, plus one.
+constexpr int kScanTile = 4096;
+constexpr int64_t scan_scratch_count(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 int64_t scan_scratch_elems(int64_t n);
 si_status scan_inclusive_i32(const int *in, int *out, int64_t n, int *scratch, cudaStream_t st);
 si_status scan_inclusive_i64(const long long *in, long long *out, int64_t n, long long *scratch,

@@ -46,14 +46,18 @@ constexpr size_t kOffStart = align256(kOffCount + sizeof(int) * kNAMaxCells);
 constexpr size_t kOffSpos = align256(kOffStart + sizeof(int) * (kNAMaxCells + 1));
 constexpr size_t kOffPerm = align256(kOffSpos + sizeof(float4) * kNAMaxPoints);
 constexpr size_t kOffScan = align256(kOffPerm + sizeof(int) * kNAMaxPoints);
-constexpr size_t kOffPartial = align256(kOffScan + sizeof(int) * (kNAMaxCells / 4096 + 2));
+constexpr size_t kOffPartial = align256(kOffScan + sizeof(int) * scan_scratch_count(kNAMaxCells));
 constexpr size_t kOffStatus = align256(kOffPartial + sizeof(double) * kNAMaxBlocks);
 constexpr size_t kNoAllocBytes = align256(kOffStatus + sizeof(int));
+// the figure the header states (2,364,416 bytes, 2.25 MiB)
+static_assert(kNoAllocBytes == 2364416, "update the scratch size stated in include/si.h");
 
 __device__ __align__(256) static unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Device address of the scratch array, looked up once per device with that
-// device current (the host-side symbol is only a stand-in for it).
+// device current (the host-side symbol is only a stand-in for it) and kept
+// for the life of the process: a reset of that device's context would leave
+// it stale, which the header states.
 std::mutex g_na_mu;
 unsigned char *g_na_addr[64] = {nullptr};
 
@@ -77,7 +81,7 @@ struct EnergyVisitor {
   const QueryGeom &Q;
   float r2, inv_r2;
   int self;
-  float e;
+  double e;   // FP32 terms, FP64 sum: the order of a cell's points varies between calls
   __device__ __forceinline__ void operator()(const Target &t, bool) {
     const int b = __ldg(g.cell_start + t.key), en = __ldg(g.cell_start + t.key + 1);
     for (int j = b; j < en; ++j) {
@@ -99,7 +103,7 @@ struct EnergyVisitor {
       const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
       if (d2 < r2) {
         const float w = fmaf(-d2, inv_r2, 1.f);
-        e = fmaf(w * w, w, e);
+        e += (double)(w * w * w);
       }
     }
   }
@@ -113,9 +117,9 @@ __global__ void __launch_bounds__(kNAThreads) k_energy_noalloc(GridDev g, float 
   double e = 0.0;
   if (s < g.n) {
     const QueryGeom Q = make_geom(g.spos[s], g);
-    EnergyVisitor v{g, Q, r2, inv_r2, s, 0.f};
+    EnergyVisitor v{g, Q, r2, inv_r2, s, 0.0};
     walk_cube(g, Q, dg, v);
-    e = (double)v.e;
+    e = v.e;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);

@@ -9,7 +9,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kItems = 16;
-constexpr int kTile = kThreads * kItems;   // 4096 values per block
+constexpr int kTile = kThreads * kItems;   // values per block
+static_assert(kTile == kScanTile, "the scan's tile is the one scan_scratch_count assumes");
 
 template <typename T>
 __device__ __forceinline__ T warp_incl_scan(T v) {
@@ -122,7 +123,7 @@ si_status scan_inclusive(const T *in, T *out, int64_t n, T *scratch, cudaStream_
 
 }  // namespace
 
-int64_t scan_scratch_elems(int64_t n) { return (n + kTile - 1) / kTile + 1; }
+int64_t scan_scratch_elems(int64_t n) { return scan_scratch_count(n); }
 
 si_status scan_inclusive_i32(const int *in, int *out, int64_t n, int *scratch, cudaStream_t st) {
   return scan_inclusive<int>(in, out, n, scratch, st);

@@ -90,3 +90,29 @@ def test_cell_classes_follow_the_binning_rule():
         want = (3 if n27 >= 768 else 1) if heavy else (2 if n27 >= 24 else 0)
         assert cls[key] == want, key
     assert cls[nc] == (2 if cnt[nc] >= 24 else 0)
+
+
+def test_grouped_cells_rule():
+    # the group split the bench predicts, against a per-cell reading of the
+    # rule: a non-empty heavy cell (small class) of at most 128 points is
+    # grouped when its aligned 2x2x2 block holds another such cell
+    pos = synth.gaussian_mixture_points(30_000, 5, n_comp=6, sigma=0.08)
+    scene = synth.Scene(pos, (0, 0, 0), 1 / 16, (4, 4, 4), 7, 1.5 / 16)
+    start = cell_start(scene)
+    cls = bench.cell_classes(start, scene.log2_cells)
+    got = bench.grouped_cells(cls, start, scene.log2_cells, 1.5)
+    cnt = np.diff(start)
+    G = 16
+    want = np.zeros_like(got)
+    for c in range(G ** 3):
+        if cls[c] != 1 or cnt[c] == 0 or cnt[c] > 128:
+            continue
+        x, y, z = c % G, (c // G) % G, c // (G * G)
+        mates = 0
+        for k, j, i in itertools.product(range(2), repeat=3):
+            c2 = (x & ~1) + i + G * ((y & ~1) + j) + G * G * ((z & ~1) + k)
+            mates += cls[c2] == 1 and cnt[c2] > 0
+        want[c] = mates >= 2
+    assert np.array_equal(got, want) and want.sum() > 20 and (cls == 1).sum() > want.sum()
+    # too small a lattice for the group rows at this distance: nothing grouped
+    assert not bench.grouped_cells(cls, start, scene.log2_cells, 7.2).any()

@@ -72,3 +72,14 @@ def test_noalloc_limits_and_invalid_points():
     assert np.isnan(noalloc_energy(scene))
     good = synth.Scene(synth.uniform_points(500, 2), (0, 0, 0), 1 / 16, (4, 4, 4), 7, 0.1)
     assert abs(noalloc_energy(good) - grid_energy(good)) <= TOL * grid_energy(good)
+
+
+def test_noalloc_at_its_limits():
+    # exactly the maxima: 65,536 points on a 2^16-cell lattice (5 + 5 + 6),
+    # which fills every scratch region to its computed end; two calls in a row
+    pos = synth.uniform_points(65_536, 33, box=(1.0, 1.0, 2.0))
+    scene = synth.Scene(pos, (0, 0, 0), 1 / 32, (5, 5, 6), 7, 1.4 / 32)
+    want = grid_energy(scene)
+    for _ in range(2):
+        got = noalloc_energy(scene)
+        assert want > 0 and abs(got - want) <= TOL * want
