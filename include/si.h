@@ -67,6 +67,11 @@ typedef enum {
                                   each plane skipped when empty, taken as its
                                   point list when sparse, else walked by rows:
                                   for points concentrated on a few planes      */
+#define SI_FAST_D2       256u  /* K nearest: report the kernel's FP32 squared
+                                  distance (within 12u D2 + 16u L sqrt(D2) of
+                                  the canonical D2, u = 2^-24) instead of the
+                                  FP32 rounding of the canonical FP64 D2,
+                                  which costs K FP64 evaluations per query  */
 #define SI_NO_GROUPS     128u  /* radius: serve every crowded cell on its own
                                   (by default neighbouring crowded cells of an
                                   aligned 2x2x2 block share one candidate
@@ -177,7 +182,9 @@ si_status si_query_radius(si_grid *g, const float *d_centers, int64_t m, float r
  * with invalid coordinates gets count 0, ids -1 and d2 +inf).
  * Up to k (1 <= k <= 64) nearest points within r_max_query (inclusive), ordered
  * by (canonical D2, index); d_ids[m * k] int32 padded with -1, d_d2[m * k]
- * float (nullable; FP32 rounding of the canonical D2, +inf padding), and
+ * float (nullable; the FP32 rounding of the canonical FP64 D2, evaluated for
+ * the reported neighbors only, or with SI_FAST_D2 the kernel's FP32 value;
+ * +inf padding), and
  * d_counts[m] int32 (number found).  r_max_query <= the grid's r_max
  * (+inf allowed when the grid's r_max is +inf). */
 si_status si_query_knn(si_grid *g, const float *d_centers, int64_t m, int k,

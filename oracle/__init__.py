@@ -6,7 +6,9 @@ benchmark's CPU-baseline / reference legs may import, call or link anything
 in this package.  It shares no code with the CUDA path and never imports it.
 
 * `brute.c` (built into `_brute.so` by `build()`): FP64 brute force over all
-  objects -- the plain definition of the query (Sec. I, Sec. II.A).
+  objects -- the plain definition of the query (Sec. I, Sec. II.A) -- and
+  the same reduction through a plain bin lattice (cells at least r wide,
+  3 x 3 x 3 cells per object), for sizes where O(n^2) is too slow.
 * `sphere_index.py`: the paper's own method restated on the CPU in float64
   (tables of Sec. II.A and Sec. III.A, cell locations of Sec. II.B).  Used to
   pin the brute force against an independent algorithm and to check the
@@ -50,6 +52,7 @@ def _load():
         lib.or_radius_lists.argtypes = [P, I64, P, I64, P, P, I32, D, P, P, I32]
         lib.or_knn.argtypes = [P, I64, P, I64, P, P, I32, D, I32, P, P, P, I32]
         lib.or_reduce.argtypes = [P, I64, P, I64, P, I32, D, P, P, I32]
+        lib.or_reduce_cells.argtypes = [P, I64, P, I32, D, P, P, I32]
         _lib = lib
     return _lib
 
@@ -144,4 +147,19 @@ def reduce(pos, idx, box, cyclic_mask: int, r: float, threads: int = 0):
     g = np.zeros((idx.shape[0], 3), dtype=np.float64)
     lib.or_reduce(_ptr(pos), pos.shape[0], _ptr(idx), idx.shape[0], _ptr(L), int(cyclic_mask),
                   float(r), _ptr(e), _ptr(g), int(threads))
+    return e, g
+
+
+def reduce_all(pos, box, cyclic_mask: int, r: float, threads: int = 0):
+    """reduce() for every object, through the bin lattice of or_reduce_cells
+    (the same pairs and per-pair terms; only the order of each sum differs)."""
+    lib = _load()
+    pos = _f4(pos)
+    n = pos.shape[0]
+    L = np.ascontiguousarray(box, dtype=np.float64)
+    e = np.zeros(n, dtype=np.float64)
+    g = np.zeros((n, 3), dtype=np.float64)
+    if lib.or_reduce_cells(_ptr(pos), n, _ptr(L), int(cyclic_mask), float(r), _ptr(e), _ptr(g),
+                           int(threads)) != 0:
+        raise MemoryError("or_reduce_cells: allocation failed")
     return e, g

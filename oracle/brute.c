@@ -202,3 +202,123 @@ int or_reduce(const float *pos, int64_t n, const int64_t *idx, int64_t m,
     }
     return 0;
 }
+
+/*
+ * The same reduction as or_reduce for every object at once, through the plain
+ * bin lattice of Sec. I (the "cube" of cells around a query): objects are
+ * binned into cells at least r wide on every axis, so every pair with
+ * D2 < r2 lies in the same or adjacent cells (adjacent across the wrap on a
+ * cyclic axis).  Each object scans the 3 x 3 x 3 cells around its own and
+ * applies, per pair, the predicate and the terms of or_reduce; only the order
+ * of the sum over j differs.  Cyclic axis a: G_a = floor(L_a / r) cells of
+ * side L_a / G_a >= r, cell floor(x G_a / L_a) mod G_a (G_a >= 3, else the
+ * call falls back to or_reduce); non-cyclic axis: cells of side r from the
+ * smallest coordinate.  e[n], g[3n] (nullable) as or_reduce with idx = 0..n-1.
+ */
+int or_reduce_cells(const float *pos, int64_t n, const double *L, int cyc, double r, double *e,
+                    double *g, int nthreads) {
+    const double r2 = r * r;
+    int64_t G[3];
+    double lo[3], w[3];
+    for (int a = 0; a < 3; ++a) {
+        if ((cyc >> a) & 1) {
+            G[a] = (int64_t)floor(L[a] / r);
+            lo[a] = 0.0;
+            w[a] = L[a] / (double)G[a];
+            if (G[a] < 3) {
+                int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+                for (int64_t i = 0; i < n; ++i) idx[i] = i;
+                const int rc = or_reduce(pos, n, idx, n, L, cyc, r, e, g, nthreads);
+                free(idx);
+                return rc;
+            }
+        } else {
+            double mn = INFINITY, mx = -INFINITY;
+            for (int64_t i = 0; i < n; ++i) {
+                const double x = (double)pos[4 * i + a];
+                if (x < mn) mn = x;
+                if (x > mx) mx = x;
+            }
+            if (n == 0) mn = mx = 0.0;
+            lo[a] = mn;
+            w[a] = r;
+            G[a] = (int64_t)floor((mx - mn) / r) + 1;
+        }
+    }
+    const int64_t C = G[0] * G[1] * G[2];
+    int64_t *cell = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *start = (int64_t *)calloc((size_t)C + 1, sizeof(int64_t));
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)C);
+    if (!cell || !start || !order || !fill) {
+        free(cell); free(start); free(order); free(fill);
+        return -1;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t c[3];
+        for (int a = 0; a < 3; ++a) {
+            const double x = (double)pos[4 * i + a];
+            int64_t k;
+            if ((cyc >> a) & 1) {
+                k = (int64_t)floor(x / L[a] * (double)G[a]);
+                k %= G[a];
+                if (k < 0) k += G[a];
+            } else {
+                k = (int64_t)floor((x - lo[a]) / w[a]);
+                if (k < 0) k = 0;
+                if (k >= G[a]) k = G[a] - 1;
+            }
+            c[a] = k;
+        }
+        cell[i] = (c[2] * G[1] + c[1]) * G[0] + c[0];
+        ++start[cell[i] + 1];
+    }
+    for (int64_t c = 0; c < C; ++c) start[c + 1] += start[c];
+    for (int64_t c = 0; c < C; ++c) fill[c] = start[c];
+    for (int64_t i = 0; i < n; ++i) order[fill[cell[i]]++] = i;   /* ascending index inside a cell */
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        const float *pi = pos + 4 * i;
+        const int64_t ci = cell[i];
+        const int64_t cx = ci % G[0], cy = (ci / G[0]) % G[1], cz = ci / (G[0] * G[1]);
+        double es = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+        for (int dz = -1; dz <= 1; ++dz) {
+            int64_t z = cz + dz;
+            if (cyc & 4) z = (z + G[2]) % G[2];
+            else if (z < 0 || z >= G[2]) continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                int64_t y = cy + dy;
+                if (cyc & 2) y = (y + G[1]) % G[1];
+                else if (y < 0 || y >= G[1]) continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int64_t x = cx + dx;
+                    if (cyc & 1) x = (x + G[0]) % G[0];
+                    else if (x < 0 || x >= G[0]) continue;
+                    const int64_t c = (z * G[1] + y) * G[0] + x;
+                    for (int64_t t = start[c]; t < start[c + 1]; ++t) {
+                        const int64_t j = order[t];
+                        if (j == i) continue;
+                        const float *pj = pos + 4 * j;
+                        const double dd = or_canon_d2(pi, pj, L, cyc);
+                        if (!(dd < r2)) continue;
+                        const double u = 1.0 - dd / r2;
+                        es += u * u * u;
+                        const double cu = u * u;
+                        gx += cu * axis_disp((double)pi[0], (double)pj[0], L[0], cyc & 1);
+                        gy += cu * axis_disp((double)pi[1], (double)pj[1], L[1], (cyc >> 1) & 1);
+                        gz += cu * axis_disp((double)pi[2], (double)pj[2], L[2], (cyc >> 2) & 1);
+                    }
+                }
+            }
+        }
+        e[i] = es;
+        if (g) {
+            g[3 * i + 0] = -12.0 / r2 * gx;
+            g[3 * i + 1] = -12.0 / r2 * gy;
+            g[3 * i + 2] = -12.0 / r2 * gz;
+        }
+    }
+    free(cell); free(start); free(order); free(fill);
+    return 0;
+}

@@ -211,11 +211,12 @@ class Grid:
         return off, ids
 
     def query_knn(self, k: int, r_max=None, include_self: bool = False, with_d2: bool = True,
-                  out=None, centers=None):
+                  out=None, centers=None, fast_d2: bool = False):
         """K nearest within r_max (None = grid's whole region), for every point
         (centers None) or for each row of a CUDA float32 (m, 4) tensor of
         query centers.  Returns (ids int32[m,k] padded -1, d2 float32[m,k]
-        or None, counts int32[m])."""
+        or None, counts int32[m]).  d2 is the FP32 rounding of the canonical
+        FP64 squared distance; fast_d2 reports the kernel's FP32 value."""
         dev = self._pos.device
         m = self.n
         if centers is not None:
@@ -231,7 +232,7 @@ class Grid:
             if d2 is not None:
                 _check_out(d2, torch.float32, m * k, "out d2")
         rm = float("inf") if r_max is None else float(r_max)
-        flags = N.SI_INCLUDE_SELF if include_self else 0
+        flags = (N.SI_INCLUDE_SELF if include_self else 0) | (N.SI_FAST_D2 if fast_d2 else 0)
         N.check(self._lib.si_query_knn(self._h, _ptr(centers), m, int(k), rm, flags, _ptr(ids), _ptr(d2),
                                        _ptr(cnt), _stream()), "si_query_knn")
         return ids, d2, cnt

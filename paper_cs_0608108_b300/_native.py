@@ -12,7 +12,7 @@ SO_PATH = os.path.join(_PKG, "libsi.so")
 
 SI_OK, SI_ERR_INVALID, SI_ERR_OOM, SI_ERR_CUDA, SI_ERR_CAPACITY, SI_ERR_TIMEOUT, SI_ERR_INTERNAL = range(7)
 SI_METHOD_SPHERE, SI_METHOD_CUBE, SI_INCLUDE_SELF, SI_NO_SORT, SI_WALK_PAPER = 0, 1, 2, 4, 8
-SI_METHOD_LIST, SI_SPHERE_ONLY, SI_WALK_PLANES, SI_NO_GROUPS = 16, 32, 64, 128
+SI_METHOD_LIST, SI_SPHERE_ONLY, SI_WALK_PLANES, SI_NO_GROUPS, SI_FAST_D2 = 16, 32, 64, 128, 256
 SI_KERNEL_POLY6_CUBED = 0
 
 c_float3 = ctypes.c_float * 3

@@ -212,9 +212,12 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(GridDev g, int K, float dma
   const int orig = __ldg(g.qid + s);
   int *oi = out_ids + (size_t)orig * K;
   for (int k = 0; k < K; ++k) oi[k] = k < cnt ? __ldg(g.perm + L.j[L.at(k)]) : -1;
-  if (out_d2) {
+  if (out_d2) {   // the FP32 rounding of the canonical FP64 D2 of each reported neighbor, or the FP32 value
     float *od = out_d2 + (size_t)orig * K;
-    for (int k = 0; k < K; ++k) od[k] = k < cnt ? L.d[L.at(k)] : __int_as_float(0x7f800000);
+    const bool fast = flags & SI_FAST_D2;
+    for (int k = 0; k < K; ++k)
+      od[k] = k >= cnt ? __int_as_float(0x7f800000)
+                       : (fast ? L.d[L.at(k)] : __double2float_rn(canon_d2(Q.q, g.spos[L.j[L.at(k)]], g)));
   }
   out_counts[orig] = cnt;
 }
@@ -457,7 +460,12 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, f
     const bool have = k < kept;
     const unsigned long long x = have ? key[k] : 0ull;
     oi[k] = have ? __ldg(g.perm + (int)(x & 0xffffffffu)) : -1;
-    if (od) od[k] = have ? __uint_as_float((unsigned)(x >> 32)) : __int_as_float(0x7f800000);
+    // the FP32 rounding of the canonical FP64 D2 of each reported neighbor,
+    // or (SI_FAST_D2) the FP32 value the kernel sorted by
+    if (od)
+      od[k] = !have ? __int_as_float(0x7f800000)
+                    : ((flags & SI_FAST_D2) ? __uint_as_float((unsigned)(x >> 32))
+                                            : __double2float_rn(canon_d2(Q.q, g.spos[(int)(x & 0xffffffffu)], g)));
   }
   if (lane == 0) out_counts[orig] = kept;
 }
@@ -478,7 +486,7 @@ extern "C" si_status si_query_knn(si_grid *g, const float *d_centers, int64_t m,
   }
   if (k < 1 || k > 64) return fail(SI_ERR_INVALID, "k must be in [1, 64]");
   if (!d_ids || !d_counts) return fail(SI_ERR_INVALID, "null output");
-  if (flags & ~(SI_INCLUDE_SELF)) return fail(SI_ERR_INVALID, "unknown flags");
+  if (flags & ~(SI_INCLUDE_SELF | SI_FAST_D2)) return fail(SI_ERR_INVALID, "unknown flags");
   const bool unb = !(r_max_query > 0.f) || std::isinf(r_max_query);
   if (unb && !g->lat.unbounded) return fail(SI_ERR_INVALID, "unbounded r_max needs an unbounded grid");
   if (!unb && !g->lat.unbounded && (double)r_max_query > (double)g->desc.r_max)

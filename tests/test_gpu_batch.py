@@ -88,3 +88,38 @@ def test_batch_with_a_single_kind_of_scene(kind):
             assert totals[k] == off_p[-1]
             assert np.array_equal(o, off_p)
             assert np.array_equal(ids[k].cpu().numpy()[: o[-1]], ids_p)
+
+
+def test_full_size_256_scene_batch_sampled():
+    # the batched configuration at full size (256 scenes, 1,000-200,000
+    # points each, lattices 16^3-128^3, r 1-3 cells, random cyclic masks),
+    # replayed from its graph: every scene's total against the single-scene
+    # path, and a sample of queries in every scene, element by element,
+    # against the FP64 oracle
+    from paper_cs_0608108_b300 import Grid
+    scenes = synth.batched_scenes()
+    totals = []
+    for sc in scenes:
+        g = Grid.for_scene(sc)
+        g.build(to_dev(sc.pos))
+        off, _ = g.query_radius(sc.r)
+        totals.append(int(off[-1].item()))
+        g.close()
+    b, offs, ids = make_batch(scenes, caps=[t + 1 for t in totals])
+    b.run(use_graph=False)
+    b.sync()
+    for _ in range(2):
+        b.run(use_graph=True)
+    got = b.sync()
+    assert got == totals
+    rng = np.random.default_rng(256)
+    for k, sc in enumerate(scenes):
+        if sc.n == 0:
+            continue
+        q = rng.choice(sc.n, min(6, sc.n), replace=False)
+        off_o, ids_o = oracle_radius(sc, queries=q)
+        o = offs[k].cpu().numpy()
+        lst = ids[k].cpu().numpy()
+        assert o[-1] == totals[k]
+        for t, qi in enumerate(q):
+            assert np.array_equal(lst[o[qi]:o[qi + 1]], ids_o[off_o[t]:off_o[t + 1]]), (k, qi)

@@ -1,5 +1,6 @@
 """Parity of the CUDA K-nearest query with the FP64 oracle: ids (ordered by
-(D2, index)) and counts bit-exact; the FP32 distances within their bound."""
+(D2, index)) and counts bit-exact; the distances are the FP32 roundings of
+the canonical FP64 D2, bit-exact."""
 import numpy as np
 import pytest
 import torch
@@ -31,8 +32,8 @@ def check(scene, k, r_max, ids, d2, cnt, queries):
     fin = np.isfinite(od)
     got = d2[queries].astype(np.float64)
     assert np.all(np.isinf(got[~fin]))
-    L = max(scene.box)
-    assert np.all(np.abs(got[fin] - od[fin]) <= 12 * U * od[fin] + 16 * U * L * np.sqrt(od[fin]) + 1e-30)
+    # the FP32 rounding of the canonical FP64 D2, exactly
+    assert np.array_equal(d2[queries][fin], od[fin].astype(np.float32))
 
 
 def test_tiny_config_k8_unbounded_exact():
@@ -90,3 +91,21 @@ def test_crowded_queries_overflowing_the_warp_buffer():
     for k in (16, 64):
         ids, d2, cnt = run_knn(scene, k, scene.r)
         check(scene, k, scene.r, ids, d2, cnt, np.arange(scene.n))
+
+
+def test_fast_distances_within_their_bound():
+    # SI_FAST_D2: the same ids and counts, the kernel's FP32 squared distance
+    # within 12u D2 + 16u L sqrt(D2) of the canonical D2
+    pos = synth.uniform_points(30_000, 77)
+    scene = synth.Scene(pos, (0, 0, 0), 1 / 32, (5, 5, 5), 3, 4 / 32)
+    g = gpu_grid(scene)
+    ids, d2, cnt = g.query_knn(16, r_max=scene.r, fast_d2=True)
+    g.sync()
+    q = np.arange(0, scene.n, 5)
+    oi, od, oc = oracle.knn(scene.pos, scene.pos[q], scene.box, 3, 16, float(np.float32(scene.r)), q)
+    assert np.array_equal(cnt.cpu().numpy()[q], oc) and np.array_equal(ids.cpu().numpy()[q], oi)
+    got = d2.cpu().numpy()[q].astype(np.float64)
+    fin = np.isfinite(od)
+    assert np.all(np.isinf(got[~fin]))
+    L = max(scene.box)
+    assert np.all(np.abs(got[fin] - od[fin]) <= 12 * U * od[fin] + 16 * U * L * np.sqrt(od[fin]) + 1e-30)

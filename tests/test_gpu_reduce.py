@@ -36,6 +36,29 @@ def test_energy_and_gradient_exact_small(mask):
     assert np.linalg.norm(G - g) <= TOL * np.linalg.norm(g)
 
 
+def test_full_size_1m_energy_and_gradient_exact():
+    # config 5 positions (1M uniform, 128^3 cyclic, r = 1.5 cells) and three
+    # random-walk steps with rebinning: E and every gradient against the FP64
+    # oracle through its bin lattice (all points, not a sample)
+    scene = synth.uniform_1m_scene()
+    g = Grid(scene.origin, scene.cell_size, scene.log2_cells, 7, scene.r, scene.n)
+    pos = scene.pos
+    for step in range(4):
+        if step:
+            pos = synth.random_walk_step(pos, synth.SEEDS["walk_1m"], step, 0.1 * scene.cell_size)
+        g.build(to_dev(pos))
+        e = torch.empty(1, dtype=torch.float64, device="cuda")
+        gr = torch.empty((scene.n, 4), dtype=torch.float32, device="cuda")
+        g.neighbor_reduce(scene.r, energy=e, grad=gr)
+        g.sync()
+        eo, go = oracle.reduce_all(pos, scene.box, 7, scene.r)
+        G = gr.cpu().numpy()[:, :3]
+        assert abs(float(e.item()) - eo.sum()) <= TOL * eo.sum()
+        assert np.linalg.norm(G - go) <= TOL * np.linalg.norm(go)
+        rms = np.sqrt((go ** 2).sum(axis=1).mean())
+        assert np.abs(G - go).max() <= 1e-3 * rms
+
+
 def test_full_size_1m_gradient_sampled():
     scene = synth.uniform_1m_scene()
     E, G, _ = gpu_reduce(scene)
