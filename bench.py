@@ -537,9 +537,13 @@ class WalkWork:
 
 
 class BatchWork:
-    def __init__(self, scenes, graph=True):
+    """The batch of scenes in one library batch; params: the planner's
+    choices (None: the ones tuned for this batch on a B300, from the
+    package's cache, else the defaults)."""
+
+    def __init__(self, scenes, graph=True, params="tuned"):
         import torch
-        from paper_cs_0608108_b300 import Batch, Grid
+        from paper_cs_0608108_b300 import Batch, Grid, lookup_batch_params
         self.scenes = scenes
         self.pos = [torch.from_numpy(s.pos).cuda() for s in scenes]
         self.offs = [torch.empty(s.n + 1, dtype=torch.int64, device="cuda") for s in scenes]
@@ -552,7 +556,8 @@ class BatchWork:
             self.totals.append(int(off[-1].item()))
             g.close()
         self.ids = [torch.empty(max(t, 1), dtype=torch.int32, device="cuda") for t in self.totals]
-        self.batch = Batch(list(zip(scenes, self.pos)), self.offs, self.ids)
+        self.params = lookup_batch_params(scenes) if params == "tuned" else params
+        self.batch = Batch(list(zip(scenes, self.pos)), self.offs, self.ids, params=self.params)
         self.graph = graph
         self.queries = sum(s.n for s in scenes)
 
@@ -723,15 +728,22 @@ def same_run_comparisons(steps, warmup, flush, local):
         bw = BatchWork(scenes)
         ms_b = time_steps(bw, steps, warmup, flush)
         bw.check()
+        bd = BatchWork(scenes, params=None)
+        ms_d = time_steps(bd, steps, warmup, flush)
+        bd.check()
+        del bd
         lw = LoopWork(scenes)
         ms_l = time_steps(lw, steps, warmup, flush)
         lw.check()
         same = all(torch.equal(a, b) for a, b in zip(bw.offs, lw.off)) and \
             all(torch.equal(a[:t], b[:t]) for a, b, t in zip(bw.ids, lw.ids, bw.totals))
         out["batched"] = {"ms_per_step": float(np.mean(ms_b)), "queries_per_s": bw.queries / (np.mean(ms_b) * 1e-3),
-                          "scenes": len(scenes), "points": bw.queries,
+                          "scenes": len(scenes), "points": bw.queries, "planner": bw.params or "defaults",
                           "description": "256 uneven scenes, one graph replay (fused short-list scenes, "
-                                         "concurrent branches for long-list scenes)"}
+                                         "concurrent branches for long-list scenes), planner choices tuned "
+                                         "on a B300 (package cache)"}
+        out["batched_default_planner"] = {"ms_per_step": float(np.mean(ms_d)),
+                                          "queries_per_s": bw.queries / (np.mean(ms_d) * 1e-3)}
         out["batched_loop"] = {"ms_per_step": float(np.mean(ms_l)), "queries_per_s": lw.queries / (np.mean(ms_l) * 1e-3),
                                "description": "the plain single-scene path called scene after scene"}
         out["batched_equals_loop"] = bool(same)

@@ -273,11 +273,49 @@ typedef struct {
 
 typedef struct si_batch si_batch;
 
+/* The batch planner's choices (the paper's discretization tuning, Sec.
+ * IV.A, carried over to the batch: the best split depends on the scenes).
+ *   heavy_hits     expected list length (load x sphere volume in cells) from
+ *                  which a scene runs the single-scene pipeline instead of
+ *                  the fused launches (default 24; 0: every non-empty scene)
+ *   q_tile         queries per work item, and threads per block, of the
+ *                  fused query kernels (one thread per query): 64, 128 or 256
+ *                  (default 128)
+ *   branches       concurrent graph branches of the single-scene pipelines,
+ *                  1..8 (default 8)
+ *   blocks_per_sm  resident blocks per SM of the fused persistent query
+ *                  kernels, 1..2048 / q_tile (default 8) */
+typedef struct {
+  float heavy_hits;
+  int32_t q_tile;
+  int32_t branches;
+  int32_t blocks_per_sm;
+} si_batch_params;
+
+/* The defaults above, into *p (host). */
+si_status si_batch_default_params(si_batch_params *p);
+
 /* Plan a batch: validates every scene, builds each scene's tables and
  * allocates the batch's device memory (cell arrays of all scenes, sorted
  * points, work queue).  Scene pointers are captured: later runs read the
- * scenes' current point data and write their outputs. */
+ * scenes' current point data and write their outputs.  si_batch_create uses
+ * the default planner choices; si_batch_create_params takes them from
+ * *params (host, nullable = defaults; SI_ERR_INVALID when out of range). */
 si_status si_batch_create(const si_scene *scenes, int n_scenes, uint32_t flags, si_batch **out);
+si_status si_batch_create_params(const si_scene *scenes, int n_scenes, uint32_t flags,
+                                 const si_batch_params *params, si_batch **out);
+
+/* Time planner choices on these scenes: for each of the n_cand candidates
+ * (host array) a batch is created, run once eagerly, captured, replayed twice
+ * and then timed over `reps` graph replays with CUDA events on a stream of
+ * its own; h_ms[i] (host) receives the median milliseconds, *h_best (host)
+ * the index of the fastest.  The runs write the scenes' outputs.
+ * Synchronises; allocates and frees each candidate's batch.  Errors:
+ * SI_ERR_INVALID (bad arguments, a candidate out of range), and those of
+ * si_batch_create_params / si_batch_run / si_batch_sync (e.g.
+ * SI_ERR_CAPACITY when an id buffer is too small). */
+si_status si_batch_tune(const si_scene *scenes, int n_scenes, uint32_t flags, const si_batch_params *cands,
+                        int n_cand, int reps, float *h_ms, int32_t *h_best);
 
 /* Run the batch on `stream`: bin all scenes, count, scan, write, sort.
  * Capacity overflow is reported by si_batch_sync.  The first call runs

@@ -9,6 +9,10 @@ kernels; there is no CPU path.
 from __future__ import annotations
 
 import ctypes
+import hashlib
+import json
+import math
+import os
 
 import torch
 
@@ -283,27 +287,49 @@ def neighbor_energy(pos: torch.Tensor, grid: Grid, r: float) -> torch.Tensor:
     return NeighborEnergy.apply(pos, grid, r)
 
 
-class Batch:
-    """Many independent scenes served by one fixed set of launches."""
+def _scene_array(scenes, offsets, ids, keep):
+    arr = (N.SceneDesc * len(scenes))()
+    for k, (sc, pos) in enumerate(scenes):
+        pos = _check_points(pos)
+        keep.append(pos)
+        arr[k].desc = make_desc(sc.origin, sc.cell_size, sc.log2_cells, sc.cyclic_mask, sc.r)
+        arr[k].d_pos = pos.data_ptr()
+        arr[k].n = pos.shape[0]
+        arr[k].r = float(sc.r)
+        arr[k].d_offsets = offsets[k].data_ptr()
+        arr[k].d_ids = ids[k].data_ptr()
+        arr[k].ids_capacity = ids[k].numel()
+    keep += list(offsets) + list(ids)
+    return arr
 
-    def __init__(self, scenes, offsets, ids, flags: int = 0):
+
+def default_batch_params() -> dict:
+    """The batch planner's defaults (si_batch_default_params)."""
+    p = N.BatchParams()
+    N.check(N.lib().si_batch_default_params(ctypes.byref(p)), "si_batch_default_params")
+    return {"heavy_hits": p.heavy_hits, "q_tile": p.q_tile, "branches": p.branches,
+            "blocks_per_sm": p.blocks_per_sm}
+
+
+def _params(d) -> N.BatchParams:
+    return N.BatchParams(float(d["heavy_hits"]), int(d["q_tile"]), int(d["branches"]), int(d["blocks_per_sm"]))
+
+
+class Batch:
+    """Many independent scenes served by one fixed set of launches; params
+    (a dict of si_batch_params fields, None = defaults) sets the planner's
+    choices, e.g. the ones tune_batch found."""
+
+    def __init__(self, scenes, offsets, ids, flags: int = 0, params=None):
         self._lib = N.lib()
-        arr = (N.SceneDesc * len(scenes))()
         self._keep = []
-        for k, (sc, pos) in enumerate(scenes):
-            pos = _check_points(pos)
-            self._keep.append(pos)
-            arr[k].desc = make_desc(sc.origin, sc.cell_size, sc.log2_cells, sc.cyclic_mask, sc.r)
-            arr[k].d_pos = pos.data_ptr()
-            arr[k].n = pos.shape[0]
-            arr[k].r = float(sc.r)
-            arr[k].d_offsets = offsets[k].data_ptr()
-            arr[k].d_ids = ids[k].data_ptr()
-            arr[k].ids_capacity = ids[k].numel()
-        self._keep += list(offsets) + list(ids)
+        arr = _scene_array(scenes, offsets, ids, self._keep)
         self.n_scenes = len(scenes)
         h = ctypes.c_void_p()
-        N.check(self._lib.si_batch_create(arr, len(scenes), int(flags), ctypes.byref(h)), "si_batch_create")
+        prm = _params(params) if params is not None else None
+        N.check(self._lib.si_batch_create_params(arr, len(scenes), int(flags),
+                                                 ctypes.byref(prm) if prm is not None else None, ctypes.byref(h)),
+                "si_batch_create_params")
         self._h = h
 
     def run(self, use_graph: bool = False):
@@ -324,3 +350,77 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Batch planner tuning with a cache on disk
+# ---------------------------------------------------------------------------
+def batch_scene_key(scene) -> tuple:
+    """What the planner's choices depend on for one scene: its point count
+    (bucket: rounded log2), its lattice (log2 cells per axis), its radius in
+    cells (to a quarter cell), its load (points per cell, bucket: rounded
+    2 log2) and its cyclic mask."""
+    n = int(scene.n)
+    cells = 1 << sum(scene.log2_cells)
+    d = float(scene.r) / float(scene.cell_size)
+    load = n / cells
+    return (int(round(math.log2(n))) if n > 0 else -1, tuple(int(w) for w in scene.log2_cells),
+            round(d * 4) / 4, int(round(2 * math.log2(load))) if load > 0 else -99, int(scene.cyclic_mask))
+
+
+def batch_signature(scenes, flags: int = 0) -> str:
+    """Cache key of a batch: the sorted multiset of its scenes' keys (the
+    order of the scenes does not matter) and the flags."""
+    keys = sorted(batch_scene_key(sc) for sc in scenes)
+    return hashlib.sha1(repr((int(flags), keys)).encode()).hexdigest()
+
+
+DEFAULT_CANDIDATES = [{"heavy_hits": h, "q_tile": t, "branches": 8, "blocks_per_sm": 2048 // t // 2}
+                      for h in (0.0, 4.0, 8.0, 16.0, 24.0, 64.0) for t in (64, 128, 256)]
+
+
+TUNING_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "batch_tuning.json")
+
+
+def lookup_batch_params(scenes, cache: str = TUNING_CACHE, flags: int = 0):
+    """The cached planner choices for these scenes (Scene objects), or None;
+    times nothing.  The package's cache holds choices tuned on a B300."""
+    if not cache or not os.path.exists(cache):
+        return None
+    with open(cache) as fh:
+        store = json.load(fh)
+    hit = store.get(batch_signature(scenes, flags))
+    return dict(hit["params"]) if hit else None
+
+
+def tune_batch(scenes, offsets, ids, flags: int = 0, cache: str | None = None, candidates=None,
+               reps: int = 3):
+    """The planner choices for these scenes ((scene, pos) pairs, outputs as
+    for Batch): looked up in the JSON cache file `cache` by batch_signature,
+    else timed by si_batch_tune over the candidates (default: the heavy-list
+    threshold 0 / 4 / 8 / 16 / 24 / 64, query tile 64 / 128 / 256, 8
+    branches) and stored there.  Returns (params dict, {"ms": [...] or None, "cached": bool,
+    "signature": str})."""
+    sig = batch_signature([sc for sc, _ in scenes], flags)
+    store = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as fh:
+            store = json.load(fh)
+        if sig in store:
+            return dict(store[sig]["params"]), {"ms": None, "cached": True, "signature": sig}
+    cands = list(candidates or DEFAULT_CANDIDATES)
+    keep = []
+    arr = _scene_array(scenes, offsets, ids, keep)
+    carr = (N.BatchParams * len(cands))(*[_params(c) for c in cands])
+    ms = (ctypes.c_float * len(cands))()
+    best = ctypes.c_int32(-1)
+    N.check(N.lib().si_batch_tune(arr, len(scenes), int(flags), carr, len(cands), int(reps), ms, ctypes.byref(best)),
+            "si_batch_tune")
+    params = dict(cands[best.value])
+    if cache:
+        store[sig] = {"params": params, "ms": float(ms[best.value]), "scenes": len(scenes)}
+        tmp = cache + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(store, fh, indent=1, sort_keys=True)
+        os.replace(tmp, cache)
+    return params, {"ms": [float(x) for x in ms], "cached": False, "signature": sig}

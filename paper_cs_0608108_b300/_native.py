@@ -32,6 +32,11 @@ class GridInfo(ctypes.Structure):
                 ("table_n_max", ctypes.c_int32), ("spec_shells", ctypes.c_int32)]
 
 
+class BatchParams(ctypes.Structure):
+    _fields_ = [("heavy_hits", ctypes.c_float), ("q_tile", ctypes.c_int32), ("branches", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32)]
+
+
 class SceneDesc(ctypes.Structure):
     _fields_ = [("desc", GridDesc), ("d_pos", ctypes.c_void_p), ("n", ctypes.c_int64),
                 ("r", ctypes.c_float), ("d_offsets", ctypes.c_void_p), ("d_ids", ctypes.c_void_p),
@@ -54,6 +59,10 @@ SIGNATURES = {
     "si_neighbor_energy_noalloc": (I32, [ctypes.POINTER(GridDesc), P, I64, F, P, P]),
     "si_tune_lattice": (I32, [ctypes.POINTER(GridDesc), P, I64, P, I64, F, I32, P, I32, I32, P, P, P]),
     "si_batch_create": (I32, [ctypes.POINTER(SceneDesc), I32, U32, ctypes.POINTER(P)]),
+    "si_batch_default_params": (I32, [ctypes.POINTER(BatchParams)]),
+    "si_batch_create_params": (I32, [ctypes.POINTER(SceneDesc), I32, U32, ctypes.POINTER(BatchParams),
+                                     ctypes.POINTER(P)]),
+    "si_batch_tune": (I32, [ctypes.POINTER(SceneDesc), I32, U32, ctypes.POINTER(BatchParams), I32, I32, P, P]),
     "si_batch_run": (I32, [P, I32, P]),
     "si_batch_sync": (I32, [P, P, P]),
     "si_batch_destroy": (I32, [P]),

@@ -26,11 +26,18 @@
 namespace si {
 
 constexpr int kBinTile = 256;
-constexpr int kQTile = 128;
 constexpr int kBatchInlineSort = 32;
 constexpr int kBatchSortThreads = 512;
 constexpr int kBatchSortSmem = 8192;
-constexpr double kBatchHeavyHits = 24.0;   // expected list length from which a scene gets its own pipeline
+// Planner defaults (si_batch_params; si_batch_tune times alternatives): the
+// expected list length from which a scene gets its own pipeline, the
+// queries per item (threads per block) of the fused query kernels, the
+// concurrent graph branches of the own pipelines, the resident blocks per
+// SM of the fused persistent kernels.
+constexpr float kDefHeavyHits = 24.f;
+constexpr int kDefQTile = 128;
+constexpr int kDefBranches = 8;
+constexpr int kDefBlocksPerSm = 8;
 
 struct SceneDev {
   GridDev g;               // spos/perm: batch-global arrays; cell_start: the scene's cells
@@ -92,8 +99,8 @@ __global__ void __launch_bounds__(kBinTile) k_batch_scatter(const SceneDev *__re
 // Persistent query pass.  WRITE = false: counts into gcount (global index
 // pbase + local id).  WRITE = true: lists into each scene's ids, using the
 // inclusive scan gscan of gcount.
-template <bool WRITE>
-__global__ void __launch_bounds__(kQTile) k_batch_query(const SceneDev *__restrict__ sc,
+template <bool WRITE, int TILE>
+__global__ void __launch_bounds__(TILE) k_batch_query(const SceneDev *__restrict__ sc,
                                                         const Item *__restrict__ items, int n_items,
                                                         int *__restrict__ queue,
                                                         long long *__restrict__ gcount,
@@ -247,6 +254,7 @@ __global__ void __launch_bounds__(kBatchSortThreads) k_batch_sort(const SceneDev
 using namespace si;
 
 struct si_batch {
+  si_batch_params params;         // the planner's choices
   struct Heavy {
     int scene;                    // index in `scenes`
     si_grid *grid;
@@ -324,13 +332,37 @@ static bool plan_cube(double d) {
   return d < 1.0 && cube < 1.15 * sphere;
 }
 
+static bool params_valid(const si_batch_params &p) {
+  return p.heavy_hits >= 0.f && (p.q_tile == 64 || p.q_tile == 128 || p.q_tile == 256) && p.branches >= 1 &&
+         p.branches <= 8 && p.blocks_per_sm >= 1 && p.blocks_per_sm <= 2048 / p.q_tile;
+}
+
+extern "C" si_status si_batch_default_params(si_batch_params *p) {
+  if (!p) return fail(SI_ERR_INVALID, "null params");
+  p->heavy_hits = kDefHeavyHits;
+  p->q_tile = kDefQTile;
+  p->branches = kDefBranches;
+  p->blocks_per_sm = kDefBlocksPerSm;
+  return SI_OK;
+}
+
 extern "C" si_status si_batch_create(const si_scene *scenes, int n_scenes, uint32_t flags,
                                      si_batch **out) {
+  return si_batch_create_params(scenes, n_scenes, flags, nullptr, out);
+}
+
+extern "C" si_status si_batch_create_params(const si_scene *scenes, int n_scenes, uint32_t flags,
+                                            const si_batch_params *params, si_batch **out) {
   if (!scenes || !out || n_scenes <= 0) return fail(SI_ERR_INVALID, "bad batch arguments");
   if (flags & ~(SI_METHOD_CUBE | SI_INCLUDE_SELF)) return fail(SI_ERR_INVALID, "unknown flags");
+  si_batch_params prm;
+  si_batch_default_params(&prm);
+  if (params) prm = *params;
+  if (!params_valid(prm)) return fail(SI_ERR_INVALID, "batch parameters out of range");
   *out = nullptr;
   si_batch *b = new (std::nothrow) si_batch();
   if (!b) return fail(SI_ERR_OOM, "host allocation failed");
+  b->params = prm;
   b->n_scenes = n_scenes;
   b->scenes.assign(scenes, scenes + n_scenes);
   b->flags = flags;
@@ -358,7 +390,7 @@ extern "C" si_status si_batch_create(const si_scene *scenes, int n_scenes, uint3
     // expected list length: load times the sphere's volume in cells
     const double dcell = (double)sc.r * lat.inv_s;
     const double hits = (double)sc.n / (double)(1ll << lat.W) * 4.0 / 3.0 * M_PI * dcell * dcell * dcell;
-    if (!(flags & SI_METHOD_CUBE) && sc.n > 0 && hits >= kBatchHeavyHits) {
+    if (!(flags & SI_METHOD_CUBE) && sc.n > 0 && hits >= (double)prm.heavy_hits) {
       si_grid_desc desc = sc.desc;
       desc.r_max = sc.r;
       si_grid *gr = nullptr;
@@ -414,7 +446,7 @@ extern "C" si_status si_batch_create(const si_scene *scenes, int n_scenes, uint3
     for (int64_t f = 0; f < sc.n; f += kBinTile) bin_items.push_back({fi, (int)f});
     // cost of one query tile: cells visited x (1 + load): heaviest first
     const double cells = 1.0 + 6.0 * d + 3.0 * M_PI * d * d + 4.0 / 3.0 * M_PI * d * d * d;
-    for (int64_t f = 0; f < sc.n; f += kQTile) q_items.push_back({{fi, (int)f}, cells * (1.0 + load)});
+    for (int64_t f = 0; f < sc.n; f += prm.q_tile) q_items.push_back({{fi, (int)f}, cells * (1.0 + load)});
     b->n_total += sc.n;
     b->cells_total += (1ll << lat.W) + 1;
   }
@@ -466,7 +498,7 @@ extern "C" si_status si_batch_create(const si_scene *scenes, int n_scenes, uint3
   if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_pinned, (n_scenes + 1) * sizeof(long long) * 2);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_status, std::max(n_fused, 1) * sizeof(int));
   // heavy scenes: heaviest first on the least-loaded branch
-  b->n_branches = std::min<int>(8, (int)b->heavy.size());
+  b->n_branches = std::min<int>(prm.branches, (int)b->heavy.size());
   {
     std::vector<size_t> order(b->heavy.size());
     std::iota(order.begin(), order.end(), 0);
@@ -525,13 +557,32 @@ static si_status batch_launches(si_batch *b, cudaStream_t st) {
                                                          b->start, b->spos, b->perm));
   }
   if (N == 0) return SI_OK;
-  const int grid = 148 * 8;
-  SI_KLAUNCH("k_batch_query count", st, k_batch_query<false><<<grid, kQTile, 0, st>>>(b->d_scenes, b->d_q_items, b->n_q_items, b->queues,
-                                               b->gcount, nullptr, b->longq, b->scene_status));
+  const int tile = b->params.q_tile;
+  const int grid = 148 * b->params.blocks_per_sm;
+  auto query = [&](bool write) -> si_status {
+    const char *name = write ? "k_batch_query write" : "k_batch_query count";
+    int *q = b->queues + (write ? 1 : 0);
+    long long *cnt = write ? nullptr : b->gcount;
+    const long long *scn = write ? b->gcount : nullptr;
+#define SI_BATCH_Q(W, T)                                                                                      \
+  SI_KLAUNCH(name, st, k_batch_query<W, T><<<grid, T, 0, st>>>(b->d_scenes, b->d_q_items, b->n_q_items, q, cnt, \
+                                                                scn, b->longq, b->scene_status))
+    if (write) {
+      if (tile == 64) SI_BATCH_Q(true, 64);
+      else if (tile == 256) SI_BATCH_Q(true, 256);
+      else SI_BATCH_Q(true, 128);
+    } else {
+      if (tile == 64) SI_BATCH_Q(false, 64);
+      else if (tile == 256) SI_BATCH_Q(false, 256);
+      else SI_BATCH_Q(false, 128);
+    }
+#undef SI_BATCH_Q
+    return SI_OK;
+  };
+  if ((s = query(false)) != SI_OK) return s;
   if ((s = scan_inclusive_i64(b->gcount, b->gcount, N, b->scan_i64, st)) != SI_OK) return s;
-  SI_KLAUNCH("k_batch_offsets", st, k_batch_offsets<<<b->n_q_items, kQTile, 0, st>>>(b->d_scenes, b->d_q_items, b->gcount));
-  SI_KLAUNCH("k_batch_query write", st, k_batch_query<true><<<grid, kQTile, 0, st>>>(b->d_scenes, b->d_q_items, b->n_q_items, b->queues + 1,
-                                              nullptr, b->gcount, b->longq, b->scene_status));
+  SI_KLAUNCH("k_batch_offsets", st, k_batch_offsets<<<b->n_q_items, tile, 0, st>>>(b->d_scenes, b->d_q_items, b->gcount));
+  if ((s = query(true)) != SI_OK) return s;
   SI_KLAUNCH("k_batch_sort", st, k_batch_sort<<<2 * 148, kBatchSortThreads, 0, st>>>(b->d_scenes, b->longq, b->scene_status));
   return SI_OK;
 }
@@ -655,5 +706,53 @@ extern "C" si_status si_batch_destroy(si_batch *b) {
   if (!b) return SI_OK;
   cudaDeviceSynchronize();
   batch_free(b);
+  return SI_OK;
+}
+
+// Planner tuning: each candidate batch is created, run once eagerly (tables,
+// scratch), captured, warmed by two replays and timed over `reps` replays
+// with CUDA events on a stream of its own (median); the candidates write the
+// scenes' outputs in turn.
+extern "C" si_status si_batch_tune(const si_scene *scenes, int n_scenes, uint32_t flags,
+                                   const si_batch_params *cands, int n_cand, int reps, float *h_ms,
+                                   int32_t *h_best) {
+  if (!cands || n_cand <= 0 || reps <= 0 || !h_ms || !h_best) return fail(SI_ERR_INVALID, "bad tuning arguments");
+  for (int i = 0; i < n_cand; ++i)
+    if (!params_valid(cands[i])) return fail(SI_ERR_INVALID, "candidate " + std::to_string(i) + " out of range");
+  cudaStream_t st;
+  SI_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  si_status s = e == cudaSuccess ? SI_OK : cuda_fail(e, "cudaEventCreate");
+  int best = -1;
+  for (int i = 0; s == SI_OK && i < n_cand; ++i) {
+    si_batch *b = nullptr;
+    if ((s = si_batch_create_params(scenes, n_scenes, flags, cands + i, &b)) != SI_OK) break;
+    s = si_batch_run(b, 1, st);
+    if (s == SI_OK) s = si_batch_sync(b, nullptr, st);
+    for (int w = 0; s == SI_OK && w < 2; ++w) s = si_batch_run(b, 1, st);
+    std::vector<float> ms;
+    for (int r = 0; s == SI_OK && r < reps; ++r) {
+      cudaEventRecord(e0, st);
+      s = si_batch_run(b, 1, st);
+      cudaEventRecord(e1, st);
+      if (s == SI_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) s = cuda_fail(e, "batch tuning");
+      float t = 0.f;
+      if (s == SI_OK) cudaEventElapsedTime(&t, e0, e1);
+      ms.push_back(t);
+    }
+    if (s == SI_OK) s = si_batch_sync(b, nullptr, st);
+    si_batch_destroy(b);
+    if (s != SI_OK) break;
+    std::sort(ms.begin(), ms.end());
+    h_ms[i] = ms[ms.size() / 2];
+    if (best < 0 || h_ms[i] < h_ms[best]) best = i;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  if (s != SI_OK) return s;
+  *h_best = best;
   return SI_OK;
 }

@@ -123,3 +123,34 @@ def test_full_size_256_scene_batch_sampled():
         assert o[-1] == totals[k]
         for t, qi in enumerate(q):
             assert np.array_equal(lst[o[qi]:o[qi + 1]], ids_o[off_o[t]:off_o[t + 1]]), (k, qi)
+
+
+def test_tuned_batch_matches_oracle_and_caches(tmp_path):
+    # the planner's choices timed on the GPU (a few candidates, including
+    # every scene fused and every scene on its own pipeline), the fastest
+    # kept in a cache file; the tuned batch's lists are the oracle's
+    import os
+    from paper_cs_0608108_b300 import tune_batch
+    scenes = synth.batched_scenes(12, seed=321, n_lo=500, n_hi=30_000)
+    ref = [oracle_radius(sc) for sc in scenes]
+    pos = [to_dev(s.pos) for s in scenes]
+    offs = [torch.empty(s.n + 1, dtype=torch.int64, device="cuda") for s in scenes]
+    ids = [torch.empty(int(o[-1]) + 1, dtype=torch.int32, device="cuda") for o, _ in ref]
+    cands = [{"heavy_hits": h, "q_tile": t, "branches": 4, "blocks_per_sm": 4}
+             for h, t in ((0.0, 128), (24.0, 64), (24.0, 256), (1e9, 128))]
+    cache = os.path.join(tmp_path, "tune.json")
+    params, info = tune_batch(list(zip(scenes, pos)), offs, ids, cache=cache, candidates=cands, reps=2)
+    assert not info["cached"] and len(info["ms"]) == 4 and params in cands
+    again, info2 = tune_batch(list(zip(scenes, pos)), offs, ids, cache=cache, candidates=cands)
+    assert info2["cached"] and again == params
+    for cand in (params, cands[0], cands[3]):
+        b = Batch(list(zip(scenes, pos)), offs, ids, params=cand)
+        for t in ids:
+            t.fill_(-7)
+        b.run(use_graph=True)
+        b.run(use_graph=True)
+        b.sync()
+        for k, (off_o, ids_o) in enumerate(ref):
+            o = offs[k].cpu().numpy()
+            assert_csr_equal(o, ids[k].cpu().numpy()[: o[-1]], off_o, ids_o)
+        b.close()
