@@ -606,15 +606,16 @@ si_status launch_cell_pass(const GridDev &g, const WalkParams &P, const Band &B,
 // queries of one cell, with no block-wide barrier, so that the latency of
 // each item's loads (its record, its queries' output positions) is hidden
 // by the other warps of the SM.  k_expand_plan lists the items: a cell
-// served by one record of at most kItemCap candidates gives ceil(nq / kItemQ)
-// of them; split cells and longer records go to k_cell_expand (a block per
-// cell).  A warp stages its item's ordered ids in its own shared rows (32
-// ids per row, rows padded to 33 words) and expands each query's masks as
-// k_cell_expand does.
+// served by one record gives ceil(nq / kItemQ) of them; split cells go to
+// k_cell_expand (a block per cell).  A warp goes through its item's
+// candidates a round of 32 chunks (1024 candidates) at a time: it stages
+// the round's ordered ids in its own shared rows (32 ids per row, rows
+// padded to 33 words), then expands that round's masks of each query as
+// k_cell_expand does, carrying each query's write position from round to
+// round in the register of lane t (query q0 + t).
 constexpr int kItemQ = 8;
-constexpr int kItemCap = 1280;
 constexpr int kItemWarps = 8;
-constexpr int kItemRows = kItemCap / 32;
+constexpr int kItemRows = 32;
 
 __global__ void __launch_bounds__(256) k_expand_plan(GridDev g, const int *__restrict__ heavy,
                                                      const long long *__restrict__ cell_rec,
@@ -625,7 +626,7 @@ __global__ void __launch_bounds__(256) k_expand_plan(GridDev g, const int *__res
     const long long ref = cell_rec[key];
     if (ref == -1) continue;   // served by the per-query path
     const int qs = __ldg(g.cell_start + key), nq = __ldg(g.cell_start + key + 1) - qs;
-    if (ref < -1 || __ldg(scratch + ref) > kItemCap) {
+    if (ref < -1) {
       blocks[1 + atomicAdd(blocks, 1)] = (int)key;
       continue;
     }
@@ -659,28 +660,29 @@ __global__ void __launch_bounds__(kItemWarps * 32) k_expand_items(GridDev g, con
     const int *rec_ids = scratch + rec + 1;
     const unsigned *rec_masks = reinterpret_cast<const unsigned *>(rec_ids + nc);
     // output positions of the item's queries (lane t: query q0 + t)
-    const long long wp = lane < cnt ? offsets[__ldg(g.perm + qs + q0 + lane)] : 0ll;
+    long long wp = lane < cnt ? offsets[__ldg(g.perm + qs + q0 + lane)] : 0ll;
     unsigned mnext = lane < nchunk ? __ldg(rec_masks + (long long)q0 * nchunk + lane) : 0u;
-    __syncwarp();   // the previous item's rows are no longer read
-    for (int k = lane; k < nc; k += 32) rows[(k >> 5) * 33 + (k & 31)] = __ldg(rec_ids + k);
-    __syncwarp();
-    for (int t = 0; t < cnt; ++t) {
-      const int ql = q0 + t;
-      long long wpos = __shfl_sync(0xffffffffu, wp, t);
-      const unsigned *mk = rec_masks + (long long)ql * nchunk;
-      for (int c0 = 0; c0 < nchunk; c0 += 32) {
+    for (int c0 = 0; c0 < nchunk; c0 += 32) {
+      __syncwarp();   // the previous round's (or item's) rows are no longer read
+      const int kend = min(nc, (c0 + 32) * 32);
+      for (int k = c0 * 32 + lane; k < kend; k += 32) rows[((k >> 5) - c0) * 33 + (k & 31)] = __ldg(rec_ids + k);
+      __syncwarp();
+      for (int t = 0; t < cnt; ++t) {
         const unsigned mm = mnext;
-        // prefetch: the rest of this query's masks, else the next query's first 32
-        if (c0 + 32 < nchunk) {
+        // prefetch: the next query's masks of this round, else the first
+        // query's masks of the next round
+        if (t + 1 < cnt) {
+          const int ch = c0 + lane;
+          mnext = ch < nchunk ? __ldg(rec_masks + (long long)(q0 + t + 1) * nchunk + ch) : 0u;
+        } else if (c0 + 32 < nchunk) {
           const int ch = c0 + 32 + lane;
-          mnext = ch < nchunk ? __ldg(mk + ch) : 0u;
-        } else if (t + 1 < cnt) {
-          mnext = lane < nchunk ? __ldg(mk + nchunk + lane) : 0u;
+          mnext = ch < nchunk ? __ldg(rec_masks + (long long)q0 * nchunk + ch) : 0u;
         }
+        const long long wpos = __shfl_sync(0xffffffffu, wp, t);
         const int c = __popc(mm);
         const int inc = warp_incl_scan_i(c);
         int o = inc - c;
-        const int *row = rows + (c0 + lane) * 33;   // read only where a bit is set
+        const int *row = rows + lane * 33;   // read only where a bit is set
 #pragma unroll
         for (int b = 0; b < 32; ++b) {
           const bool set = (mm >> b) & 1u;
@@ -691,7 +693,7 @@ __global__ void __launch_bounds__(kItemWarps * 32) k_expand_items(GridDev g, con
         const int tot = __shfl_sync(0xffffffffu, inc, 31);
         for (int i = lane; i < tot; i += 32) ids[wpos + i] = buf[i];
         __syncwarp();
-        wpos += tot;
+        if (lane == t) wp += tot;
       }
     }
   }
