@@ -604,6 +604,10 @@ def make_work(name):
             "same, GPU bin-lattice cube scan"
     if name == "knn_4m":
         return KnnWork(synth.knn_4m_scene()), "4M-point K-nearest (K=16 and 64), 256^3, cyclic x,y, r_max=4 cells"
+    if name == "knn_250k":
+        return KnnWork(synth.knn_250k_scene()), \
+            "250k-point K-nearest (K=16 and 64) at the 4M configuration's density, 128x128x64, cyclic x,y, " \
+            "r_max=4 cells"
     if name == "walk_1m":
         return WalkWork(synth.uniform_1m_scene()), \
             "1M-point random walk step: rebin + energy + adjoint, 128^3 cyclic, r=1.5 cells"
@@ -825,6 +829,8 @@ def _oracle_scene(name):
         return synth.mixture_1m_scene()
     if name == "knn_4m":
         return synth.knn_4m_scene()
+    if name == "knn_250k":
+        return synth.knn_250k_scene()
     if name == "radius_far_20k":
         return make_work_scene_far()
     if name in ("terrain_1m", "terrain_1m_planes"):

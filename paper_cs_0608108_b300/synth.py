@@ -202,6 +202,14 @@ def knn_4m_scene(n: int = 4_000_000, seed: int = SEEDS["knn_4m"]) -> Scene:
                  4.0 / 256, "knn_4m", {"k": (16, 64)})
 
 
+def knn_250k_scene(n: int = 250_000, seed: int = SEEDS["knn_4m"]) -> Scene:
+    """The 4M K-nearest configuration's density on a sixteenth of its
+    region: 250k uniform points, cell side 1/256, 128 x 128 x 64 cells
+    (load 0.238), cyclic in x and y, r_max = 4 cells; for profiling."""
+    return Scene(uniform_points(n, seed, box=(0.5, 0.5, 0.25)), (0.0, 0.0, 0.0), 1.0 / 256, (7, 7, 6), 3,
+                 4.0 / 256, "knn_250k", {"k": (16, 64)})
+
+
 def batched_scenes(n_scenes: int = 256, seed: int = SEEDS["batched"],
                    n_lo: int = 1_000, n_hi: int = 200_000) -> list:
     """Independent scenes of uneven size: n log-uniform in [n_lo, n_hi], box side
