@@ -113,7 +113,11 @@ si_status scan_inclusive_i64(const long long *in, long long *out, int64_t n, lon
 Band make_band(const Lattice &lat, float r);
 // Band coefficients for comparing two FP32 squared distances (KNN order).
 struct PairBand {
-  float c2, c1;        // |d2f - D2| <= c2 * d2 + c1 * sqrt(d2)
+  // two FP32 squared distances of one query further apart than
+  // c2 * d2 + c1 * sqrt(d2) are in the order of their canonical FP64 values;
+  // the c1 term (the rounding of a coordinate shifted by a box side) is
+  // needed only when one of them came through a wrapped image
+  float c2, c1;
 };
 PairBand make_pair_band(const Lattice &lat);
 

@@ -221,14 +221,106 @@ __device__ __forceinline__ double canon_gap(float a, float b, float L, bool cycl
   return d;
 }
 
-__device__ __forceinline__ double canon_d2(const float4 &q, const float4 &p, const GridDev &g) {
-  const double ax = canon_gap(q.x, p.x, g.Lx, g.cyc & 1u);
-  const double ay = canon_gap(q.y, p.y, g.Ly, (g.cyc >> 1) & 1u);
-  const double az = canon_gap(q.z, p.z, g.Lz, (g.cyc >> 2) & 1u);
+__device__ __forceinline__ double canon_d2_raw(const float4 &q, const float4 &p, float Lx, float Ly, float Lz,
+                                               unsigned cyc) {
+  const double ax = canon_gap(q.x, p.x, Lx, cyc & 1u);
+  const double ay = canon_gap(q.y, p.y, Ly, (cyc >> 1) & 1u);
+  const double az = canon_gap(q.z, p.z, Lz, (cyc >> 2) & 1u);
   double s = __dmul_rn(ax, ax);
   s = __dadd_rn(s, __dmul_rn(ay, ay));
   s = __dadd_rn(s, __dmul_rn(az, az));
   return s;
+}
+__device__ __forceinline__ double canon_d2(const float4 &q, const float4 &p, const GridDev &g) {
+  return canon_d2_raw(q, p, g.Lx, g.Ly, g.Lz, g.cyc);
+}
+// The same value behind a real call: for rare uses inside hot loops, where
+// an inlined copy would be predicated and issue its FP64 instructions (at a
+// small fraction of the FP32 rate on this GPU) for every warp.
+static __device__ __noinline__ double canon_d2_call(float4 q, float4 p, float Lx, float Ly, float Lz, unsigned cyc) {
+  return canon_d2_raw(q, p, Lx, Ly, Lz, cyc);
+}
+
+// ---------------------------------------------------------------------------
+// The FP32 rounding of canon_d2, mostly without FP64 (the FP64 pipe of this
+// GPU is slow).  The exact squared distance E of the two points is formed as
+// an unevaluated sum H + lo of two floats by error-free transformations
+// (Knuth's TwoSum, Dekker's Fast2Sum, the rounding error of a product by one
+// fused multiply-add): each axis gap exactly as a float pair (its cyclic
+// image L - gap exactly too, by Sterbenz's lemma, wherever it is the shorter
+// one), its square to within 2^-45 relative, the sum of the three to within
+// 2^-43 (every term is >= 0: no cancellation).  canon_d2 differs from E by a
+// few FP64 roundings (under 2^-49 relative).  H is the float nearest to
+// H + lo; the float nearest to canon_d2 is H as well unless H + lo lies
+// within 2^-40 H of the midpoint between H and its neighbour on lo's side,
+// and those distances (about one in 2^15) take canon_d2 itself, as do
+// coordinates outside a cyclic box (gap > L), values below 2^-70 (where
+// flushed subnormals could matter) or above 2^120.  The result equals
+// __double2float_rn(canon_d2(q, p, g)) for every pair.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {   // |a| >= |b|
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// Gap of one axis as a float pair (h, l), h + l = |b - a| exactly (or the
+// shorter way round a cyclic axis), then its square as a float pair (sh, sl);
+// false for a cyclic gap longer than L.
+__device__ __forceinline__ bool gap_sq(float a, float b, float L, bool cyclic, float &sh, float &sl) {
+  float s, t;
+  two_sum(b, -a, s, t);
+  float h = fabsf(s), l = s < 0.f ? -t : t;
+  if (cyclic) {
+    if (!(h <= L)) return false;
+    float u, v;
+    two_sum(L, -h, u, v);   // v = 0 whenever h >= L / 2
+    float wh, wl;
+    fast_two_sum(u, __fsub_rn(v, l), wh, wl);
+    if (wh < h || (wh == h && wl < l)) {   // both pairs normalised: lexicographic order is the order of the sums
+      h = wh;
+      l = wl;
+    }
+  }
+  sh = __fmul_rn(h, h);
+  float e = __fmaf_rn(h, h, -sh);
+  e = __fmaf_rn(__fmul_rn(2.f, h), l, e);
+  sl = __fmaf_rn(l, l, e);
+  return true;
+}
+// true with v = the FP32 rounding of canon_d2 when the FP32 form settles
+// it; false (v unset) for the pairs that need canon_d2 itself
+__device__ __forceinline__ bool canon_d2_f32_try(const float4 &q, const float4 &p, const GridDev &g, float &v) {
+  if (q.x == p.x && q.y == p.y && q.z == p.z) {   // every gap exactly 0
+    v = 0.f;
+    return true;
+  }
+  float xh, xl, yh, yl, zh, zl;
+  const bool ok = gap_sq(q.x, p.x, g.Lx, g.cyc & 1u, xh, xl) & gap_sq(q.y, p.y, g.Ly, (g.cyc >> 1) & 1u, yh, yl) &
+                  gap_sq(q.z, p.z, g.Lz, (g.cyc >> 2) & 1u, zh, zl);
+  float s, e, H, lo;
+  two_sum(xh, yh, s, e);
+  fast_two_sum(s, __fadd_rn(e, __fadd_rn(xl, yl)), H, lo);
+  two_sum(H, zh, s, e);
+  fast_two_sum(s, __fadd_rn(e, __fadd_rn(lo, zl)), H, lo);
+  if (ok && H >= 0x1p-70f && H <= 0x1p120f) {
+    // half the gap from H to its neighbour on lo's side (exact; H is a
+    // positive normal float, so its neighbours are one encoding step away)
+    const unsigned hb = __float_as_uint(H);
+    const float m = 0.5f * (lo >= 0.f ? __fsub_rn(__uint_as_float(hb + 1u), H) : __fsub_rn(H, __uint_as_float(hb - 1u)));
+    if (__fsub_rn(m, fabsf(lo)) > H * 0x1p-40f) {
+      v = H;
+      return true;
+    }
+  }
+  return false;
+}
+__device__ __forceinline__ float canon_d2_f32(const float4 &q, const float4 &p, const GridDev &g) {
+  float v;
+  return canon_d2_f32_try(q, p, g, v) ? v : __double2float_rn(canon_d2(q, p, g));
 }
 
 // ---------------------------------------------------------------------------

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(GridDev g, int K, float dma
     const bool fast = flags & SI_FAST_D2;
     for (int k = 0; k < K; ++k)
       od[k] = k >= cnt ? __int_as_float(0x7f800000)
-                       : (fast ? L.d[L.at(k)] : __double2float_rn(canon_d2(Q.q, g.spos[L.j[L.at(k)]], g)));
+                       : (fast ? L.d[L.at(k)] : canon_d2_f32(Q.q, g.spos[L.j[L.at(k)]], g));
   }
   out_counts[orig] = cnt;
 }
@@ -238,7 +238,7 @@ struct KnnRuns {                  // up to two runs per row of a 32-row batch
 // (the K nearest then all lie within it); else a second pass within r_max
 // (dmax_g, n_query, B).  dmax1 == dmax_g: one pass.  list (nullable): [0] =
 // count, then the sorted slots to serve; else every slot.
-__global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, float dmax_g, int n_query,
+__global__ void __launch_bounds__(kKnnWarps * 32, 4) k_knn_warp(GridDev g, int K, float dmax_g, int n_query,
                                                             Band B, float dmax1, int n1, Band B1,
                                                             PairBand pb, unsigned flags,
                                                             int *__restrict__ out_ids,
@@ -265,10 +265,14 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, f
   const bool cyc_x = g.cyc & 1u;
   int cnt = 0;
   bool overflow = false, out_any = false;
-  auto add = [&](bool in, float d, int j) {
+  // key: FP32 d2 above, then bit 31 set for a candidate compared through a
+  // wrapped image (its FP32 value carries the absolute error term of the
+  // pair bound), then the sorted slot
+  auto add = [&](bool in, float d, int j, bool wr) {
     const unsigned m = __ballot_sync(0xffffffffu, in);
     const int at = cnt + __popc(m & lt);
-    if (in && at < kKnnCap) key[at] = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)j;
+    if (in && at < kKnnCap)
+      key[at] = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)j | (wr ? 0x80000000u : 0u);
     cnt += __popc(m);
   };
   // every candidate within the cut (cut2 = its square in cell units, n_q its
@@ -350,9 +354,10 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, f
     __syncwarp();
     const int total = __shfl_sync(0xffffffffu, inc, 31);
     for (int f = lane; f - lane < total; f += 32) {
-      bool in = false;
+      bool in = false, band = false, wr = false;
       float d = 0.f;
       int j = 0;
+      float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
       if (f < total) {
         int L = 0;
 #pragma unroll
@@ -366,15 +371,21 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, f
         }
         j = R.b[slot] + off;
         if (j != self) {
-          const float4 p = g.spos[j];
+          p = g.spos[j];
           const float dx = p.x - R.qx[slot], dy = p.y - R.qy[slot], dz = p.z - R.qz[slot];
           d = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-          const bool wr = R.wrapped[slot];
+          wr = R.wrapped[slot];
           const float blo = wr ? B.lo_w : B.lo, bhi = wr ? B.hi_w : B.hi;
-          in = d <= blo || (!(d > bhi) && canon_d2(Q.q, p, g) <= B.r2);
+          in = d <= blo;
+          band = !in && !(d > bhi);
         }
       }
-      add(in, d, j);
+      // the guard band in FP64, behind a warp-uniform branch: FP64 issues
+      // only when some lane needs it (rare), never predicated for all
+      if (__any_sync(0xffffffffu, band)) {
+        if (band) in = canon_d2_call(Q.q, p, g.Lx, g.Ly, g.Lz, g.cyc) <= B.r2;
+      }
+      add(in, d, j, wr);
     }
     __syncwarp();   // the next batch rewrites R
     if (cnt > kKnnCap) overflow = true;
@@ -391,13 +402,18 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, f
         in = D <= B.r2;
         d = (float)D;
       }
-      add(in, d, j);
+      add(in, d, j, false);
     }
     if (cnt > kKnnCap) overflow = true;
   }
   };
-  gather(dmax1 * dmax1, n1, B1);
-  if (!overflow && cnt < K && dmax1 < dmax_g) gather(dmax_g * dmax_g, n_query, B);
+  // one call site, so the gather inlines: the first pass, then the second
+  // when the first held fewer than K
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1 && (overflow || cnt >= K || !(dmax1 < dmax_g))) break;
+    const float dm = pass ? dmax_g : dmax1;
+    gather(dm * dm, pass ? n_query : n1, pass ? B : B1);
+  }
   if (overflow) {   // the per-thread kernel takes it
     if (lane == 0) fallq[1 + atomicAdd(fallq, 1)] = s;
     return;
@@ -406,40 +422,40 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, f
   warp_sort(key, cnt, lane, ~0ull);
   __syncwarp();
   // runs of keys closer than the FP32 error bound, up to the K-th (and the
-  // first one past it, which decides who is in), in canonical order
+  // first one past it, which decides who is in), in canonical order.  Two
+  // FP32 values further apart than both their bounds are in canonical order
+  // already; the absolute term of the bound applies only when one of them
+  // came through a wrapped image (the rounding of q + L), otherwise each is
+  // within a relative c2 / 2 of its canonical value.
+  auto close = [&](unsigned long long xa, unsigned long long xb) {
+    const float da = __uint_as_float((unsigned)(xa >> 32));
+    const float db = __uint_as_float((unsigned)(xb >> 32));
+    const float m = db * 1.000001f;
+    const bool wr = ((unsigned)xa | (unsigned)xb) >> 31;
+    return !(db - da > fmaf(pb.c2, m, wr ? pb.c1 * sqrtf(m) : 0.f) + 1e-37f);
+  };
   const int top = min(cnt, K + 1);
   bool ties = false;   // an adjacent pair within the bound, up to the (K+1)-th
   for (int e0 = 1; e0 < min(top + 1, cnt); e0 += 32) {
     const int e = e0 + lane;
     bool t = false;
-    if (e < min(top + 1, cnt)) {
-      const float da = __uint_as_float((unsigned)(key[e - 1] >> 32));
-      const float db = __uint_as_float((unsigned)(key[e] >> 32));
-      const float m = db * 1.000001f;
-      t = !(db - da > fmaf(pb.c2, m, pb.c1 * sqrtf(m)) + 1e-37f);
-    }
+    if (e < min(top + 1, cnt)) t = close(key[e - 1], key[e]);
     ties |= __any_sync(0xffffffffu, t);
   }
   if (ties && lane == 0) {
     int a = 0;
     while (a < top) {
       int e = a + 1;
-      while (e < cnt) {
-        const float da = __uint_as_float((unsigned)(key[e - 1] >> 32));
-        const float db = __uint_as_float((unsigned)(key[e] >> 32));
-        const float m = db * 1.000001f;
-        if (db - da > fmaf(pb.c2, m, pb.c1 * sqrtf(m)) + 1e-37f) break;
-        ++e;
-      }
+      while (e < cnt && close(key[e - 1], key[e])) ++e;
       if (e - a > 1) {   // insertion sort of [a, e) by (D2, index)
         for (int i = a + 1; i < e; ++i) {
           const unsigned long long x = key[i];
-          const int jx = (int)(x & 0xffffffffu);
+          const int jx = (int)(x & 0x7fffffffu);
           const double Dx = canon_d2(Q.q, g.spos[jx], g);
           const int ix = __ldg(g.perm + jx);
           int p = i;
           while (p > a) {
-            const int jy = (int)(key[p - 1] & 0xffffffffu);
+            const int jy = (int)(key[p - 1] & 0x7fffffffu);
             const double Dy = canon_d2(Q.q, g.spos[jy], g);
             if (Dy < Dx || (Dy == Dx && __ldg(g.perm + jy) < ix)) break;
             key[p] = key[p - 1];
@@ -456,16 +472,31 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn_warp(GridDev g, int K, f
   const int orig = __ldg(g.qid + s);
   int *oi = out_ids + (size_t)orig * K;
   float *od = out_d2 ? out_d2 + (size_t)orig * K : nullptr;
-  for (int k = lane; k < K; k += 32) {
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    const int k = k0 + lane;
     const bool have = k < kept;
     const unsigned long long x = have ? key[k] : 0ull;
-    oi[k] = have ? __ldg(g.perm + (int)(x & 0xffffffffu)) : -1;
+    if (k < K) oi[k] = have ? __ldg(g.perm + (int)(x & 0x7fffffffu)) : -1;
     // the FP32 rounding of the canonical FP64 D2 of each reported neighbor,
-    // or (SI_FAST_D2) the FP32 value the kernel sorted by
-    if (od)
-      od[k] = !have ? __int_as_float(0x7f800000)
-                    : ((flags & SI_FAST_D2) ? __uint_as_float((unsigned)(x >> 32))
-                                            : __double2float_rn(canon_d2(Q.q, g.spos[(int)(x & 0xffffffffu)], g)));
+    // or (SI_FAST_D2) the FP32 value the kernel sorted by; the rare pairs
+    // the FP32 form cannot settle take FP64 behind a call
+    if (od) {
+      float v = __int_as_float(0x7f800000);
+      bool hard = false;
+      float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (have) {
+        if (flags & SI_FAST_D2) {
+          v = __uint_as_float((unsigned)(x >> 32));
+        } else {
+          p = g.spos[(int)(x & 0x7fffffffu)];
+          hard = !canon_d2_f32_try(Q.q, p, g, v);
+        }
+      }
+      if (__any_sync(0xffffffffu, hard)) {
+        if (hard) v = __double2float_rn(canon_d2_call(Q.q, p, g.Lx, g.Ly, g.Lz, g.cyc));
+      }
+      if (k < K) od[k] = v;
+    }
   }
   if (lane == 0) out_counts[orig] = kept;
 }
