@@ -491,7 +491,8 @@ class KnnWork:
     def algorithmic_bytes(self):
         n, C = self.scene.n, (1 << sum(self.scene.log2_cells)) + 1
         kb = float(np.mean([16 * n + 4 * n + 4 * C + 8 * k * n + 4 * n for k in self.ks]))
-        return {"k_knn": kb, "k_bin_key": 24 * n + 8 * C, "k_bin_scatter": 48 * n + 4 * C}
+        return {"k_knn_lane": kb, "k_knn_warp": kb, "k_knn": kb, "k_bin_key": 24 * n + 8 * C,
+                "k_bin_scatter": 48 * n + 4 * C}
 
     def step_bytes(self):
         n, C = self.scene.n, (1 << sum(self.scene.log2_cells)) + 1

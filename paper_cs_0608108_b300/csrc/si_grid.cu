@@ -243,6 +243,9 @@ bool build_tables(const int w[3], unsigned cyc, int n_max, HostTables &out, std:
       e.b2 = r.b2;
       out.rows.push_back(e);
     }
+    out.row_end.assign((size_t)n_max + 1, 0);
+    for (const RowRaw &r : rr) ++out.row_end[(size_t)r.b2];
+    for (int n = 1; n <= n_max; ++n) out.row_end[(size_t)n] += out.row_end[(size_t)n - 1];
     out.row_lim_x = lim[0];
   }
   // Specialized tables: for shell fl (fl^2 <= b2 < (fl+1)^2) and the 6-bit
@@ -295,6 +298,7 @@ si_status upload_tables(const HostTables &h, DevTables &d) {
   if ((s = upload(h.spec_end, d.spec_end)) != SI_OK) return s;
   if ((s = upload(h.rows, d.rows)) != SI_OK) return s;
   d.n_rows = (int)h.rows.size();
+  d.row_end = h.row_end;
   d.row_lim_x = h.row_lim_x;
   d.n_max = h.n_max;
   d.spec_shells = h.spec_shells;

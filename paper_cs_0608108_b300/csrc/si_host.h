@@ -58,6 +58,7 @@ struct HostTables {
   int n_max = 0;
   int spec_shells = 0;
   std::vector<RowEntry> rows;      // x-rows of the sphere, by b2 of their y-z offset
+  std::vector<int> row_end;        // row_end[n] = rows with b2 <= n, n = 0..n_max
   int row_lim_x = 0;
 };
 
@@ -78,6 +79,7 @@ struct DevTables {
   int *spec_begin = nullptr;
   int *spec_end = nullptr;
   RowEntry *rows = nullptr;
+  std::vector<int> row_end;        // host copy: row_end[n] = rows with b2 <= n
   int n_max = 0, spec_shells = 0, n_rows = 0, row_lim_x = 0;
   int64_t entries = 0;
 };

@@ -8,17 +8,21 @@
 // FP64, so the kept set and its order are exact while almost every
 // comparison stays in FP32.
 //
-// Two kernels.  With a bounded r_max, k_knn_warp serves a query with one
-// warp: the x-rows of the r_max sphere (rows of cells whose y-z bound is
-// within r_max, each cut to the x-interval the query's exact y-z distance
-// allows) are decoded by the lanes in parallel, every candidate within r_max
-// (the exact predicate) goes to the warp's shared buffer as an FP32 key, and
-// a warp bitonic sort orders the buffer; runs of adjacent keys closer than
-// the FP32 error bound are then put in canonical order.  r_max is the cut
-// here from the start: on these workloads it is close to the K-th distance,
-// so shrinking it saves little.  k_knn, one thread per query with the
-// shrinking cut described above, serves unbounded r_max, query points outside
-// the region and queries whose candidates overflow the warp's buffer.
+// Three kernels.  With a bounded r_max and K <= kLaneKMax, k_knn_lane serves
+// a query with one thread: the lanes of a warp hold neighbouring queries and
+// walk the same x-rows of the sphere (rows of cells whose y-z bound is within
+// the cut, each cut to the x-interval the query's exact y-z distance allows)
+// in step, keeping the K + 1 smallest FP32 distances and shrinking the cut
+// as described above.  For larger K, and for the queries whose K-th
+// neighbour the lane kernel's list cannot settle, k_knn_warp serves a query
+// with one warp: the lanes decode 32 x-rows at a time, every candidate
+// within the cut (the exact predicate) goes to the warp's shared buffer as an
+// FP32 key, and a warp bitonic sort orders the buffer.  Both take a first
+// cut expected to hold a little more than K points and widen it to r_max
+// when it holds fewer; runs of adjacent values closer than the FP32 error
+// bound are put in canonical order.  k_knn, one thread per query with the
+// shrinking cut from r_max, serves unbounded r_max, query points outside the
+// region and queries whose candidates overflow the warp's buffer.
 #include <cmath>
 
 #include "si_host.h"
@@ -225,35 +229,20 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(GridDev g, int K, float dma
 constexpr int kKnnWarps = 8;      // warps per block of k_knn_warp
 constexpr int kKnnCap = 512;      // candidates a warp holds
 
-struct KnnRuns {                  // up to two runs per row of a 32-row batch
-  int b[64];
-  int len[64];
-  float qx[64], qy[64], qz[64];
-  unsigned char wrapped[64];
-  int pre[33];
-};
-
-// First pass within dmax1 (n1, B1: its table bound and guard band), a radius
-// expected to hold about K + 2 sqrt(K) + 4 points: exact whenever it holds at least K
-// (the K nearest then all lie within it); else a second pass within r_max
-// (dmax_g, n_query, B).  dmax1 == dmax_g: one pass.  list (nullable): [0] =
+// First pass within dmax1 (rows1, B1: the x-rows whose y-z bound is within
+// it and its guard band), a radius expected to hold about K + 2 sqrt(K) + 4
+// points: exact whenever it holds at least K (the K nearest then all lie
+// within it); else a second pass within r_max (dmax_g, rows_q, B).  dmax1 ==
+// dmax_g: one pass.  list (nullable): [0] =
 // count, then the sorted slots to serve; else every slot.
-__global__ void __launch_bounds__(kKnnWarps * 32, 4) k_knn_warp(GridDev g, int K, float dmax_g, int n_query,
-                                                            Band B, float dmax1, int n1, Band B1,
-                                                            PairBand pb, unsigned flags,
-                                                            int *__restrict__ out_ids,
-                                                            float *__restrict__ out_d2,
-                                                            int *__restrict__ out_counts,
-                                                            int *__restrict__ fallq,
-                                                            const int *__restrict__ list) {
-  __shared__ unsigned long long keys[kKnnWarps][kKnnCap];
-  __shared__ KnnRuns runs[kKnnWarps];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int item = blockIdx.x * kKnnWarps + w;
-  if (item >= (list ? list[0] : g.n)) return;
-  const int s = list ? list[1 + item] : item;   // the warp's query (sorted slot)
-  unsigned long long *key = keys[w];
-  KnnRuns &R = runs[w];
+// One query (sorted slot s) served by the calling warp; key is the warp's
+// candidate buffer (kKnnCap keys).
+__device__ __forceinline__ void knn_warp_query(const GridDev &g, int s, unsigned long long *key, int K,
+                                               float dmax_g, int rows_q, const Band &B, float dmax1, int rows1,
+                                               const Band &B1, const PairBand &pb, unsigned flags,
+                                               int *__restrict__ out_ids, float *__restrict__ out_d2,
+                                               int *__restrict__ out_counts, int *__restrict__ fallq) {
+  const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const QueryGeom Q = make_geom(g.qpos[s], g);
   if (Q.outside) {   // the bounding-cube walk of the per-thread kernel
@@ -275,121 +264,89 @@ __global__ void __launch_bounds__(kKnnWarps * 32, 4) k_knn_warp(GridDev g, int K
       key[at] = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)j | (wr ? 0x80000000u : 0u);
     cnt += __popc(m);
   };
-  // every candidate within the cut (cut2 = its square in cell units, n_q its
-  // table bound, Bc its guard band), decided exactly, into the buffer
-  auto gather = [&](float cut2, int n_query, const Band &B) {
+  // every candidate within the cut (cut2 = its square in cell units, nrows
+  // the rows whose y-z bound is within it, Bc its guard band), decided
+  // exactly, into the buffer.  Lane i takes row base + i of a 32-row batch:
+  // its x-interval of cells is one run of sorted points (and a second run
+  // where it wraps a cyclic x axis), which the lane then walks point by
+  // point while any lane of the warp has points left.
+  auto gather = [&](float cut2, int nrows, const Band &B) {
   cnt = 0;
   overflow = false;
   out_any = false;
-  for (int base = 0; base < g.n_rows && !overflow; base += 32) {
+  for (int base = 0; base < nrows && !overflow; base += 32) {
     const int r = base + lane;
     int b0 = 0, l0 = 0, b1 = 0, l1 = 0;
     float qx0 = 0.f, qy0 = 0.f, qz0 = 0.f, qx1 = 0.f;
-    bool w0 = false, out = false, live = false;
-    if (r < g.n_rows) {
+    bool w0 = false, out = false;
+    if (r < nrows) {
       const RowEntry E = g.rows[r];
-      live = E.b2 <= n_query && (float)E.b2 <= cut2;   // rows are sorted by b2
-      if (live) {
-        const float ty = E.oy > 0 ? (float)(E.oy - 1) + Q.zp[1] : (E.oy < 0 ? (float)(-E.oy - 1) + Q.zn[1] : 0.f);
-        const float tz = E.oz > 0 ? (float)(E.oz - 1) + Q.zp[2] : (E.oz < 0 ? (float)(-E.oz - 1) + Q.zn[2] : 0.f);
-        const float rem = cut2 - fmaf(ty, ty, tz * tz);
-        if (rem >= 0.f) {
-          const float h = sqrtf(rem) + g.eps;
-          const int lo = max((int)floorf(Q.u[0] - h) - Q.c[0], -g.row_lim_x);
-          const int hi = min((int)floorf(Q.u[0] + h) - Q.c[0], g.row_lim_x);
-          if (lo <= hi) {
-            const Target tg = translate_raw(E.unp, Q, g);
-            if (tg.outside) {
-              out = true;
-            } else {
-              const unsigned row = tg.key - (unsigned)Q.c[0];
-              int x0 = Q.c[0] + lo, x1 = Q.c[0] + hi;
-              qx0 = tg.qx;
-              qy0 = tg.qy;
-              qz0 = tg.qz;
-              w0 = tg.wrapped;
-              if (!cyc_x) {
-                if (x0 < 0 || x1 >= Gx) out = true;
-                x0 = max(x0, 0);
-                x1 = min(x1, Gx - 1);
-              } else if (x0 < 0 || x1 >= Gx) {
-                const int wa = x0 < 0 ? x0 + Gx : 0, wb = x0 < 0 ? Gx - 1 : x1 - Gx;
-                b1 = __ldg(g.cell_start + row + wa);
-                l1 = __ldg(g.cell_start + row + wb + 1) - b1;
-                qx1 = Q.q.x + (x0 < 0 ? g.Lx : -g.Lx);
-                x0 = max(x0, 0);
-                x1 = min(x1, Gx - 1);
-              }
-              if (x0 <= x1) {
-                b0 = __ldg(g.cell_start + row + x0);
-                l0 = __ldg(g.cell_start + row + x1 + 1) - b0;
-              }
+      const float ty = E.oy > 0 ? (float)(E.oy - 1) + Q.zp[1] : (E.oy < 0 ? (float)(-E.oy - 1) + Q.zn[1] : 0.f);
+      const float tz = E.oz > 0 ? (float)(E.oz - 1) + Q.zp[2] : (E.oz < 0 ? (float)(-E.oz - 1) + Q.zn[2] : 0.f);
+      const float rem = cut2 - fmaf(ty, ty, tz * tz);
+      if (rem >= 0.f) {
+        const float h = sqrtf(rem) + g.eps;
+        const int lo = max((int)floorf(Q.u[0] - h) - Q.c[0], -g.row_lim_x);
+        const int hi = min((int)floorf(Q.u[0] + h) - Q.c[0], g.row_lim_x);
+        if (lo <= hi) {
+          const Target tg = translate_raw(E.unp, Q, g);
+          if (tg.outside) {
+            out = true;
+          } else {
+            const unsigned row = tg.key - (unsigned)Q.c[0];
+            int x0 = Q.c[0] + lo, x1 = Q.c[0] + hi;
+            qx0 = tg.qx;
+            qy0 = tg.qy;
+            qz0 = tg.qz;
+            w0 = tg.wrapped;
+            if (!cyc_x) {
+              if (x0 < 0 || x1 >= Gx) out = true;
+              x0 = max(x0, 0);
+              x1 = min(x1, Gx - 1);
+            } else if (x0 < 0 || x1 >= Gx) {
+              const int wa = x0 < 0 ? x0 + Gx : 0, wb = x0 < 0 ? Gx - 1 : x1 - Gx;
+              b1 = __ldg(g.cell_start + row + wa);
+              l1 = __ldg(g.cell_start + row + wb + 1) - b1;
+              qx1 = Q.q.x + (x0 < 0 ? g.Lx : -g.Lx);
+              x0 = max(x0, 0);
+              x1 = min(x1, Gx - 1);
+            }
+            if (x0 <= x1) {
+              b0 = __ldg(g.cell_start + row + x0);
+              l0 = __ldg(g.cell_start + row + x1 + 1) - b0;
             }
           }
         }
       }
     }
     out_any |= __any_sync(0xffffffffu, out);
-    const bool more = __any_sync(0xffffffffu, live);
-    R.b[2 * lane] = b0;
-    R.len[2 * lane] = l0;
-    R.qx[2 * lane] = qx0;
-    R.qy[2 * lane] = qy0;
-    R.qz[2 * lane] = qz0;
-    R.wrapped[2 * lane] = w0 ? 1 : 0;
-    R.b[2 * lane + 1] = b1;
-    R.len[2 * lane + 1] = l1;
-    R.qx[2 * lane + 1] = qx1;
-    R.qy[2 * lane + 1] = qy0;
-    R.qz[2 * lane + 1] = qz0;
-    R.wrapped[2 * lane + 1] = 1;
-    int inc = l0 + l1;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += v;
-    }
-    R.pre[lane + 1] = inc;
-    if (lane == 0) R.pre[0] = 0;
-    __syncwarp();
-    const int total = __shfl_sync(0xffffffffu, inc, 31);
-    for (int f = lane; f - lane < total; f += 32) {
+    const int nt = l0 + l1;
+    for (int k = 0; __any_sync(0xffffffffu, k < nt); ++k) {
       bool in = false, band = false, wr = false;
       float d = 0.f;
       int j = 0;
       float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (f < total) {
-        int L = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1)
-          if (R.pre[L + step] <= f) L += step;
-        int off = f - R.pre[L];
-        int slot = 2 * L;
-        if (off >= R.len[slot]) {
-          off -= R.len[slot];
-          ++slot;
-        }
-        j = R.b[slot] + off;
+      if (k < nt) {
+        const bool second = k >= l0;   // the run through the x wrap
+        j = second ? b1 + (k - l0) : b0 + k;
+        wr = second || w0;
         if (j != self) {
           p = g.spos[j];
-          const float dx = p.x - R.qx[slot], dy = p.y - R.qy[slot], dz = p.z - R.qz[slot];
+          const float dx = p.x - (second ? qx1 : qx0), dy = p.y - qy0, dz = p.z - qz0;
           d = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-          wr = R.wrapped[slot];
           const float blo = wr ? B.lo_w : B.lo, bhi = wr ? B.hi_w : B.hi;
           in = d <= blo;
           band = !in && !(d > bhi);
         }
       }
-      // the guard band in FP64, behind a warp-uniform branch: FP64 issues
-      // only when some lane needs it (rare), never predicated for all
+      // the guard band in FP64, behind a warp-uniform branch and a real
+      // call: FP64 issues only when some lane needs it (rare)
       if (__any_sync(0xffffffffu, band)) {
         if (band) in = canon_d2_call(Q.q, p, g.Lx, g.Ly, g.Lz, g.cyc) <= B.r2;
       }
       add(in, d, j, wr);
     }
-    __syncwarp();   // the next batch rewrites R
     if (cnt > kKnnCap) overflow = true;
-    if (!more) break;   // every later row lies beyond r_max
   }
   if (out_any && !overflow) {   // the outside cell: every pair in FP64
     const int b = __ldg(g.cell_start + g.outside), e = __ldg(g.cell_start + g.outside + 1);
@@ -412,7 +369,7 @@ __global__ void __launch_bounds__(kKnnWarps * 32, 4) k_knn_warp(GridDev g, int K
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1 && (overflow || cnt >= K || !(dmax1 < dmax_g))) break;
     const float dm = pass ? dmax_g : dmax1;
-    gather(dm * dm, pass ? n_query : n1, pass ? B : B1);
+    gather(dm * dm, pass ? rows_q : rows1, pass ? B : B1);
   }
   if (overflow) {   // the per-thread kernel takes it
     if (lane == 0) fallq[1 + atomicAdd(fallq, 1)] = s;
@@ -501,6 +458,227 @@ __global__ void __launch_bounds__(kKnnWarps * 32, 4) k_knn_warp(GridDev g, int K
   if (lane == 0) out_counts[orig] = kept;
 }
 
+__global__ void __launch_bounds__(kKnnWarps * 32, 4) k_knn_warp(GridDev g, int K, float dmax_g, int rows_q,
+                                                            Band B, float dmax1, int rows1, Band B1,
+                                                            PairBand pb, unsigned flags,
+                                                            int *__restrict__ out_ids,
+                                                            float *__restrict__ out_d2,
+                                                            int *__restrict__ out_counts,
+                                                            int *__restrict__ fallq,
+                                                            const int *__restrict__ list) {
+  __shared__ unsigned long long keys[kKnnWarps][kKnnCap];
+  const int w = threadIdx.x >> 5;
+  const int count = list ? list[0] : g.n;
+  for (int item = blockIdx.x * kKnnWarps + w; item < count; item += gridDim.x * kKnnWarps) {
+    __syncwarp();   // the previous query's buffer is no longer read
+    knn_warp_query(g, list ? list[1 + item] : item, keys[w], K, dmax_g, rows_q, B, dmax1, rows1, B1, pb, flags,
+                   out_ids, out_d2, out_counts, fallq);
+  }
+}
+
+// One thread per query, for K <= kLaneKMax with a bounded r_max.  The lanes
+// of a warp serve consecutive sorted queries, which lie in neighbouring cells
+// of one x-row, so they walk the same x-rows (the rows table, centre to edge)
+// in step and their loads of cell starts and points fall close together.
+// Each lane keeps its K + 1 smallest FP32 distances, sorted, in its column of
+// shared memory; once it holds K + 1 the cut shrinks to the (K+1)-th value
+// plus the FP32 error bound (the running radius of Sec. II.A), which skips
+// later rows, cells and candidates.  A candidate that is dropped beyond the
+// list is remembered by the smallest FP32 value dropped: when that value lies
+// within the error bound of the K-th, the list alone does not settle the K-th
+// neighbour and the query goes to the warp kernel's queue (warpq), which
+// keeps every candidate.  Runs of list entries closer than the bound are put
+// in canonical (D2, index) order, as in the warp kernel.
+constexpr int kLaneT = 128;
+constexpr int kLaneKMax = 16;   // measured: faster than the warp kernel up to K = 16, slower at K = 64
+
+__global__ void __launch_bounds__(kLaneT) k_knn_lane(GridDev g, int K, float dmax_g, int rows_q, Band B,
+                                                     float dmax1, int rows1, Band B1, PairBand pb,
+                                                     unsigned flags, int *__restrict__ out_ids,
+                                                     float *__restrict__ out_d2, int *__restrict__ out_counts,
+                                                     int *__restrict__ fallq, int *__restrict__ warpq,
+                                                     const int *__restrict__ list) {
+  extern __shared__ __align__(16) unsigned char lane_smem[];
+  const int T = blockDim.x, t = threadIdx.x;
+  const int KP = K + 1;
+  float *Ld = reinterpret_cast<float *>(lane_smem);              // [k * T + t]: FP32 d2, ascending
+  unsigned *Lj = reinterpret_cast<unsigned *>(Ld + (size_t)KP * T);   // sorted slot | wrapped << 31
+  const int ti = blockIdx.x * T + t;
+  if (ti >= (list ? list[0] : g.n)) return;
+  const int s = list ? list[1 + ti] : ti;
+  const QueryGeom Q = make_geom(g.qpos[s], g);
+  if (Q.outside) {   // the bounding-cube walk of the per-thread kernel
+    fallq[1 + atomicAdd(fallq, 1)] = s;
+    return;
+  }
+  const int self = query_self(g, flags, s);
+  const int Gx = 1 << g.wx;
+  const bool cyc_x = g.cyc & 1u;
+  auto bound = [&](float d) {   // FP32 error bound of a pair of values near d (wrapped or not)
+    const float m = d * 1.000001f;
+    return fmaf(pb.c2, m, pb.c1 * sqrtf(m)) + 1e-37f;
+  };
+  int cnt = 0;
+  float dmin_drop = INFINITY;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1 && (cnt >= K || !(dmax1 < dmax_g))) break;
+    const Band Bp = pass ? B : B1;
+    const float dm = pass ? dmax_g : dmax1;
+    const int nrows = pass ? rows_q : rows1;
+    const float hi0 = fmaxf(Bp.hi, Bp.hi_w);
+    cnt = 0;
+    dmin_drop = INFINITY;
+    float cut2 = dm * dm;   // cell units: rows and cells beyond it are skipped
+    float hi = hi0;         // world units: candidates beyond it are skipped
+    // an accepted candidate into the sorted list of the K + 1 smallest
+    auto insert = [&](float d, unsigned code) {
+      int at;
+      if (cnt == KP) {
+        const float last = Ld[K * T + t];
+        if (!(d < last)) {
+          dmin_drop = fminf(dmin_drop, d);
+          return;
+        }
+        dmin_drop = fminf(dmin_drop, last);   // the old (K+1)-th leaves the list
+        at = K;
+      } else {
+        at = cnt++;
+      }
+      while (at > 0 && Ld[(at - 1) * T + t] > d) {
+        Ld[at * T + t] = Ld[(at - 1) * T + t];
+        Lj[at * T + t] = Lj[(at - 1) * T + t];
+        --at;
+      }
+      Ld[at * T + t] = d;
+      Lj[at * T + t] = code;
+      if (cnt == KP) {   // shrink: only values below the (K+1)-th, or within its bound, still matter
+        const float dl = Ld[K * T + t];
+        hi = fminf(hi0, dl + bound(dl));
+        const float rc = sqrtf(hi) * g.inv_s + g.eps;
+        cut2 = fminf(cut2, rc * rc);
+      }
+    };
+    auto consider = [&](float d, int j, bool wr, const float4 &p) {
+      if (d > hi) return;
+      const float blo = wr ? Bp.lo_w : Bp.lo, bhi = wr ? Bp.hi_w : Bp.hi;
+      bool in = d <= blo;
+      if (!in && !(d > bhi)) in = canon_d2_call(Q.q, p, g.Lx, g.Ly, g.Lz, g.cyc) <= Bp.r2;
+      if (in) insert(d, (unsigned)j | (wr ? 0x80000000u : 0u));
+    };
+    bool out_any = false;
+    for (int r = 0; r < nrows; ++r) {
+      const RowEntry E = g.rows[r];
+      if ((float)E.b2 > cut2) break;   // rows by b2: every later row lies beyond the cut
+      const float ty = E.oy > 0 ? (float)(E.oy - 1) + Q.zp[1] : (E.oy < 0 ? (float)(-E.oy - 1) + Q.zn[1] : 0.f);
+      const float tz = E.oz > 0 ? (float)(E.oz - 1) + Q.zp[2] : (E.oz < 0 ? (float)(-E.oz - 1) + Q.zn[2] : 0.f);
+      const float rem = cut2 - fmaf(ty, ty, tz * tz);
+      if (rem < 0.f) continue;
+      const float h = sqrtf(rem) + g.eps;
+      const int lo = max((int)floorf(Q.u[0] - h) - Q.c[0], -g.row_lim_x);
+      const int hx = min((int)floorf(Q.u[0] + h) - Q.c[0], g.row_lim_x);
+      if (lo > hx) continue;
+      const Target tg = translate_raw(E.unp, Q, g);
+      if (tg.outside) {
+        out_any = true;
+        continue;
+      }
+      const unsigned row = tg.key - (unsigned)Q.c[0];
+      int x0 = Q.c[0] + lo, x1 = Q.c[0] + hx;
+      if (!cyc_x) {
+        if (x0 < 0 || x1 >= Gx) out_any = true;
+      } else if (x0 < 0 || x1 >= Gx) {   // the part through the x wrap
+        const int wa = x0 < 0 ? x0 + Gx : 0, wb = x0 < 0 ? Gx - 1 : x1 - Gx;
+        const int b = __ldg(g.cell_start + row + wa), e = __ldg(g.cell_start + row + wb + 1);
+        const float qx = Q.q.x + (x0 < 0 ? g.Lx : -g.Lx);
+        for (int j = b; j < e; ++j) {
+          if (j == self) continue;
+          const float4 p = g.spos[j];
+          const float dx = p.x - qx, dy = p.y - tg.qy, dz = p.z - tg.qz;
+          consider(fmaf(dz, dz, fmaf(dy, dy, dx * dx)), j, true, p);
+        }
+      }
+      x0 = max(x0, 0);
+      x1 = min(x1, Gx - 1);
+      if (x0 > x1) continue;
+      const int b = __ldg(g.cell_start + row + x0), e = __ldg(g.cell_start + row + x1 + 1);
+      for (int j = b; j < e; ++j) {
+        if (j == self) continue;
+        const float4 p = g.spos[j];
+        const float dx = p.x - tg.qx, dy = p.y - tg.qy, dz = p.z - tg.qz;
+        consider(fmaf(dz, dz, fmaf(dy, dy, dx * dx)), j, tg.wrapped, p);
+      }
+    }
+    if (out_any) {   // the outside cell: every pair in FP64 (its FP32 rounding is within the relative bound)
+      const int b = __ldg(g.cell_start + g.outside), e = __ldg(g.cell_start + g.outside + 1);
+      for (int j = b; j < e; ++j) {
+        if (j == self) continue;
+        const double D = canon_d2_call(Q.q, g.spos[j], g.Lx, g.Ly, g.Lz, g.cyc);
+        if (D <= Bp.r2 && (float)D <= hi) insert((float)D, (unsigned)j);
+      }
+    }
+  }
+  // the K-th is settled by the list unless a dropped candidate lies within
+  // the error bound of it
+  if (cnt == KP && dmin_drop <= Ld[(K - 1) * T + t] + bound(Ld[(K - 1) * T + t])) {
+    warpq[1 + atomicAdd(warpq, 1)] = s;
+    return;
+  }
+  // runs of adjacent entries closer than the bound, in canonical order
+  auto close = [&](int a) {   // entries a and a + 1
+    const float da = Ld[a * T + t], db = Ld[(a + 1) * T + t];
+    const bool wr = (Lj[a * T + t] | Lj[(a + 1) * T + t]) >> 31;
+    const float m = db * 1.000001f;
+    return !(db - da > fmaf(pb.c2, m, wr ? pb.c1 * sqrtf(m) : 0.f) + 1e-37f);
+  };
+  for (int a = 0; a + 1 < cnt; ++a) {
+    if (!close(a)) continue;
+    int e = a + 1;
+    while (e + 1 < cnt && close(e)) ++e;
+    // insertion sort of [a, e] by (D2, index)
+    for (int i = a + 1; i <= e; ++i) {
+      const float dx = Ld[i * T + t];
+      const unsigned cx = Lj[i * T + t];
+      const int jx = (int)(cx & 0x7fffffffu);
+      const double Dx = canon_d2_call(Q.q, g.spos[jx], g.Lx, g.Ly, g.Lz, g.cyc);
+      const int ix = __ldg(g.perm + jx);
+      int p = i;
+      while (p > a) {
+        const int jy = (int)(Lj[(p - 1) * T + t] & 0x7fffffffu);
+        const double Dy = canon_d2_call(Q.q, g.spos[jy], g.Lx, g.Ly, g.Lz, g.cyc);
+        if (Dy < Dx || (Dy == Dx && __ldg(g.perm + jy) < ix)) break;
+        Ld[p * T + t] = Ld[(p - 1) * T + t];
+        Lj[p * T + t] = Lj[(p - 1) * T + t];
+        --p;
+      }
+      Ld[p * T + t] = dx;
+      Lj[p * T + t] = cx;
+    }
+    a = e;
+  }
+  const int kept = min(cnt, K);
+  const int orig = __ldg(g.qid + s);
+  int *oi = out_ids + (size_t)orig * K;
+  float *od = out_d2 ? out_d2 + (size_t)orig * K : nullptr;
+  for (int k = 0; k < K; ++k) {
+    const bool have = k < kept;
+    const int j = have ? (int)(Lj[k * T + t] & 0x7fffffffu) : 0;
+    oi[k] = have ? __ldg(g.perm + j) : -1;
+    if (od) {
+      float v = __int_as_float(0x7f800000);
+      if (have) {
+        if (flags & SI_FAST_D2) {
+          v = Ld[k * T + t];
+        } else {
+          const float4 p = g.spos[j];
+          if (!canon_d2_f32_try(Q.q, p, g, v)) v = __double2float_rn(canon_d2_call(Q.q, p, g.Lx, g.Ly, g.Lz, g.cyc));
+        }
+      }
+      od[k] = v;
+    }
+  }
+  out_counts[orig] = kept;
+}
+
 }  // namespace si
 
 using namespace si;
@@ -566,28 +744,59 @@ extern "C" si_status si_query_knn(si_grid *g, const float *d_centers, int64_t m,
                                                                      d_ids, d_d2, d_counts, list));
     return SI_OK;
   }
-  // first cut: the radius expected to hold K + 2 sqrt(K) + 4 points at the
-  // mean load, two standard deviations of a Poisson count above K (exact when
-  // it holds K; the kernel widens it to r_max otherwise)
-  float dmax1 = dmax_g;
-  int n1 = n_query;
-  Band B1 = B;
+  // first cut: the radius expected to hold `want` points at the mean load
+  // (exact when it holds K; the kernels widen it to r_max otherwise).  The
+  // warp kernel takes K + 2 sqrt(K) + 4, two standard deviations of a
+  // Poisson count above K; the lane kernel, whose lanes wait for the warp's
+  // slowest, K + 3 sqrt(K) + 8, so that a second pass is rare in any warp
+  // (its cut shrinks as soon as K + 1 are held, so the wider start costs
+  // little).
   const double load = (double)g->n / (double)std::max<int64_t>(g->n_cells - 1, 1);
-  if (load > 0.0) {
-    const double want = k + 2.0 * std::sqrt((double)k) + 4.0;
+  const std::vector<int> &row_end = g->tables.row_end;   // rows with b2 <= n
+  const int rows_q = row_end[(size_t)std::min(n_query, g->tables.n_max)];
+  auto first_cut = [&](double want, float &dmax1, int &rows1, Band &B1) {
+    dmax1 = dmax_g;
+    rows1 = rows_q;
+    B1 = B;
+    if (load <= 0.0) return;
     const double r1 = std::cbrt(3.0 * want / (4.0 * M_PI * load)) / (double)lat.inv_s;   // world units
     if (r1 < 0.9 * (double)r_max_query) {
       B1 = make_band(lat, (float)r1);
       dmax1 = (float)r1 * lat.inv_s + (float)lat.eps;
-      n1 = std::min((int)std::floor(dmax1 * dmax1), g->tables.n_max);
+      rows1 = row_end[(size_t)std::min((int)std::floor(dmax1 * dmax1), g->tables.n_max)];
     }
-  }
-  // a warp per query; the queries it hands back go to the per-thread kernel
+  };
+  float dmax1w;
+  int rows1w;
+  Band B1w;
+  first_cut(k + 2.0 * std::sqrt((double)k) + 4.0, dmax1w, rows1w, B1w);
   SI_CUDA_TRY(cudaMemsetAsync(fallq, 0, sizeof(int), st));
-  const unsigned wblocks = (unsigned)((m + kKnnWarps - 1) / kKnnWarps);
-  SI_KLAUNCH("k_knn_warp", st, k_knn_warp<<<wblocks, kKnnWarps * 32, 0, st>>>(dv, k, dmax_g, n_query, B, dmax1,
-                                                                              n1, B1, pb, flags, d_ids, d_d2,
-                                                                              d_counts, fallq, list));
+  if (k <= kLaneKMax) {
+    // a thread per query; the queries whose K-th it cannot settle go to the
+    // warp kernel (warpq), those outside the region to the per-thread kernel
+    int *warpq = d_centers ? g->chuge : g->hugeq;   // idle during a K-nearest call
+    SI_CUDA_TRY(cudaMemsetAsync(warpq, 0, sizeof(int), st));
+    float dmax1l;
+    int rows1l;
+    Band B1l;
+    first_cut(k + 3.0 * std::sqrt((double)k) + 8.0, dmax1l, rows1l, B1l);
+    const size_t lsmem = (size_t)(k + 1) * kLaneT * (sizeof(float) + sizeof(unsigned));
+    SI_CUDA_TRY(cudaFuncSetAttribute(k_knn_lane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
+    const unsigned lblocks = (unsigned)((m + kLaneT - 1) / kLaneT);
+    SI_KLAUNCH("k_knn_lane", st, k_knn_lane<<<lblocks, kLaneT, lsmem, st>>>(dv, k, dmax_g, rows_q, B, dmax1l, rows1l,
+                                                                           B1l, pb, flags, d_ids, d_d2, d_counts,
+                                                                           fallq, warpq, list));
+    const unsigned wblocks = (unsigned)std::min<int64_t>((m + kKnnWarps - 1) / kKnnWarps, 148 * 4);
+    SI_KLAUNCH("k_knn_warp (lane queue)", st, k_knn_warp<<<wblocks, kKnnWarps * 32, 0, st>>>(dv, k, dmax_g, rows_q, B, dmax1w,
+                                                                                rows1w, B1w, pb, flags, d_ids, d_d2,
+                                                                                d_counts, fallq, warpq));
+  } else {
+    // a warp per query; the queries it hands back go to the per-thread kernel
+    const unsigned wblocks = (unsigned)((m + kKnnWarps - 1) / kKnnWarps);
+    SI_KLAUNCH("k_knn_warp", st, k_knn_warp<<<wblocks, kKnnWarps * 32, 0, st>>>(dv, k, dmax_g, rows_q, B, dmax1w,
+                                                                                rows1w, B1w, pb, flags, d_ids, d_d2,
+                                                                                d_counts, fallq, list));
+  }
   // sized for every query; blocks past the queue's length exit at once
   const unsigned fblocks = (unsigned)((m + kKnnThreads - 1) / kKnnThreads);
   SI_KLAUNCH("k_knn", st, k_knn<<<fblocks, kKnnThreads, smem, st>>>(dv, k, dmax_g, n_query, B, pb, flags,

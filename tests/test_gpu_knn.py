@@ -61,6 +61,32 @@ def test_ties_on_a_coarse_lattice_broken_by_index():
     check(scene, 12, scene.r, ids, d2, cnt, np.arange(scene.n))
 
 
+def _float32_midpoints(od):
+    """How many FP64 values lie exactly halfway between two FP32 values."""
+    f = od.astype(np.float32)
+    lo = f.astype(np.float64)
+    nb = np.nextafter(f, np.where(od > lo, np.float32(np.inf), np.float32(-np.inf))).astype(np.float64)
+    return int(np.sum((od != lo) & (2.0 * od == lo + nb)))
+
+
+@pytest.mark.parametrize("mask", [7, 0])
+def test_distances_at_float32_midpoints(mask):
+    """Coordinates on a 2^-16 grid: squared distances carry about 27
+    significant bits, so many canonical values fall exactly halfway between
+    two FP32 values (and many more within a few units of the 2^-40 margin),
+    where the FP32 form of the rounding hands over to FP64; ties-to-even
+    must come out as the FP64 conversion does."""
+    rng = np.random.default_rng(11 + mask)
+    pos = np.zeros((20_000, 4), np.float32)
+    pos[:, :3] = rng.integers(0, 1 << 16, size=(20_000, 3)) / float(1 << 16)
+    scene = synth.Scene(pos, (0, 0, 0), 1 / 32, (5, 5, 5), mask, 3 / 32)
+    ids, d2, cnt = run_knn(scene, 16, scene.r)
+    q = np.arange(scene.n)
+    check(scene, 16, scene.r, ids, d2, cnt, q)
+    _, od, _ = oracle.knn(scene.pos, scene.pos, scene.box, scene.cyclic_mask, 16, float(np.float32(scene.r)), q)
+    assert _float32_midpoints(od[np.isfinite(od)]) > 1000
+
+
 def test_duplicates_and_points_outside_region():
     pos = synth.uniform_points(8000, 8)
     pos[100:140] = pos[7]                  # 40 copies of point 7: distance-0 ties
