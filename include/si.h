@@ -70,8 +70,9 @@ typedef enum {
 #define SI_FAST_D2       256u  /* K nearest: report the kernel's FP32 squared
                                   distance (within 12u D2 + 16u L sqrt(D2) of
                                   the canonical D2, u = 2^-24) instead of the
-                                  FP32 rounding of the canonical FP64 D2,
-                                  which costs K FP64 evaluations per query  */
+                                  FP32 rounding of the canonical FP64 D2
+                                  (formed in FP32 by error-free transforms,
+                                  FP64 only next to a rounding midpoint)      */
 #define SI_NO_GROUPS     128u  /* radius: serve every crowded cell on its own
                                   (by default neighbouring crowded cells of an
                                   aligned 2x2x2 block share one candidate
