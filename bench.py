@@ -884,12 +884,46 @@ class OracleRunner:
                 f"FP64 brute force over all points, {self.threads} threads, {total_s:.1f} s")
 
 
+def tier_b(name):
+    """The CPU cell walks of oracle/cells.c (FP64, every host thread) over the
+    whole radius workload: binning plus every query's sorted list, for the
+    spherical index (offset table + Eq. 1 cell test) and the bin-lattice cube
+    scan.  None for workloads other than the all-agents radius scenes."""
+    import oracle
+    from paper_cs_0608108_b300 import synth
+    scenes = {"radius_1m": [synth.uniform_1m_scene, synth.mixture_1m_scene],
+              "radius_1m_cube": [synth.uniform_1m_scene, synth.mixture_1m_scene],
+              "radius_uniform": [synth.uniform_1m_scene], "radius_uniform_cube": [synth.uniform_1m_scene],
+              "radius_mixture": [synth.mixture_1m_scene], "radius_mixture_cube": [synth.mixture_1m_scene],
+              "tiny": [synth.tiny_scene]}.get(name)
+    if scenes is None:
+        return None
+    out = {"unit": "queries/s", "threads": oracle.max_threads(), "kind": "cpu cell walks (oracle/cells.c), FP64",
+           "sample": "every query of " + " + ".join(f.__name__.replace("_scene", "") for f in scenes)
+                     + ", binning included"}
+    for method in ("sphere", "cube"):
+        q, t = 0, 0.0
+        for make in scenes:
+            sc = make()
+            t0 = time.perf_counter()
+            oracle.cells_radius(sc.pos, sc.origin, sc.cell_size, sc.log2_cells, sc.cyclic_mask,
+                                float(np.float32(sc.r)), method=method)
+            t += time.perf_counter() - t0
+            q += sc.n
+        out[method] = {"value": q / t, "seconds": t}
+    return out
+
+
 def cpu_baseline(name, budget_s=15.0):
     r = OracleRunner(name)
     m = r.calibrate(budget_s)
     dt = r.run(m)
-    return {"value": m / dt, "unit": "queries/s", "cores": r.threads, "kind": "oracle",
-            "sample": r.describe(m, dt, 1)}
+    cb = {"value": m / dt, "unit": "queries/s", "cores": r.threads, "kind": "oracle",
+          "sample": r.describe(m, dt, 1)}
+    tb = tier_b(name)
+    if tb is not None:
+        cb["tier_b"] = tb
+    return cb
 
 
 # ---------------------------------------------------------------------------

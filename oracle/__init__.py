@@ -9,6 +9,10 @@ in this package.  It shares no code with the CUDA path and never imports it.
   objects -- the plain definition of the query (Sec. I, Sec. II.A) -- and
   the same reduction through a plain bin lattice (cells at least r wide,
   3 x 3 x 3 cells per object), for sizes where O(n^2) is too slow.
+* `cells.c` (in the same library): the radius query through CPU cell walks,
+  the bin-lattice cube scan and the spherical index (Sec. II.A offset table
+  by minimum bound, Sec. III.A Eq. 1 cell test), FP64: the timed CPU
+  baselines of the cell methods, checked against the brute force.
 * `sphere_index.py`: the paper's own method restated on the CPU in float64
   (tables of Sec. II.A and Sec. III.A, cell locations of Sec. II.B).  Used to
   pin the brute force against an independent algorithm and to check the
@@ -31,11 +35,11 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile brute.c with gcc (no FMA contraction, OpenMP)."""
-    src = os.path.join(_HERE, "brute.c")
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+    """Compile brute.c and cells.c with gcc (no FMA contraction, OpenMP)."""
+    srcs = [os.path.join(_HERE, f) for f in ("brute.c", "cells.c")]
+    if force or not os.path.exists(_SO) or any(os.path.getmtime(_SO) < os.path.getmtime(f) for f in srcs):
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-fopenmp", src, "-o", _SO, "-lm"])
+                               "-fno-fast-math", "-fopenmp", *srcs, "-o", _SO, "-lm"])
     return _SO
 
 
@@ -53,6 +57,7 @@ def _load():
         lib.or_knn.argtypes = [P, I64, P, I64, P, P, I32, D, I32, P, P, P, I32]
         lib.or_reduce.argtypes = [P, I64, P, I64, P, I32, D, P, P, I32]
         lib.or_reduce_cells.argtypes = [P, I64, P, I32, D, P, P, I32]
+        lib.or_cells_radius.argtypes = [P, I64, P, D, P, I32, D, I32, P, I64, P, P, P, I32]
         _lib = lib
     return _lib
 
@@ -134,6 +139,34 @@ def knn(pos, centers, box, cyclic_mask: int, k: int, r_max: float | None, self_i
     lib.or_knn(_ptr(pos), n, _ptr(centers), m, _ptr(s), _ptr(L), int(cyclic_mask), rm, int(k),
                _ptr(ids), _ptr(d2), _ptr(cnt), int(threads))
     return ids, d2, cnt
+
+
+def cells_radius(pos, origin, cell_size: float, log2_cells, cyclic_mask: int, r: float, queries=None,
+                 method: str = "sphere", threads: int = 0):
+    """Radius lists of the points `queries` (default all; each leaves itself
+    out) through a CPU cell walk of cells.c: method "sphere" (the offset
+    table by minimum bound with the Eq. 1 cell test) or "cube" (the bounding
+    cube of cells).  Same lists as radius(); returns (offsets, ids)."""
+    lib = _load()
+    pos = _f4(pos)
+    n = pos.shape[0]
+    q = np.arange(n, dtype=np.int64) if queries is None else np.ascontiguousarray(queries, dtype=np.int64)
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    w = np.ascontiguousarray(log2_cells, dtype=np.int32)
+    mode = {"cube": 0, "sphere": 1}[method]
+    counts = np.zeros(q.shape[0], dtype=np.int64)
+    rc = lib.or_cells_radius(_ptr(pos), n, _ptr(o), float(cell_size), _ptr(w), int(cyclic_mask), float(r), mode,
+                             _ptr(q), q.shape[0], _ptr(counts), None, None, int(threads))
+    if rc != 0:
+        raise ValueError(f"or_cells_radius failed ({rc})")
+    offsets = np.zeros(q.shape[0] + 1, dtype=np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    ids = np.zeros(int(offsets[-1]), dtype=np.int32)
+    rc = lib.or_cells_radius(_ptr(pos), n, _ptr(o), float(cell_size), _ptr(w), int(cyclic_mask), float(r), mode,
+                             _ptr(q), q.shape[0], None, _ptr(offsets), _ptr(ids), int(threads))
+    if rc != 0:
+        raise ValueError(f"or_cells_radius failed ({rc})")
+    return offsets, ids
 
 
 def reduce(pos, idx, box, cyclic_mask: int, r: float, threads: int = 0):
