@@ -176,6 +176,22 @@ si_status si_query_radius(si_grid *g, const float *d_centers, int64_t m, float r
                           uint32_t flags, int64_t *d_offsets, int32_t *d_ids,
                           int64_t ids_capacity, int64_t *h_total, void *stream);
 
+/* End to end with host buffers: the all-agents radius query of n points
+ * held in host memory.  Copies h_pos (n * 4 floats, host; page-locked memory
+ * makes the copy direct and fast) into the grid's own device buffer, bins
+ * it (si_grid_build), runs the all-agents si_query_radius into the grid's
+ * own device output buffers, copies the CSR result to h_offsets[n + 1]
+ * (int64, host) and h_ids (int32, host, capacity ids_capacity), and waits
+ * for the copies: on return the host buffers hold the result.  *h_total
+ * (host, required) receives the number of ids; SI_ERR_CAPACITY, with
+ * nothing written to h_ids, when it exceeds ids_capacity.  The first call,
+ * and a call with more points or a larger ids_capacity than before,
+ * allocates those device buffers (16 n + 8 (n + 1) + 4 ids_capacity bytes);
+ * si_grid_destroy frees them. */
+si_status si_query_radius_host(si_grid *g, const float *h_pos, int64_t n, float r, uint32_t flags,
+                               int64_t *h_offsets, int32_t *h_ids, int64_t ids_capacity,
+                               int64_t *h_total, void *stream);
+
 /* K-nearest query (Sec. II.A, last paragraph: once K neighbors are found
  * the search radius shrinks to the K-th distance; Sec. IV.B), for all agents
  * (d_centers NULL, m = the grid's n; own index excluded unless

@@ -214,6 +214,32 @@ class Grid:
             return off, ids[: int(total.value)]
         return off, ids
 
+    def query_radius_host(self, h_pos: torch.Tensor, r: float, h_offsets: torch.Tensor, h_ids: torch.Tensor,
+                          include_self: bool = False, sort: bool = True) -> int:
+        """End to end with host buffers (si_query_radius_host): h_pos, a CPU
+        float32 (n, 4) tensor (page-locked for a direct copy), is copied to
+        the device, binned and queried for all agents; the CSR result lands in
+        the CPU tensors h_offsets (int64, n + 1) and h_ids (int32, its length
+        is the capacity).  Returns the number of ids; raises when they do not
+        fit."""
+        if h_pos.device.type != "cpu" or h_pos.dtype != torch.float32 or h_pos.dim() != 2 or h_pos.shape[1] != 4:
+            raise ValueError("h_pos must be a CPU float32 (n, 4) tensor")
+        if not h_pos.is_contiguous():
+            raise ValueError("h_pos must be contiguous")
+        n = h_pos.shape[0]
+        for t, dt, want in ((h_offsets, torch.int64, n + 1), (h_ids, torch.int32, 0)):
+            if t.device.type != "cpu" or t.dtype != dt or not t.is_contiguous() or t.numel() < want:
+                raise ValueError("h_offsets must be CPU int64 (n + 1); h_ids CPU int32, contiguous")
+        flags = (N.SI_INCLUDE_SELF if include_self else 0) | (0 if sort else N.SI_NO_SORT)
+        total = ctypes.c_int64(0)
+        N.check(self._lib.si_query_radius_host(self._h, h_pos.data_ptr(), n, float(r), flags, h_offsets.data_ptr(),
+                                               h_ids.data_ptr(), h_ids.numel(), ctypes.byref(total), _stream()),
+                "si_query_radius_host")
+        self.n = n
+        if self._pos is None:   # the grid now holds the uploaded points; outputs go to this device
+            self._pos = torch.empty((0, 4), dtype=torch.float32, device=torch.device("cuda", torch.cuda.current_device()))
+        return int(total.value)
+
     def query_knn(self, k: int, r_max=None, include_self: bool = False, with_d2: bool = True,
                   out=None, centers=None, fast_d2: bool = False):
         """K nearest within r_max (None = grid's whole region), for every point

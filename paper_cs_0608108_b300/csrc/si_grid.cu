@@ -681,6 +681,9 @@ static void grid_free(si_grid *g) {
   cudaFree(g->chuge);
   cudaFree(g->cstage);
   cudaFree(g->ipos);
+  cudaFree(g->io_pos);
+  cudaFree(g->io_off);
+  cudaFree(g->io_ids);
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
   free_tables(g->tables);
   delete g;

@@ -227,5 +227,13 @@ struct si_grid {
   int64_t cstage_cap = 0;
   si_status ensure_centers(int64_t m, bool stage);
   float4 *ipos = nullptr;        // cap: points in input order (non-empty list method; allocated on first use)
+  // si_query_radius_host: the points and the CSR result on the device,
+  // grown on demand
+  float4 *io_pos = nullptr;
+  int64_t io_pos_cap = 0;
+  long long *io_off = nullptr;
+  int64_t io_off_cap = 0;
+  int *io_ids = nullptr;
+  int64_t io_ids_cap = 0;
   si::GridDev dev() const;
 };

@@ -923,3 +923,43 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   if (!(flags & SI_NO_SORT)) return launch_sorts(off, d_ids, g->longq, g->hugeq, st);
   return SI_OK;
 }
+
+// All-agents radius query from host memory to host memory (the end-to-end
+// form of the path): H2D copy, binning, query, D2H copy, all on `stream`.
+extern "C" si_status si_query_radius_host(si_grid *g, const float *h_pos, int64_t n, float r, uint32_t flags,
+                                          int64_t *h_offsets, int32_t *h_ids, int64_t ids_capacity,
+                                          int64_t *h_total, void *stream) {
+  if (!g) return fail(SI_ERR_INVALID, "null grid");
+  if (!h_pos || !h_offsets || !h_total) return fail(SI_ERR_INVALID, "null host buffer");
+  if (ids_capacity < 0 || (ids_capacity > 0 && !h_ids)) return fail(SI_ERR_INVALID, "bad ids buffer");
+  if (n < 0 || n > g->cap) return fail(SI_ERR_INVALID, "n out of range (0 .. capacity)");
+  cudaStream_t st = (cudaStream_t)stream;
+  auto grow = [](auto *&p, int64_t &cap, int64_t want, size_t elem) -> si_status {
+    if (want <= cap) return SI_OK;
+    cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    const cudaError_t e = cudaMalloc((void **)&p, (size_t)std::max<int64_t>(want, 1) * elem);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return cuda_fail(e, "si_query_radius_host buffers");
+    }
+    cap = want;
+    return SI_OK;
+  };
+  si_status s;
+  if ((s = grow(g->io_pos, g->io_pos_cap, n, sizeof(float4))) != SI_OK) return s;
+  if ((s = grow(g->io_off, g->io_off_cap, n + 1, sizeof(long long))) != SI_OK) return s;
+  if ((s = grow(g->io_ids, g->io_ids_cap, ids_capacity, sizeof(int))) != SI_OK) return s;
+  if (n > 0) SI_CUDA_TRY(cudaMemcpyAsync(g->io_pos, h_pos, (size_t)n * sizeof(float4), cudaMemcpyHostToDevice, st));
+  if ((s = si_grid_build(g, reinterpret_cast<const float *>(g->io_pos), n, stream)) != SI_OK) return s;
+  // the call waits after counting, stores the total and refuses an ids
+  // buffer that is too small
+  if ((s = si_query_radius(g, nullptr, n, r, flags, reinterpret_cast<int64_t *>(g->io_off), g->io_ids, ids_capacity,
+                           h_total, stream)) != SI_OK)
+    return s;
+  SI_CUDA_TRY(cudaMemcpyAsync(h_offsets, g->io_off, (size_t)(n + 1) * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  if (*h_total > 0)
+    SI_CUDA_TRY(cudaMemcpyAsync(h_ids, g->io_ids, (size_t)*h_total * sizeof(int), cudaMemcpyDeviceToHost, st));
+  return si_grid_sync(g, stream);
+}
