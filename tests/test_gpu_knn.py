@@ -119,19 +119,39 @@ def test_crowded_queries_overflowing_the_warp_buffer():
         check(scene, k, scene.r, ids, d2, cnt, np.arange(scene.n))
 
 
+@pytest.mark.parametrize("k", [1, 8, 16, 40])
+@pytest.mark.parametrize("mask", [7, 0])
+def test_include_self_through_both_kernels(k, mask):
+    # K <= 16 runs the thread-per-query kernel, K = 40 the warp kernel; the
+    # query's own point comes first, at distance 0
+    pos = synth.uniform_points(20_000, 60 + mask)
+    scene = synth.Scene(pos, (0, 0, 0), 1 / 32, (5, 5, 5), mask, 3 / 32)
+    g = gpu_grid(scene)
+    ids, d2, cnt = g.query_knn(k, r_max=scene.r, include_self=True)
+    g.sync()
+    ids, d2, cnt = ids.cpu().numpy(), d2.cpu().numpy(), cnt.cpu().numpy()
+    q = np.arange(scene.n)
+    oi, od, oc = oracle.knn(scene.pos, scene.pos, scene.box, mask, k, float(np.float32(scene.r)), None)
+    assert np.array_equal(cnt, oc) and np.array_equal(ids, oi)
+    fin = np.isfinite(od)
+    assert np.array_equal(d2[fin], od[fin].astype(np.float32))
+    assert np.all(ids[:, 0] == q) and np.all(d2[:, 0] == 0.0)
+
+
 def test_fast_distances_within_their_bound():
     # SI_FAST_D2: the same ids and counts, the kernel's FP32 squared distance
     # within 12u D2 + 16u L sqrt(D2) of the canonical D2
     pos = synth.uniform_points(30_000, 77)
     scene = synth.Scene(pos, (0, 0, 0), 1 / 32, (5, 5, 5), 3, 4 / 32)
     g = gpu_grid(scene)
-    ids, d2, cnt = g.query_knn(16, r_max=scene.r, fast_d2=True)
-    g.sync()
     q = np.arange(0, scene.n, 5)
-    oi, od, oc = oracle.knn(scene.pos, scene.pos[q], scene.box, 3, 16, float(np.float32(scene.r)), q)
-    assert np.array_equal(cnt.cpu().numpy()[q], oc) and np.array_equal(ids.cpu().numpy()[q], oi)
-    got = d2.cpu().numpy()[q].astype(np.float64)
-    fin = np.isfinite(od)
-    assert np.all(np.isinf(got[~fin]))
-    L = max(scene.box)
-    assert np.all(np.abs(got[fin] - od[fin]) <= 12 * U * od[fin] + 16 * U * L * np.sqrt(od[fin]) + 1e-30)
+    for k in (16, 40):   # the thread-per-query kernel, then the warp kernel
+        ids, d2, cnt = g.query_knn(k, r_max=scene.r, fast_d2=True)
+        g.sync()
+        oi, od, oc = oracle.knn(scene.pos, scene.pos[q], scene.box, 3, k, float(np.float32(scene.r)), q)
+        assert np.array_equal(cnt.cpu().numpy()[q], oc) and np.array_equal(ids.cpu().numpy()[q], oi)
+        got = d2.cpu().numpy()[q].astype(np.float64)
+        fin = np.isfinite(od)
+        assert np.all(np.isinf(got[~fin]))
+        L = max(scene.box)
+        assert np.all(np.abs(got[fin] - od[fin]) <= 12 * U * od[fin] + 16 * U * L * np.sqrt(od[fin]) + 1e-30)
