@@ -144,6 +144,16 @@ si_status si_build_grid(const si_grid_desc *desc, const float *d_pos, int64_t n,
 si_status si_grid_sync(si_grid *g, void *stream);
 
 si_status si_grid_get_info(const si_grid *g, si_grid_info *info);
+
+/* Run-time method selection of the radius queries (Appendix: a weighting
+ * factor for the volume comparison, and an optional reversal to the bin
+ * lattice below a distance, off by default).  list_weight (>= 0): with
+ * SI_METHOD_SPHERE the non-empty list method is taken when list_weight times
+ * its estimated cost is below the spherical index's (default 1.2; 0: always
+ * the list, +inf: never).  cube_below (>= 0, cell units): a radius query with
+ * r / s below it takes the bin-lattice cube scan instead of the spherical
+ * index (default 0: never).  Every choice returns the same lists. */
+si_status si_grid_set_method(si_grid *g, float list_weight, float cube_below);
 si_status si_grid_destroy(si_grid *g);
 
 /* Fixed-radius query (Sec. I: every agent queries its neighborhood;

@@ -214,6 +214,15 @@ class Grid:
             return off, ids[: int(total.value)]
         return off, ids
 
+    def set_method(self, list_weight: float = 1.2, cube_below: float = 0.0) -> "Grid":
+        """Run-time method selection (si_grid_set_method, the Appendix's
+        weighting factor and reversal distance): the list method is taken
+        when list_weight times its estimated cost is below the sphere's
+        (inf: never, 0: always); radius queries with r below cube_below cell
+        sides take the bin-lattice cube scan.  The lists do not change."""
+        N.check(self._lib.si_grid_set_method(self._h, float(list_weight), float(cube_below)), "si_grid_set_method")
+        return self
+
     def query_radius_host(self, h_pos: torch.Tensor, r: float, h_offsets: torch.Tensor, h_ids: torch.Tensor,
                           include_self: bool = False, sort: bool = True) -> int:
         """End to end with host buffers (si_query_radius_host): h_pos, a CPU

@@ -154,6 +154,11 @@ struct si_grid {
   si_grid_desc desc;
   si::Lattice lat;
   int64_t cap = 0, n = 0;
+  // run-time method selection (si_grid_set_method): the weight of the list
+  // method's estimated cost, and the radius (cell units) below which radius
+  // queries take the bin-lattice cube scan
+  double list_weight = 1.2;
+  double cube_below = 0.0;
   int64_t n_cells = 0;
   si::DevTables tables;
   // device arrays

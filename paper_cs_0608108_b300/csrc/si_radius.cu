@@ -702,7 +702,8 @@ static si_status query_radius_list(si_grid *g, const float *d_centers, int64_t m
 //   list:   0.0019 per point + 0.0028 per hit + 1.2
 // with candidates = load x the Steiner volume 1 + 6d + 3 pi d^2 + 4/3 pi d^3
 // (cells meeting the sphere around a random center) and hits = load x
-// 4/3 pi d^3.  The list is taken when estimated 1.2x cheaper.
+// 4/3 pi d^3.  The list is taken when its estimate times the grid's weight
+// (the Appendix's weighting factor, 1.2 by default) is below the sphere's.
 static bool list_cheaper(const si_grid *g, float r, int walk) {
   if (g->n <= 0 || g->n_cells <= 1) return false;
   const double d = (double)r * (double)g->lat.inv_s;
@@ -717,7 +718,7 @@ static bool list_cheaper(const si_grid *g, float r, int walk) {
     sphere += 0.015 * steiner;
   }
   const double list = 0.0019 * (double)g->n + 0.0028 * hits + 1.2;
-  return 1.2 * list < sphere;
+  return g->list_weight * list < sphere;
 }
 
 // Radius query from caller-given centers (sorted by coarse cell first; see
@@ -796,6 +797,10 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   cudaStream_t st = (cudaStream_t)stream;
   if (flags & SI_METHOD_LIST)
     return query_radius_list(g, d_centers, m, r, flags, d_offsets, d_ids, ids_capacity, h_total, st);
+  // the optional reversal to the bin lattice below a radius (Appendix; off
+  // unless si_grid_set_method sets it)
+  if (!(flags & (SI_WALK_PAPER | SI_SPHERE_ONLY | SI_WALK_PLANES)) && (double)r * (double)g->lat.inv_s < g->cube_below)
+    flags |= SI_METHOD_CUBE;
   if (!(flags & (SI_METHOD_CUBE | SI_WALK_PAPER | SI_SPHERE_ONLY | SI_WALK_PLANES))) {
     // the walk the sphere method would take (class tables when they can be
     // built for this radius), then the volume comparison

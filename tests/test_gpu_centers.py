@@ -9,7 +9,7 @@ import torch
 import oracle
 from paper_cs_0608108_b300 import _native, synth
 
-from gpu_helpers import assert_csr_equal, gpu_grid, to_dev
+from gpu_helpers import assert_csr_equal, gpu_grid, oracle_radius, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -271,6 +271,27 @@ def test_list_method_from_centers_exact():
     off_o, ids_o = oracle_centers(scene, c[good])
     for t, i in enumerate(good):
         assert np.array_equal(ids[off[i]:off[i + 1]], ids_o[off_o[t]:off_o[t + 1]])
+
+
+def test_method_weight_and_reversal_to_the_bin_lattice():
+    # the Appendix's weighting factor and reversal distance: they change the
+    # kernels a query runs, never its lists
+    scene = synth.Scene(synth.uniform_points(30_000, 531), (0, 0, 0), 1 / 32, (5, 5, 5), 6, 1.2 / 32)
+    off_o, ids_o = oracle_radius(scene)
+    g = gpu_grid(scene)
+    cases = [((0.0, 0.0), "k_radius_all_count"),            # weight 0: always the list
+             ((float("inf"), 0.0), "k_radius_count"),       # never the list
+             ((1.2, 2.0), "k_radius_count_cube"),           # r = 1.2 cells < 2: the cube scan
+             ((1.2, 0.0), "k_radius_count")]                # the defaults
+    for (w, cb), kernel in cases:
+        g.set_method(w, cb)
+        names = kernels_run(lambda: g.query_radius(scene.r))
+        assert kernel in names, (w, cb, names)
+        off, ids = g.query_radius(scene.r)
+        g.sync()
+        assert_csr_equal(off.cpu().numpy(), ids.cpu().numpy(), off_o, ids_o)
+    with pytest.raises(_native.SIError):
+        g.set_method(-1.0, 0.0)
 
 
 def test_volume_comparison_picks_the_list_at_low_load_and_large_radius():
