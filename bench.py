@@ -503,7 +503,7 @@ class CentersWork:
 
 
 class KnnWork:
-    def __init__(self, scene, ks=(16, 64)):
+    def __init__(self, scene, ks=(16, 64), method="sphere"):
         import torch
         from paper_cs_0608108_b300 import Grid
         self.scene = scene
@@ -514,11 +514,12 @@ class KnnWork:
                         torch.empty((scene.n, k), dtype=torch.float32, device="cuda"),
                         torch.empty(scene.n, dtype=torch.int32, device="cuda")) for k in ks}
         self.queries = scene.n * len(ks)
+        self.method = method
 
     def step(self):
         self.grid.build(self.pos)
         for k in self.ks:
-            self.grid.query_knn(k, r_max=self.scene.r, out=self.out[k])
+            self.grid.query_knn(k, r_max=self.scene.r, out=self.out[k], method=self.method)
 
     def check(self):
         self.grid.sync()
@@ -526,7 +527,7 @@ class KnnWork:
     def algorithmic_bytes(self):
         n, C = self.scene.n, (1 << sum(self.scene.log2_cells)) + 1
         kb = float(np.mean([16 * n + 4 * n + 4 * C + 8 * k * n + 4 * n for k in self.ks]))
-        return {"k_knn_lane": kb, "k_knn_warp": kb, "k_knn": kb, "k_bin_key": 24 * n + 8 * C,
+        return {"k_knn_lane": kb, "k_knn_warp": kb, "k_knn": kb, "k_knn_cube": kb, "k_bin_key": 24 * n + 8 * C,
                 "k_bin_scatter": 48 * n + 4 * C}
 
     def step_bytes(self):
@@ -640,6 +641,9 @@ def make_work(name):
             "same, GPU bin-lattice cube scan"
     if name == "knn_4m":
         return KnnWork(synth.knn_4m_scene()), "4M-point K-nearest (K=16 and 64), 256^3, cyclic x,y, r_max=4 cells"
+    if name == "knn_4m_cube":
+        return KnnWork(synth.knn_4m_scene(), method="cube"), \
+            "4M-point K-nearest (K=16 and 64), 256^3, cyclic x,y, r_max=4 cells, GPU bin-lattice walk"
     if name == "knn_250k":
         return KnnWork(synth.knn_250k_scene()), \
             "250k-point K-nearest (K=16 and 64) at the 4M configuration's density, 128x128x64, cyclic x,y, " \
@@ -863,7 +867,7 @@ def _oracle_scene(name):
         return synth.mixture_250k_scene()
     if name in ("radius_mixture", "radius_mixture_cube", "radius_centers_1m"):
         return synth.mixture_1m_scene()
-    if name == "knn_4m":
+    if name in ("knn_4m", "knn_4m_cube"):
         return synth.knn_4m_scene()
     if name == "knn_250k":
         return synth.knn_250k_scene()
@@ -899,7 +903,7 @@ class OracleRunner:
         t = time.perf_counter()
         if self.centers is not None:
             o.radius(sc.pos, self.centers[q], sc.box, sc.cyclic_mask, sc.r, None)
-        elif self.name == "knn_4m":
+        elif self.name in ("knn_4m", "knn_4m_cube"):
             o.knn(sc.pos, sc.pos[q], sc.box, sc.cyclic_mask, 16, sc.r, q)
         elif self.name == "walk_1m":
             o.reduce(sc.pos, q, sc.box, sc.cyclic_mask, sc.r)

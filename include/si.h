@@ -152,8 +152,13 @@ si_status si_grid_get_info(const si_grid *g, si_grid_info *info);
  * its estimated cost is below the spherical index's (default 1.2; 0: always
  * the list, +inf: never).  cube_below (>= 0, cell units): a radius query with
  * r / s below it takes the bin-lattice cube scan instead of the spherical
- * index (default 0: never).  Every choice returns the same lists. */
-si_status si_grid_set_method(si_grid *g, float list_weight, float cube_below);
+ * index (default 0: never).  knn_cube_below (>= 0, cell units): the
+ * Appendix's distinct reversal distance of the K-nearest query, whose
+ * r_max / s below it takes the bin lattice (every cell of the bounding cube
+ * of the r_max sphere, the list of the K nearest kept per query, the cut
+ * shrinking as they are found; default 0: never).  Every choice returns the
+ * same lists. */
+si_status si_grid_set_method(si_grid *g, float list_weight, float cube_below, float knn_cube_below);
 si_status si_grid_destroy(si_grid *g);
 
 /* Fixed-radius query (Sec. I: every agent queries its neighborhood;
@@ -214,6 +219,9 @@ si_status si_query_radius_host(si_grid *g, const float *h_pos, int64_t n, float 
  * +inf padding), and
  * d_counts[m] int32 (number found).  r_max_query <= the grid's r_max
  * (+inf allowed when the grid's r_max is +inf). */
+/* flags: SI_INCLUDE_SELF, SI_FAST_D2, and SI_METHOD_CUBE for the bin-lattice
+ * walk (every cell of the bounding cube of the r_max sphere) instead of the
+ * spherical index; the results do not change. */
 si_status si_query_knn(si_grid *g, const float *d_centers, int64_t m, int k,
                        float r_max_query, uint32_t flags, int32_t *d_ids, float *d_d2,
                        int32_t *d_counts, void *stream);

@@ -214,13 +214,15 @@ class Grid:
             return off, ids[: int(total.value)]
         return off, ids
 
-    def set_method(self, list_weight: float = 1.2, cube_below: float = 0.0) -> "Grid":
+    def set_method(self, list_weight: float = 1.2, cube_below: float = 0.0, knn_cube_below: float = 0.0) -> "Grid":
         """Run-time method selection (si_grid_set_method, the Appendix's
-        weighting factor and reversal distance): the list method is taken
+        weighting factor and reversal distances): the list method is taken
         when list_weight times its estimated cost is below the sphere's
         (inf: never, 0: always); radius queries with r below cube_below cell
-        sides take the bin-lattice cube scan.  The lists do not change."""
-        N.check(self._lib.si_grid_set_method(self._h, float(list_weight), float(cube_below)), "si_grid_set_method")
+        sides, and K-nearest queries with r_max below knn_cube_below, take
+        the bin lattice.  The results do not change."""
+        N.check(self._lib.si_grid_set_method(self._h, float(list_weight), float(cube_below), float(knn_cube_below)),
+                "si_grid_set_method")
         return self
 
     def query_radius_host(self, h_pos: torch.Tensor, r: float, h_offsets: torch.Tensor, h_ids: torch.Tensor,
@@ -250,12 +252,13 @@ class Grid:
         return int(total.value)
 
     def query_knn(self, k: int, r_max=None, include_self: bool = False, with_d2: bool = True,
-                  out=None, centers=None, fast_d2: bool = False):
+                  out=None, centers=None, fast_d2: bool = False, method: str = "sphere"):
         """K nearest within r_max (None = grid's whole region), for every point
         (centers None) or for each row of a CUDA float32 (m, 4) tensor of
         query centers.  Returns (ids int32[m,k] padded -1, d2 float32[m,k]
         or None, counts int32[m]).  d2 is the FP32 rounding of the canonical
-        FP64 squared distance; fast_d2 reports the kernel's FP32 value."""
+        FP64 squared distance; fast_d2 reports the kernel's FP32 value.
+        method "cube": the bin-lattice walk (same results)."""
         dev = self._pos.device
         m = self.n
         if centers is not None:
@@ -271,7 +274,10 @@ class Grid:
             if d2 is not None:
                 _check_out(d2, torch.float32, m * k, "out d2")
         rm = float("inf") if r_max is None else float(r_max)
-        flags = (N.SI_INCLUDE_SELF if include_self else 0) | (N.SI_FAST_D2 if fast_d2 else 0)
+        if method not in ("sphere", "cube"):
+            raise ValueError(f"unknown method {method!r}")
+        flags = (N.SI_INCLUDE_SELF if include_self else 0) | (N.SI_FAST_D2 if fast_d2 else 0) | \
+                (N.SI_METHOD_CUBE if method == "cube" else 0)
         N.check(self._lib.si_query_knn(self._h, _ptr(centers), m, int(k), rm, flags, _ptr(ids), _ptr(d2),
                                        _ptr(cnt), _stream()), "si_query_knn")
         return ids, d2, cnt

@@ -53,7 +53,7 @@ SIGNATURES = {
     "si_grid_sync": (I32, [P, P]),
     "si_grid_get_info": (I32, [P, ctypes.POINTER(GridInfo)]),
     "si_grid_destroy": (I32, [P]),
-    "si_grid_set_method": (I32, [P, F, F]),
+    "si_grid_set_method": (I32, [P, F, F, F]),
     "si_query_radius": (I32, [P, P, I64, F, U32, P, P, I64, ctypes.POINTER(I64), P]),
     "si_query_radius_host": (I32, [P, P, I64, F, U32, P, P, I64, ctypes.POINTER(I64), P]),
     "si_query_knn": (I32, [P, P, I64, I32, F, U32, P, P, P, P]),

@@ -874,12 +874,13 @@ extern "C" si_status si_grid_get_info(const si_grid *g, si_grid_info *info) {
   return SI_OK;
 }
 
-extern "C" si_status si_grid_set_method(si_grid *g, float list_weight, float cube_below) {
+extern "C" si_status si_grid_set_method(si_grid *g, float list_weight, float cube_below, float knn_cube_below) {
   if (!g) return fail(SI_ERR_INVALID, "null grid");
-  if (!(list_weight >= 0.f) || !(cube_below >= 0.f) || std::isnan(list_weight) || std::isnan(cube_below))
-    return fail(SI_ERR_INVALID, "list_weight and cube_below must be >= 0");
+  if (!(list_weight >= 0.f) || !(cube_below >= 0.f) || !(knn_cube_below >= 0.f))
+    return fail(SI_ERR_INVALID, "list_weight, cube_below and knn_cube_below must be >= 0");
   g->list_weight = (double)list_weight;
   g->cube_below = (double)cube_below;
+  g->knn_cube_below = (double)knn_cube_below;
   return SI_OK;
 }
 

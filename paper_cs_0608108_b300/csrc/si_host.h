@@ -159,6 +159,7 @@ struct si_grid {
   // queries take the bin-lattice cube scan
   double list_weight = 1.2;
   double cube_below = 0.0;
+  double knn_cube_below = 0.0;   // the same reversal for K-nearest queries (r_max, cell units)
   int64_t n_cells = 0;
   si::DevTables tables;
   // device arrays

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(GridDev g, int K, float dma
     }
   };
 
-  if (!Q.outside) {
+  if (!Q.outside && !(flags & SI_METHOD_CUBE)) {
     // Center to edge over x-rows (y-z minimum bound b2 ascending).  For each
     // row the exact y-z distance of the query and the current cut give the
     // x-interval of cells that can still hold a closer point: one contiguous
@@ -695,7 +695,7 @@ extern "C" si_status si_query_knn(si_grid *g, const float *d_centers, int64_t m,
   }
   if (k < 1 || k > 64) return fail(SI_ERR_INVALID, "k must be in [1, 64]");
   if (!d_ids || !d_counts) return fail(SI_ERR_INVALID, "null output");
-  if (flags & ~(SI_INCLUDE_SELF | SI_FAST_D2)) return fail(SI_ERR_INVALID, "unknown flags");
+  if (flags & ~(SI_INCLUDE_SELF | SI_FAST_D2 | SI_METHOD_CUBE)) return fail(SI_ERR_INVALID, "unknown flags");
   const bool unb = !(r_max_query > 0.f) || std::isinf(r_max_query);
   if (unb && !g->lat.unbounded) return fail(SI_ERR_INVALID, "unbounded r_max needs an unbounded grid");
   if (!unb && !g->lat.unbounded && (double)r_max_query > (double)g->desc.r_max)
@@ -737,11 +737,15 @@ extern "C" si_status si_query_knn(si_grid *g, const float *d_centers, int64_t m,
     list = g->clist0;
     fallq = g->clong;
   }
-  if (unb) {
-    // no bound: the per-thread walk with the shrinking cut
+  // the bin lattice (SI_METHOD_CUBE, or the reversal distance of
+  // si_grid_set_method): every cell of the bounding cube of the r_max sphere
+  if (!unb && (double)r_max_query * (double)lat.inv_s < g->knn_cube_below) flags |= SI_METHOD_CUBE;
+  if (unb || (flags & SI_METHOD_CUBE)) {
+    // no bound, or the cube: the per-thread walk with the shrinking cut
     const unsigned blocks = (unsigned)((m + kKnnThreads - 1) / kKnnThreads);
-    SI_KLAUNCH("k_knn", st, k_knn<<<blocks, kKnnThreads, smem, st>>>(dv, k, dmax_g, n_query, B, pb, flags,
-                                                                     d_ids, d_d2, d_counts, list));
+    SI_KLAUNCH((flags & SI_METHOD_CUBE) ? "k_knn_cube" : "k_knn", st,
+               k_knn<<<blocks, kKnnThreads, smem, st>>>(dv, k, dmax_g, n_query, B, pb, flags, d_ids, d_d2, d_counts,
+                                                        list));
     return SI_OK;
   }
   // first cut: the radius expected to hold `want` points at the mean load

@@ -138,6 +138,32 @@ def test_include_self_through_both_kernels(k, mask):
     assert np.all(ids[:, 0] == q) and np.all(d2[:, 0] == 0.0)
 
 
+@pytest.mark.parametrize("k", [1, 16, 64])
+@pytest.mark.parametrize("mask", [7, 0])
+def test_bin_lattice_walk_gives_the_same_results(k, mask):
+    # the K-nearest query through the bin lattice (every cell of the bounding
+    # cube of the r_max sphere): the oracle's ids, counts and distances
+    pos = synth.uniform_points(20_000, 80 + mask)
+    scene = synth.Scene(pos, (0, 0, 0), 1 / 32, (5, 5, 5), mask, 3 / 32)
+    g = gpu_grid(scene)
+    ids, d2, cnt = g.query_knn(k, r_max=scene.r, method="cube")
+    g.sync()
+    check(scene, k, scene.r, ids.cpu().numpy(), d2.cpu().numpy(), cnt.cpu().numpy(), np.arange(scene.n))
+
+
+def test_knn_reversal_distance_switches_to_the_bin_lattice():
+    from test_gpu_centers import kernels_run
+    pos = synth.uniform_points(10_000, 91)
+    scene = synth.Scene(pos, (0, 0, 0), 1 / 32, (5, 5, 5), 7, 2 / 32)
+    g = gpu_grid(scene)
+    ref = [t.cpu().numpy() for t in g.query_knn(8, r_max=scene.r)]
+    assert "k_knn_cube" not in kernels_run(lambda: g.query_knn(8, r_max=scene.r))
+    g.set_method(knn_cube_below=3.0)        # r_max = 2 cells < 3: the bin lattice
+    assert "k_knn_cube" in kernels_run(lambda: g.query_knn(8, r_max=scene.r))
+    got = [t.cpu().numpy() for t in g.query_knn(8, r_max=scene.r)]
+    assert all(np.array_equal(a, b) for a, b in zip(ref, got))
+
+
 def test_fast_distances_within_their_bound():
     # SI_FAST_D2: the same ids and counts, the kernel's FP32 squared distance
     # within 12u D2 + 16u L sqrt(D2) of the canonical D2
