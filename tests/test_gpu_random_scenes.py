@@ -1,0 +1,76 @@
+"""Seeded random scenes across the parameter space, every result against the
+oracle: lattices of different shapes (anisotropic powers of two, cell sides
+that are not powers of two, offset origins), every cyclic mask, uniform and
+clustered points (some outside the region on non-cyclic axes), radii from
+below a cell to several cells, all-agents radius lists through every method,
+and K-nearest queries (K from 1 to 64, ids, counts and distances)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_cs_0608108_b300 import synth
+
+from gpu_helpers import assert_csr_equal, gpu_grid, oracle_radius
+
+pytestmark = pytest.mark.gpu
+
+
+def random_scene(seed):
+    rng = np.random.default_rng(seed)
+    log2 = tuple(int(x) for x in rng.integers(3, 7, 3))
+    s = float(np.float32(rng.choice([1 / 16, 1 / 32, 0.37, 0.0625 * 1.3])))
+    origin = tuple(float(np.float32(x)) for x in rng.uniform(-2, 2, 3))
+    mask = int(rng.integers(0, 8))
+    box = tuple(s * (1 << w) for w in log2)
+    n = int(rng.integers(500, 12_000))
+    if rng.random() < 0.5:
+        pos = synth.uniform_points(n, seed, box=box, origin=origin)
+    else:   # clusters: crowded cells next to empty ones
+        k = int(rng.integers(2, 9))
+        c = rng.uniform(0, 1, (k, 3)) * np.array(box) + np.array(origin)
+        lab = rng.integers(0, k, n)
+        x = c[lab] + rng.normal(0, 0.6 * s, (n, 3))
+        for a in range(3):
+            if (mask >> a) & 1:   # wrapped into the box on cyclic axes
+                x[:, a] = origin[a] + np.mod(x[:, a] - origin[a], box[a])
+        pos = np.zeros((n, 4), np.float32)
+        pos[:, :3] = x.astype(np.float32)
+        for a in range(3):   # float32 rounding may land on the upper edge
+            if (mask >> a) & 1:
+                hi = np.float32(origin[a] + box[a])
+                pos[:, a] = np.where(pos[:, a] >= hi, np.float32(origin[a]), pos[:, a])
+    for a in range(3):   # a few points outside the region on non-cyclic axes
+        if not (mask >> a) & 1:
+            pos[a * 3:(a + 1) * 3, a] = np.float32(origin[a] - 0.5 * s if a % 2 else origin[a] + box[a] + 0.3 * s)
+    # radius: below a cell to several cells, within what a cyclic axis allows
+    gmin = min((1 << log2[a]) for a in range(3) if (mask >> a) & 1) if mask else 64
+    rmax_cells = max(0.3, min(3.5, (gmin - 1) / 2 - 1.01))
+    r = float(rng.uniform(0.3, rmax_cells)) * s
+    return synth.Scene(pos, origin, s, log2, mask, r), rng
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_scene_radius_every_method(seed):
+    scene, _ = random_scene(1000 + seed)
+    off_o, ids_o = oracle_radius(scene)
+    g = gpu_grid(scene)
+    for method, walk in (("sphere", "classes"), ("sphere", "paper"), ("cube", "classes"), ("list", "classes"),
+                         ("sphere_only", "planes")):
+        off, ids = g.query_radius(scene.r, method=method, walk=walk)
+        g.sync()
+        assert_csr_equal(off.cpu().numpy(), ids.cpu().numpy(), off_o, ids_o)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_scene_knn(seed):
+    scene, rng = random_scene(2000 + seed)
+    g = gpu_grid(scene)
+    r = float(np.float32(scene.r))
+    for k in sorted({int(rng.integers(1, 17)), int(rng.integers(17, 65))}):
+        ids, d2, cnt = g.query_knn(k, r_max=scene.r)
+        g.sync()
+        oi, od, oc = oracle.knn(scene.pos, scene.pos, scene.box, scene.cyclic_mask, k, r, np.arange(scene.n))
+        assert np.array_equal(cnt.cpu().numpy(), oc)
+        assert np.array_equal(ids.cpu().numpy(), oi)
+        fin = np.isfinite(od)
+        assert np.array_equal(d2.cpu().numpy()[fin], od[fin].astype(np.float32))
