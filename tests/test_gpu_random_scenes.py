@@ -3,7 +3,8 @@ oracle: lattices of different shapes (anisotropic powers of two, cell sides
 that are not powers of two, offset origins), every cyclic mask, uniform and
 clustered points (some outside the region on non-cyclic axes), radii from
 below a cell to several cells, all-agents radius lists through every method,
-and K-nearest queries (K from 1 to 64, ids, counts and distances)."""
+K-nearest queries (K from 1 to 64, ids, counts and distances), and both
+queries from random centers."""
 import numpy as np
 import pytest
 
@@ -74,3 +75,35 @@ def test_random_scene_knn(seed):
         assert np.array_equal(ids.cpu().numpy(), oi)
         fin = np.isfinite(od)
         assert np.array_equal(d2.cpu().numpy()[fin], od[fin].astype(np.float32))
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_scene_from_centers(seed):
+    # caller-given centers: uniform over the region and a little beyond it on
+    # non-cyclic axes, radius lists and K nearest against the oracle
+    scene, rng = random_scene(3000 + seed)
+    g = gpu_grid(scene)
+    m = int(rng.integers(100, 4000))
+    c = np.zeros((m, 4), np.float32)
+    for a in range(3):
+        lo, L = scene.origin[a], scene.box[a]
+        if (scene.cyclic_mask >> a) & 1:
+            x = (lo + rng.random(m) * L).astype(np.float32)
+            x = np.where(x >= np.float32(lo + L), np.float32(lo), x)
+        else:
+            x = (lo - 0.1 * L + rng.random(m) * 1.2 * L).astype(np.float32)
+        c[:, a] = x
+    import torch
+    cd = torch.from_numpy(c).cuda()
+    off, ids = g.query_radius(scene.r, centers=cd)
+    g.sync()
+    r = float(np.float32(scene.r))
+    off_o, ids_o = oracle.radius(scene.pos, c, scene.box, scene.cyclic_mask, r, None)
+    assert_csr_equal(off.cpu().numpy(), ids.cpu().numpy(), off_o, ids_o)
+    k = int(rng.integers(1, 65))
+    ki, kd, kc = g.query_knn(k, r_max=scene.r, centers=cd)
+    g.sync()
+    oi, od, oc = oracle.knn(scene.pos, c, scene.box, scene.cyclic_mask, k, r, None)
+    assert np.array_equal(kc.cpu().numpy(), oc) and np.array_equal(ki.cpu().numpy(), oi)
+    fin = np.isfinite(od)
+    assert np.array_equal(kd.cpu().numpy()[fin], od[fin].astype(np.float32))
