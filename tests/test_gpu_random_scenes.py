@@ -3,8 +3,8 @@ oracle: lattices of different shapes (anisotropic powers of two, cell sides
 that are not powers of two, offset origins), every cyclic mask, uniform and
 clustered points (some outside the region on non-cyclic axes), radii from
 below a cell to several cells, all-agents radius lists through every method,
-K-nearest queries (K from 1 to 64, ids, counts and distances), and both
-queries from random centers."""
+K-nearest queries (K from 1 to 64, ids, counts and distances), both
+queries from random centers, and the scenes as one batch."""
 import numpy as np
 import pytest
 
@@ -107,3 +107,33 @@ def test_random_scene_from_centers(seed):
     assert np.array_equal(kc.cpu().numpy(), oc) and np.array_equal(ki.cpu().numpy(), oi)
     fin = np.isfinite(od)
     assert np.array_equal(kd.cpu().numpy()[fin], od[fin].astype(np.float32))
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_random_scenes_in_one_batch(seed):
+    # the random scenes above (uniform and clustered, every mask) served as
+    # one batch under random planner choices, graph replays included
+    import torch
+    from paper_cs_0608108_b300 import Batch, default_batch_params
+    from gpu_helpers import to_dev
+    rng = np.random.default_rng(4000 + seed)
+    scenes = [random_scene(5000 + 20 * seed + i)[0] for i in range(int(rng.integers(4, 20)))]
+    ref = [oracle_radius(sc) for sc in scenes]
+    p = default_batch_params()
+    p["heavy_hits"] = float(rng.choice([0.0, 4.0, 24.0, 1e9]))
+    p["q_tile"] = int(rng.choice([64, 128, 256]))
+    p["branches"] = int(rng.integers(1, 9))
+    p["blocks_per_sm"] = 2048 // p["q_tile"] // 2
+    pos = [to_dev(sc.pos) for sc in scenes]
+    offs = [torch.empty(sc.n + 1, dtype=torch.int64, device="cuda") for sc in scenes]
+    ids = [torch.empty(int(o[-1]) + 1, dtype=torch.int32, device="cuda") for o, _ in ref]
+    b = Batch(list(zip(scenes, pos)), offs, ids, params=p)
+    for use_graph in (False, True, True):
+        for t in ids:
+            t.fill_(-7)
+        b.run(use_graph=use_graph)
+        totals = b.sync()
+        for k, (off_o, ids_o) in enumerate(ref):
+            o = offs[k].cpu().numpy()
+            assert totals[k] == off_o[-1]
+            assert_csr_equal(o, ids[k].cpu().numpy()[: o[-1]], off_o, ids_o)
