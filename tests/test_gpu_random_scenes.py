@@ -4,7 +4,8 @@ that are not powers of two, offset origins), every cyclic mask, uniform and
 clustered points (some outside the region on non-cyclic axes), radii from
 below a cell to several cells, all-agents radius lists through every method,
 K-nearest queries (K from 1 to 64, ids, counts and distances), both
-queries from random centers, and the scenes as one batch."""
+queries from random centers, the scenes as one batch, and the fused
+reduction (energy and gradient within 1e-4 of FP64)."""
 import numpy as np
 import pytest
 
@@ -137,3 +138,20 @@ def test_random_scenes_in_one_batch(seed):
             o = offs[k].cpu().numpy()
             assert totals[k] == off_o[-1]
             assert_csr_equal(o, ids[k].cpu().numpy()[: o[-1]], off_o, ids_o)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_scene_reduction(seed):
+    # the fused reduction on the random scenes: energy and gradient within
+    # 1e-4 of the FP64 oracle (global relative errors)
+    import torch
+    scene, _ = random_scene(6000 + seed)
+    g = gpu_grid(scene)
+    e = torch.empty(1, dtype=torch.float64, device="cuda")
+    gr = torch.empty((scene.n, 4), dtype=torch.float32, device="cuda")
+    g.neighbor_reduce(scene.r, energy=e, grad=gr)
+    g.sync()
+    eo, go = oracle.reduce(scene.pos, np.arange(scene.n), scene.box, scene.cyclic_mask, float(np.float32(scene.r)))
+    assert abs(float(e.item()) - eo.sum()) <= 1e-4 * max(eo.sum(), 1e-30)
+    G = gr.cpu().numpy()[:, :3]
+    assert np.linalg.norm(G - go) <= 1e-4 * max(np.linalg.norm(go), 1e-30)
