@@ -685,6 +685,9 @@ static void grid_free(si_grid *g) {
   cudaFree(g->io_off);
   cudaFree(g->io_ids);
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
+  if (g->side) cudaStreamDestroy(g->side);
+  if (g->fork_ev) cudaEventDestroy(g->fork_ev);
+  if (g->join_ev) cudaEventDestroy(g->join_ev);
   free_tables(g->tables);
   delete g;
 }
@@ -872,6 +875,22 @@ extern "C" si_status si_grid_get_info(const si_grid *g, si_grid_info *info) {
   info->table_n_max = g->tables.n_max;
   info->spec_shells = g->tables.spec_shells;
   return SI_OK;
+}
+
+bool si_grid::ensure_side() {
+  if (side) return true;
+  if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming) != cudaSuccess) {
+    if (side) cudaStreamDestroy(side);
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    if (join_ev) cudaEventDestroy(join_ev);
+    side = nullptr;
+    fork_ev = join_ev = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  return true;
 }
 
 extern "C" si_status si_grid_set_method(si_grid *g, float list_weight, float cube_below, float knn_cube_below) {

@@ -217,6 +217,12 @@ struct si_grid {
   double *partial = nullptr;     // reduce partial sums
   int64_t partial_len = 0;
   long long *h_pinned = nullptr; // pinned host scratch (2 values)
+  // a second stream for the per-query kernels of a radius query, which run
+  // beside the crowded cells' kernels (forked from and joined to the
+  // caller's stream by events, so CUDA graph capture follows them)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  bool ensure_side();
   // query centers in coarse cell order (si_centers.cu), grown on demand
   int64_t ccap = 0;
   float4 *cpos = nullptr;        // ccap: positions

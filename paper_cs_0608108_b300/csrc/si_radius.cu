@@ -746,13 +746,32 @@ static si_status query_radius_centers(si_grid *g, const float *d_centers, int64_
   const long long lstride = g->cstage_cap;
   const unsigned blocks = (unsigned)((std::max<int64_t>(m, 1) + kQueryThreads - 1) / kQueryThreads);
   SI_CUDA_TRY(cudaMemsetAsync(off, 0, sizeof(long long), st));
+  // the warp-per-center kernel on the side stream, beside the thread-per-center one
+  const bool fork = split && g->ensure_side();
+  cudaStream_t sq = fork ? g->side : st;
+  auto fork_side = [&]() -> si_status {
+    if (fork) {
+      SI_CUDA_TRY(cudaEventRecord(g->fork_ev, st));
+      SI_CUDA_TRY(cudaStreamWaitEvent(sq, g->fork_ev, 0));
+    }
+    return SI_OK;
+  };
+  auto join_side = [&]() -> si_status {
+    if (fork) {
+      SI_CUDA_TRY(cudaEventRecord(g->join_ev, sq));
+      SI_CUDA_TRY(cudaStreamWaitEvent(st, g->join_ev, 0));
+    }
+    return SI_OK;
+  };
   if (m > 0) {
+    if ((s = fork_side()) != SI_OK) return s;
     if ((s = launch_light<false>(walk, g, dv, P, B, flags, 0u, off + 1, nullptr, nullptr, 0, nullptr, blocks,
                                  g->clist0, lstage, lstride, st)) != SI_OK)
       return s;
     if (split && (s = launch_dense<false>(g, dv, P, B, flags, g->clist1, off + 1, nullptr, nullptr, 0, nullptr,
-                                          st)) != SI_OK)
+                                          sq)) != SI_OK)
       return s;
+    if ((s = join_side()) != SI_OK) return s;
     if ((s = scan_inclusive_i64(off + 1, off + 1, m, g->cscan64, st)) != SI_OK) return s;
   }
   if (h_total) {
@@ -764,12 +783,14 @@ static si_status query_radius_centers(si_grid *g, const float *d_centers, int64_
   if (m == 0) return SI_OK;
   SI_CUDA_TRY(cudaMemsetAsync(g->clong, 0, sizeof(int), st));
   SI_CUDA_TRY(cudaMemsetAsync(g->chuge, 0, sizeof(int), st));
+  if ((s = fork_side()) != SI_OK) return s;
   if ((s = launch_light<true>(walk, g, dv, P, B, flags, 0u, nullptr, off, d_ids, ids_capacity, g->clong, blocks,
                               g->clist0, lstage, lstride, st)) != SI_OK)
     return s;
   if (split && (s = launch_dense<true>(g, dv, P, B, flags, g->clist1, nullptr, off, d_ids, ids_capacity, g->clong,
-                                       st)) != SI_OK)
+                                       sq)) != SI_OK)
     return s;
+  if ((s = join_side()) != SI_OK) return s;
   if (!(flags & SI_NO_SORT)) return launch_sorts(off, d_ids, g->clong, g->chuge, st);
   return SI_OK;
 }
@@ -852,11 +873,19 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
     SI_CUDA_TRY(cudaMemsetAsync(g->scr_top, 0, sizeof(unsigned long long), st));
     if (m == 0) return SI_OK;
     si_status r;
+    // the per-query kernels (light and dense cells) on the side stream when
+    // the crowded cells' kernels run beside them on this one
+    const bool fork = heavy && g->ensure_side();
+    cudaStream_t sq = fork ? g->side : st;
+    if (fork) {
+      SI_CUDA_TRY(cudaEventRecord(g->fork_ev, st));
+      SI_CUDA_TRY(cudaStreamWaitEvent(sq, g->fork_ev, 0));
+    }
     if ((r = launch_light<false>(walk, g, dv, P, B, flags, skip, off + 1, nullptr, nullptr, 0,
-                                 nullptr, blocks, light_list, g->lstage, (long long)g->cap, st)) != SI_OK)
+                                 nullptr, blocks, light_list, g->lstage, (long long)g->cap, sq)) != SI_OK)
       return r;
     if (dense_path(walk, g) &&
-        (r = launch_dense<false>(g, dv, P, B, flags, g->denseq, off + 1, nullptr, nullptr, 0, nullptr, st)) !=
+        (r = launch_dense<false>(g, dv, P, B, flags, g->denseq, off + 1, nullptr, nullptr, 0, nullptr, sq)) !=
             SI_OK)
       return r;
     if (heavy) {
@@ -879,6 +908,10 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
                  k_radius_over<false><<<148 * 4, kQueryThreads, 0, st>>>(dv, P, B, flags, g->over,
                                                                          off + 1, nullptr, nullptr, 0,
                                                                          nullptr));
+    }
+    if (fork) {
+      SI_CUDA_TRY(cudaEventRecord(g->join_ev, sq));
+      SI_CUDA_TRY(cudaStreamWaitEvent(st, g->join_ev, 0));
     }
     return scan_inclusive_i64(off + 1, off + 1, m, g->scan_i64, st);
   };
@@ -909,8 +942,21 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   if (m == 0) return SI_OK;
   SI_CUDA_TRY(cudaMemsetAsync(g->longq, 0, sizeof(int), st));
   SI_CUDA_TRY(cudaMemsetAsync(g->hugeq, 0, sizeof(int), st));
+  // write pass: the per-query kernels on the side stream again, beside the
+  // expansion of the crowded cells' masks (every kernel writes its own
+  // queries' lists; the long-list queue is filled with atomics)
+  const bool fork = heavy && g->ensure_side();
+  cudaStream_t sq = fork ? g->side : st;
+  if (fork) {
+    SI_CUDA_TRY(cudaEventRecord(g->fork_ev, st));
+    SI_CUDA_TRY(cudaStreamWaitEvent(sq, g->fork_ev, 0));
+  }
   if ((s = launch_light<true>(walk, g, dv, P, B, flags, skip, nullptr, off, d_ids, ids_capacity,
-                              g->longq, blocks, light_list, g->lstage, (long long)g->cap, st)) != SI_OK)
+                              g->longq, blocks, light_list, g->lstage, (long long)g->cap, sq)) != SI_OK)
+    return s;
+  if (dense_path(walk, g) &&
+      (s = launch_dense<true>(g, dv, P, B, flags, g->denseq, nullptr, off, d_ids, ids_capacity, g->longq, sq)) !=
+          SI_OK)
     return s;
   if (heavy) {
     if ((s = launch_cell_expand(dv, g->heavy, g->cell_rec, g->scratch, g->xitems, g->xblock, off, d_ids, ids_capacity,
@@ -921,10 +967,10 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
                                                                       off, d_ids, ids_capacity,
                                                                       g->longq));
   }
-  if (dense_path(walk, g) &&
-      (s = launch_dense<true>(g, dv, P, B, flags, g->denseq, nullptr, off, d_ids, ids_capacity, g->longq, st)) !=
-          SI_OK)
-    return s;
+  if (fork) {
+    SI_CUDA_TRY(cudaEventRecord(g->join_ev, sq));
+    SI_CUDA_TRY(cudaStreamWaitEvent(st, g->join_ev, 0));
+  }
   if (!(flags & SI_NO_SORT)) return launch_sorts(off, d_ids, g->longq, g->hugeq, st);
   return SI_OK;
 }
