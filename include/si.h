@@ -317,7 +317,7 @@ typedef struct si_batch si_batch;
  *                  fused query kernels (one thread per query): 64, 128 or 256
  *                  (default 128)
  *   branches       concurrent graph branches of the single-scene pipelines,
- *                  1..8 (default 8)
+ *                  1..32 (default 8)
  *   blocks_per_sm  resident blocks per SM of the fused persistent query
  *                  kernels, 1..2048 / q_tile (default 8) */
 typedef struct {

@@ -416,8 +416,8 @@ def batch_signature(scenes, flags: int = 0) -> str:
     return hashlib.sha1(repr((int(flags), keys)).encode()).hexdigest()
 
 
-DEFAULT_CANDIDATES = [{"heavy_hits": h, "q_tile": t, "branches": 8, "blocks_per_sm": 2048 // t // 2}
-                      for h in (0.0, 4.0, 8.0, 16.0, 24.0, 64.0) for t in (64, 128, 256)]
+DEFAULT_CANDIDATES = [{"heavy_hits": h, "q_tile": t, "branches": b, "blocks_per_sm": 2048 // t // 2}
+                      for h in (0.0, 4.0, 8.0, 16.0, 24.0, 64.0) for t in (64, 128, 256) for b in (8, 24)]
 
 
 TUNING_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "batch_tuning.json")

@@ -334,7 +334,7 @@ static bool plan_cube(double d) {
 
 static bool params_valid(const si_batch_params &p) {
   return p.heavy_hits >= 0.f && (p.q_tile == 64 || p.q_tile == 128 || p.q_tile == 256) && p.branches >= 1 &&
-         p.branches <= 8 && p.blocks_per_sm >= 1 && p.blocks_per_sm <= 2048 / p.q_tile;
+         p.branches <= 32 && p.blocks_per_sm >= 1 && p.blocks_per_sm <= 2048 / p.q_tile;
 }
 
 extern "C" si_status si_batch_default_params(si_batch_params *p) {
@@ -399,6 +399,7 @@ extern "C" si_status si_batch_create_params(const si_scene *scenes, int n_scenes
         batch_free(b);
         return fail(s, "scene " + std::to_string(k) + ": " + why);
       }
+      gr->fork = false;   // the scenes' pipelines already run side by side on the graph's branches
       b->heavy.push_back({k, gr, (double)sc.n * hits, 0});
       continue;
     }

@@ -222,6 +222,7 @@ struct si_grid {
   // caller's stream by events, so CUDA graph capture follows them)
   cudaStream_t side = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  bool fork = true;              // false: one stream (the batch's scene pipelines run on branches already)
   bool ensure_side();
   // query centers in coarse cell order (si_centers.cu), grown on demand
   int64_t ccap = 0;

@@ -747,7 +747,7 @@ static si_status query_radius_centers(si_grid *g, const float *d_centers, int64_
   const unsigned blocks = (unsigned)((std::max<int64_t>(m, 1) + kQueryThreads - 1) / kQueryThreads);
   SI_CUDA_TRY(cudaMemsetAsync(off, 0, sizeof(long long), st));
   // the warp-per-center kernel on the side stream, beside the thread-per-center one
-  const bool fork = split && g->ensure_side();
+  const bool fork = split && g->fork && g->ensure_side();
   cudaStream_t sq = fork ? g->side : st;
   auto fork_side = [&]() -> si_status {
     if (fork) {
@@ -875,7 +875,7 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
     si_status r;
     // the per-query kernels (light and dense cells) on the side stream when
     // the crowded cells' kernels run beside them on this one
-    const bool fork = heavy && g->ensure_side();
+    const bool fork = heavy && g->fork && g->ensure_side();
     cudaStream_t sq = fork ? g->side : st;
     if (fork) {
       SI_CUDA_TRY(cudaEventRecord(g->fork_ev, st));
@@ -945,7 +945,7 @@ extern "C" si_status si_query_radius(si_grid *g, const float *d_centers, int64_t
   // write pass: the per-query kernels on the side stream again, beside the
   // expansion of the crowded cells' masks (every kernel writes its own
   // queries' lists; the long-list queue is filled with atomics)
-  const bool fork = heavy && g->ensure_side();
+  const bool fork = heavy && g->fork && g->ensure_side();
   cudaStream_t sq = fork ? g->side : st;
   if (fork) {
     SI_CUDA_TRY(cudaEventRecord(g->fork_ev, st));
