@@ -234,12 +234,13 @@ class RadiusWork:
         # independent scenes run on streams of their own (forked from and
         # joined to the current stream, so graph capture follows them)
         self.streams = [torch.cuda.Stream() for _ in scenes] if len(scenes) > 1 else None
+        self.serial = False                  # one stream (the per-kernel timing pass)
 
     def step(self):
         import torch
         cur = torch.cuda.current_stream()
         for k, (g, p, s, off, ids) in enumerate(zip(self.grids, self.pos, self.scenes, self.off, self.ids)):
-            if self.streams is None:
+            if self.streams is None or self.serial:
                 g.build(p)
                 g.query_radius(s.r, method=self.method, walk=self.walk, out_offsets=off, out_ids=ids,
                                sync_total=False)
@@ -249,7 +250,7 @@ class RadiusWork:
                 g.build(p)
                 g.query_radius(s.r, method=self.method, walk=self.walk, out_offsets=off, out_ids=ids,
                                sync_total=False)
-        if self.streams is not None:
+        if self.streams is not None and not self.serial:
             for st in self.streams:
                 cur.wait_stream(st)
 
@@ -351,6 +352,16 @@ class RadiusWork:
                             ("k_cell_group", 4)):
                 out.setdefault(name, []).append(p[c])
         return {kk: float(np.mean(v)) for kk, v in out.items()}
+
+    def step_pairs(self):
+        """Candidate pair tests of one step, every scene, every cell class."""
+        if self.method == "cube":
+            return None
+        tot = 0
+        for k, s in enumerate(self.scenes):
+            start, _, _ = (t.cpu().numpy() for t in self.grids[k].cell_arrays())
+            tot += sum(candidate_pairs(s, start, self.classes(k, start)).values())
+        return float(tot)
 
 
 def e2e_radius_host(work, steps, warmup):
@@ -874,6 +885,43 @@ def time_steps(work, steps, warmup, flush, graph=None):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+# kernel name -> phase of the step (bin: keys, scatter and the order inside
+# cells; scan: the prefix sums of the binning and of the list offsets; query:
+# the walks and the cell kernels' tests; sort: the sorts of long lists;
+# expand: the heavy cells' lists written from their hit masks)
+_PHASE = (("expand", ("k_expand", "k_cell_expand")), ("sort", ("k_sort",)), ("scan", ("scan",)),
+          ("bin", ("k_bin", "k_cell_order", "k_center_key", "k_center_scatter")))
+
+
+def phase_split(rows, steps):
+    """Milliseconds per step of each phase, from the per-kernel timing pass
+    (kernels one after another, so the phases add up to more than a step in
+    which streams overlap)."""
+    if not rows:
+        return None
+    out = {}
+    for name, (cnt, tot) in rows.items():
+        ph = next((p for p, keys in _PHASE if any(k in name for k in keys)), "query")
+        out[ph] = out.get(ph, 0.0) + tot / max(steps, 1)
+    return {k: round(v, 4) for k, v in sorted(out.items())}
+
+
+def step_rates(work, ms_step):
+    """Queries, list entries (hits) and candidate pair tests per second of the
+    timed step (the pair tests are the algorithmic ones: every candidate the
+    walk of the method reaches; None where the workload does not count them)."""
+    out = {"queries_per_s": work.queries / (ms_step * 1e-3)}
+    hits = getattr(work, "totals", None)
+    if hits is not None:
+        out["hits_per_s"] = float(sum(hits)) / (ms_step * 1e-3)
+    pairs = getattr(work, "step_pairs", None)
+    if pairs is not None:
+        p = pairs()
+        if p:
+            out["candidate_pairs_per_s"] = p / (ms_step * 1e-3)
+    return out
+
+
 def kernel_report(lib):
     buf = ctypes.create_string_buffer(1 << 16)
     lib.si_kernel_timing_report(buf, len(buf))
@@ -976,6 +1024,20 @@ def tier_b(name):
             t += time.perf_counter() - t0
             q += sc.n
         out[method] = {"value": q / t, "seconds": t}
+    # one thread, on every 32nd query of each scene (binning included)
+    one = {"threads": 1, "sample": "every 32nd query of each scene, binning of the whole scene included"}
+    for method in ("sphere", "cube"):
+        q, t = 0, 0.0
+        for make in scenes:
+            sc = make()
+            sel = np.arange(0, sc.n, 32, dtype=np.int64)
+            t0 = time.perf_counter()
+            oracle.cells_radius(sc.pos, sc.origin, sc.cell_size, sc.log2_cells, sc.cyclic_mask,
+                                float(np.float32(sc.r)), queries=sel, method=method, threads=1)
+            t += time.perf_counter() - t0
+            q += sel.shape[0]
+        one[method] = {"value": q / t, "seconds": t}
+    out["single_thread"] = one
     return out
 
 
@@ -1077,12 +1139,19 @@ def main():
     work.check()
     ms_step = slowest_rank_ms(float(np.mean(ms)))
     value = job_value(work.queries, world, ms_step)
-    # per-kernel timing pass (CUDA events around each launch, same stream)
+    # per-kernel timing pass (CUDA events around each launch, same stream);
+    # the library and the scenes run their kernels one after another here,
+    # so each launch is timed alone (the shares then compare with the ncu
+    # launch list, which serialises launches too)
     lib.si_kernel_timing_enable(1)
+    if hasattr(work, "serial"):
+        work.serial = True
     kernel_report(lib)
     time_steps(work, args.steps, 1, flush)
     rows = kernel_report(lib)
     lib.si_kernel_timing_enable(0)
+    if hasattr(work, "serial"):
+        work.serial = False
     alg = work.algorithmic_bytes()
     peak, peak_kind = peaks()
     from paper_cs_0608108_b300 import measure_pair_rate
@@ -1113,6 +1182,8 @@ def main():
                            "peak_kind": "measured: si_measure_pair_rate, packed f32x2 pair tests, best of 5",
                            "algorithmic_pairs_per_launch": pairs}
     step_gbs = work.step_bytes() / (ms_step * 1e-3) / 1e9
+    rates = step_rates(work, ms_step)
+    phases = phase_split(rows, args.steps)
     if roof is not None:
         roof["step"] = {"achieved": step_gbs, "frac": step_gbs / peak, "unit": "GB/s",
                         "algorithmic_bytes": work.step_bytes()}
@@ -1140,6 +1211,7 @@ def main():
                        "queries_per_step": work.queries, "parallelism": f"replicas x{world}"},
             "step_algorithmic_gbs": step_gbs, "step_hbm_frac": step_gbs / peak,
             "roofline": roof, "gpu_launches": int(launches), "clocks": clk.summary(), "e2e": e2e,
+            "rates": rates, "phases_ms_per_step": phases,
             "ms_samples": {"median": float(np.median(ms)), "min": float(np.min(ms)),
                            "max": float(np.max(ms))}}
     if args.workload == "radius_1m" and not args.no_compare:

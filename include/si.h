@@ -372,7 +372,10 @@ int64_t si_launch_count(void);
 /* Per-kernel device timing, for benchmarks.  While enabled, every kernel
  * launch of the library (and every batch graph replay) is bracketed by two
  * CUDA events recorded on its own stream; launches made during a stream
- * capture are not timed.  Not thread-safe with concurrent library calls. */
+ * capture are not timed.  While enabled, a query issues all its kernels in
+ * order on the caller's stream (no second stream for the per-query kernels),
+ * so that each launch is timed alone.  Not thread-safe with concurrent
+ * library calls. */
 si_status si_kernel_timing_enable(int enable);
 
 /* Synchronise the device, aggregate the launches timed since the last report

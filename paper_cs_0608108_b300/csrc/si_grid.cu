@@ -878,6 +878,12 @@ extern "C" si_status si_grid_get_info(const si_grid *g, si_grid_info *info) {
 }
 
 bool si_grid::ensure_side() {
+  // per-kernel timing serialises the kernels on the caller's stream, so
+  // that each launch's two events bracket that kernel alone
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (g_prof_on) return false;
+  }
   if (side) return true;
   if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming) != cudaSuccess ||
