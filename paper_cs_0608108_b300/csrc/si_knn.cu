@@ -266,10 +266,10 @@ __device__ __forceinline__ void knn_warp_query(const GridDev &g, int s, unsigned
   };
   // every candidate within the cut (cut2 = its square in cell units, nrows
   // the rows whose y-z bound is within it, Bc its guard band), decided
-  // exactly, into the buffer.  Lane i takes row base + i of a 32-row batch:
+  // exactly, into the buffer.  Lane i decodes row base + i of a 32-row batch:
   // its x-interval of cells is one run of sorted points (and a second run
-  // where it wraps a cyclic x axis), which the lane then walks point by
-  // point while any lane of the warp has points left.
+  // where it wraps a cyclic x axis); the lanes then take the batch's
+  // candidates 32 at a time, whichever rows they lie in.
   auto gather = [&](float cut2, int nrows, const Band &B) {
   cnt = 0;
   overflow = false;
@@ -320,19 +320,39 @@ __device__ __forceinline__ void knn_warp_query(const GridDev &g, int s, unsigned
       }
     }
     out_any |= __any_sync(0xffffffffu, out);
+    // the batch's candidates numbered across the lanes' runs (prefix of the
+    // run lengths) and taken 32 at a time: lane t takes candidate f0 + t of
+    // the lane L that owns it (the last lane whose runs start at or before
+    // it), fetching L's run bounds and frame by shuffle
     const int nt = l0 + l1;
-    for (int k = 0; __any_sync(0xffffffffu, k < nt); ++k) {
+    const int ninc = warp_incl_scan_i(nt);
+    const int ntot = __shfl_sync(0xffffffffu, ninc, 31);
+    const int nexc = ninc - nt;
+    for (int f0 = 0; f0 < ntot; f0 += 32) {
+      const int f = f0 + lane;
+      int L = 0;
+#pragma unroll
+      for (int sh = 16; sh > 0; sh >>= 1) {
+        const int e = __shfl_sync(0xffffffffu, nexc, L + sh);
+        if (e <= f) L += sh;
+      }
+      const int k = f - __shfl_sync(0xffffffffu, nexc, L);
+      const int ob0 = __shfl_sync(0xffffffffu, b0, L), ol0 = __shfl_sync(0xffffffffu, l0, L);
+      const int ob1 = __shfl_sync(0xffffffffu, b1, L);
+      const float oqx0 = __shfl_sync(0xffffffffu, qx0, L), oqx1 = __shfl_sync(0xffffffffu, qx1, L);
+      const float oqy = __shfl_sync(0xffffffffu, qy0, L), oqz = __shfl_sync(0xffffffffu, qz0, L);
+      const bool ow0 = __shfl_sync(0xffffffffu, (int)w0, L) != 0;
       bool in = false, band = false, wr = false;
       float d = 0.f;
       int j = 0;
       float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (k < nt) {
-        const bool second = k >= l0;   // the run through the x wrap
-        j = second ? b1 + (k - l0) : b0 + k;
-        wr = second || w0;
+      if (f < ntot) {
+        const bool second = k >= ol0;   // the run through the x wrap
+        j = second ? ob1 + (k - ol0) : ob0 + k;
+        wr = second || ow0;
         if (j != self) {
           p = g.spos[j];
-          const float dx = p.x - (second ? qx1 : qx0), dy = p.y - qy0, dz = p.z - qz0;
+          const float dx = p.x - (second ? oqx1 : oqx0), dy = p.y - oqy, dz = p.z - oqz;
           d = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
           const float blo = wr ? B.lo_w : B.lo, bhi = wr ? B.hi_w : B.hi;
           in = d <= blo;
