@@ -655,61 +655,86 @@ class LoopWork(RadiusWork):
     """The plain single-scene path looped over the batch's scenes."""
 
 
+# what each workload is (the `config.description` of both arms' lines)
+DESC = {
+    "radius_1m": "1M-point all-agents radius, 128^3 cyclic, r=1.5 cells, uniform + Gaussian mixture "
+                 "(each scene's binning and query on a stream of its own)",
+    "radius_uniform": "1M uniform all-agents radius, 128^3 cyclic, r=1.5 cells",
+    "radius_mixture": "1M Gaussian-mixture all-agents radius, 128^3 cyclic, r=1.5 cells",
+    "radius_mixture_250k": "250k Gaussian-mixture all-agents radius (16 components, the 1M mixture's density), "
+                           "128^3 cyclic, r=1.5 cells",
+    "radius_uniform_cube": "1M uniform, GPU bin-lattice cube scan",
+    "radius_mixture_cube": "1M mixture, GPU bin-lattice cube scan",
+    "radius_1m_cube": "same, GPU bin-lattice cube scan",
+    "knn_4m": "4M-point K-nearest (K=16 and 64), 256^3, cyclic x,y, r_max=4 cells",
+    "knn_4m_cube": "4M-point K-nearest (K=16 and 64), 256^3, cyclic x,y, r_max=4 cells, GPU bin-lattice walk",
+    "knn_250k": "250k-point K-nearest (K=16 and 64) at the 4M configuration's density, 128x128x64, cyclic x,y, "
+                "r_max=4 cells",
+    "walk_1m": "1M-point random walk step: rebin + energy + adjoint, 128^3 cyclic, r=1.5 cells",
+    "batched": "256 uneven scenes (log-uniform 1k-200k points), one graph replay",
+    "batched_loop": "256 uneven scenes, plain path looped per scene",
+    "tiny": "20k-point radius, 32^3 non-cyclic, r=0.96 cells",
+    "terrain_1m": "1M agents on a bumpy terrain (z = 0.5 + 0.01 sin sin), 2% flying, 128^3, cyclic x, y, "
+                  "r = 1.5 cells, classes walk",
+    "terrain_1m_planes": "1M agents on a bumpy terrain (z = 0.5 + 0.01 sin sin), 2% flying, 128^3, cyclic x, y, "
+                         "r = 1.5 cells, planes walk",
+    "radius_far_20k": "20,480 uniform points, 64^3 cyclic (load 0.078), r = 24 cells, 100k uniform centers: "
+                      "the volume comparison takes the non-empty list method",
+    "radius_centers_1m": "1M Gaussian-mixture points, 128^3 cyclic, r=1.5 cells; 1M query centers, half from the "
+                         "same mixture (another seed), half uniform",
+}
+
+
+def workload_config(name, world, queries):
+    """The `config` of a bench line, the same for both arms of a workload."""
+    return {"workload": name, "description": DESC.get(name, name), "l2": "flushed between steps",
+            "queries_per_step": int(queries), "parallelism": f"replicas x{world}"}
+
+
 def make_work(name):
     from paper_cs_0608108_b300 import synth
     if name == "radius_1m":
-        return RadiusWork([synth.uniform_1m_scene(), synth.mixture_1m_scene()]), \
-            "1M-point all-agents radius, 128^3 cyclic, r=1.5 cells, uniform + Gaussian mixture " \
-            "(each scene's binning and query on a stream of its own)"
+        return RadiusWork([synth.uniform_1m_scene(), synth.mixture_1m_scene()]), DESC[name]
     if name == "radius_uniform":
-        return RadiusWork([synth.uniform_1m_scene()]), "1M uniform all-agents radius, 128^3 cyclic, r=1.5 cells"
+        return RadiusWork([synth.uniform_1m_scene()]), DESC[name]
     if name == "radius_mixture":
-        return RadiusWork([synth.mixture_1m_scene()]), "1M Gaussian-mixture all-agents radius, 128^3 cyclic, r=1.5 cells"
+        return RadiusWork([synth.mixture_1m_scene()]), DESC[name]
     if name == "radius_mixture_250k":
-        return RadiusWork([synth.mixture_250k_scene()]), \
-            "250k Gaussian-mixture all-agents radius (16 components, the 1M mixture's density), 128^3 cyclic, " \
-            "r=1.5 cells"
+        return RadiusWork([synth.mixture_250k_scene()]), DESC[name]
     if name == "radius_uniform_cube":
-        return RadiusWork([synth.uniform_1m_scene()], "cube"), "1M uniform, GPU bin-lattice cube scan"
+        return RadiusWork([synth.uniform_1m_scene()], "cube"), DESC[name]
     if name == "radius_mixture_cube":
-        return RadiusWork([synth.mixture_1m_scene()], "cube"), "1M mixture, GPU bin-lattice cube scan"
+        return RadiusWork([synth.mixture_1m_scene()], "cube"), DESC[name]
     if name == "radius_1m_cube":
-        return RadiusWork([synth.uniform_1m_scene(), synth.mixture_1m_scene()], "cube"), \
-            "same, GPU bin-lattice cube scan"
+        return RadiusWork([synth.uniform_1m_scene(), synth.mixture_1m_scene()], "cube"), DESC[name]
     if name == "knn_4m":
-        return KnnWork(synth.knn_4m_scene()), "4M-point K-nearest (K=16 and 64), 256^3, cyclic x,y, r_max=4 cells"
+        return KnnWork(synth.knn_4m_scene()), DESC[name]
     if name == "knn_4m_cube":
-        return KnnWork(synth.knn_4m_scene(), method="cube"), \
-            "4M-point K-nearest (K=16 and 64), 256^3, cyclic x,y, r_max=4 cells, GPU bin-lattice walk"
+        return KnnWork(synth.knn_4m_scene(), method="cube"), DESC[name]
     if name == "knn_250k":
-        return KnnWork(synth.knn_250k_scene()), \
-            "250k-point K-nearest (K=16 and 64) at the 4M configuration's density, 128x128x64, cyclic x,y, " \
-            "r_max=4 cells"
+        return KnnWork(synth.knn_250k_scene()), DESC[name]
     if name == "walk_1m":
-        return WalkWork(synth.uniform_1m_scene()), \
-            "1M-point random walk step: rebin + energy + adjoint, 128^3 cyclic, r=1.5 cells"
+        return WalkWork(synth.uniform_1m_scene()), DESC[name]
     if name == "batched":
-        return BatchWork(synth.batched_scenes()), "256 uneven scenes (log-uniform 1k-200k points), one graph replay"
+        return BatchWork(synth.batched_scenes()), DESC[name]
     if name == "batched_loop":
-        return LoopWork(synth.batched_scenes()), "256 uneven scenes, plain path looped per scene"
+        return LoopWork(synth.batched_scenes()), DESC[name]
     if name == "tiny":
-        return RadiusWork([synth.tiny_scene()]), "20k-point radius, 32^3 non-cyclic, r=0.96 cells"
+        return RadiusWork([synth.tiny_scene()]), DESC[name]
     if name in ("terrain_1m", "terrain_1m_planes"):
-        sc = synth.Scene(synth.terrain_points(1_000_000, 0x51D00400), (0.0, 0.0, 0.0), 1.0 / 128, (7, 7, 7), 3,
-                         1.5 / 128, "terrain_1m")
         walk = "planes" if name.endswith("planes") else "classes"
-        return RadiusWork([sc], walk=walk), \
-            f"1M agents on a bumpy terrain (z = 0.5 + 0.01 sin sin), 2% flying, 128^3, cyclic x, y, r = 1.5 cells, " \
-            f"{walk} walk"
+        return RadiusWork([terrain_scene()], walk=walk), DESC[name]
     if name == "radius_far_20k":
-        return CentersWork(make_work_scene_far(), synth.uniform_points(100_000, 0x51D00301)), \
-            "20,480 uniform points, 64^3 cyclic (load 0.078), r = 24 cells, 100k uniform centers: " \
-            "the volume comparison takes the non-empty list method"
+        return CentersWork(make_work_scene_far(), synth.uniform_points(100_000, 0x51D00301)), DESC[name]
     if name == "radius_centers_1m":
-        return CentersWork(synth.mixture_1m_scene(), centers_1m()), \
-            "1M Gaussian-mixture points, 128^3 cyclic, r=1.5 cells; 1M query centers, half from the " \
-            "same mixture (another seed), half uniform"
+        return CentersWork(synth.mixture_1m_scene(), centers_1m()), DESC[name]
     raise SystemExit(f"unknown workload {name}")
+
+
+def terrain_scene():
+    from paper_cs_0608108_b300 import synth
+    return synth.Scene(synth.terrain_points(1_000_000, 0x51D00400), (0.0, 0.0, 0.0), 1.0 / 128, (7, 7, 7), 3,
+                       1.5 / 128, "terrain_1m")
 
 
 def make_work_scene_far():
@@ -948,8 +973,7 @@ def _oracle_scene(name):
     if name == "radius_far_20k":
         return make_work_scene_far()
     if name in ("terrain_1m", "terrain_1m_planes"):
-        return synth.Scene(synth.terrain_points(1_000_000, 0x51D00400), (0.0, 0.0, 0.0), 1.0 / 128, (7, 7, 7), 3,
-                           1.5 / 128, "terrain_1m")
+        return terrain_scene()
     if name == "tiny":
         return synth.tiny_scene()
     return synth.batched_scenes()[0]
@@ -961,29 +985,50 @@ class OracleRunner:
 
     def __init__(self, name):
         import oracle
+        from paper_cs_0608108_b300 import synth
         self.oracle = oracle
         self.name = name
-        self.sc = _oracle_scene(name)
+        # the workload's scenes (both of the two-scene step) and K values
+        if name in ("radius_1m", "radius_1m_cube"):
+            self.scs = [synth.uniform_1m_scene(), synth.mixture_1m_scene()]
+        else:
+            self.scs = [_oracle_scene(name)]
+        self.sc = self.scs[0]
+        self.knn = name in ("knn_4m", "knn_4m_cube", "knn_250k")
+        self.ks = (16, 64) if self.knn else (None,)
         self.threads = oracle.max_threads()
         self.rng = np.random.default_rng(0)
         self.centers = centers_1m() if name == "radius_centers_1m" else None
         if name == "radius_far_20k":
-            from paper_cs_0608108_b300 import synth
             self.centers = synth.uniform_points(100_000, 0x51D00301)
 
-    def run(self, m):
-        sc, o = self.sc, self.oracle
-        q = self.rng.choice(sc.n, m, replace=False)
-        t = time.perf_counter()
+    def queries_per_step(self):
+        """The queries one step of the workload answers (as the GPU arm counts them)."""
         if self.centers is not None:
-            o.radius(sc.pos, self.centers[q], sc.box, sc.cyclic_mask, sc.r, None)
-        elif self.name in ("knn_4m", "knn_4m_cube"):
-            o.knn(sc.pos, sc.pos[q], sc.box, sc.cyclic_mask, 16, sc.r, q)
-        elif self.name == "walk_1m":
-            o.reduce(sc.pos, q, sc.box, sc.cyclic_mask, sc.r)
-        else:
-            o.radius(sc.pos, sc.pos[q], sc.box, sc.cyclic_mask, sc.r, q)
-        return time.perf_counter() - t
+            return self.centers.shape[0]
+        return sum(sc.n for sc in self.scs) * len(self.ks)
+
+    def run(self, m):
+        """Time m queries, split evenly over the workload's scenes and K values."""
+        o = self.oracle
+        parts = [(sc, k) for sc in self.scs for k in self.ks]
+        t = 0.0
+        for i, (sc, k) in enumerate(parts):
+            mi = m // len(parts) + (1 if i < m % len(parts) else 0)
+            if mi == 0:
+                continue
+            q = self.rng.choice(sc.n, mi, replace=False)
+            t0 = time.perf_counter()
+            if self.centers is not None:
+                o.radius(sc.pos, self.centers[q], sc.box, sc.cyclic_mask, sc.r, None)
+            elif self.knn:
+                o.knn(sc.pos, sc.pos[q], sc.box, sc.cyclic_mask, k, sc.r, q)
+            elif self.name == "walk_1m":
+                o.reduce(sc.pos, q, sc.box, sc.cyclic_mask, sc.r)
+            else:
+                o.radius(sc.pos, sc.pos[q], sc.box, sc.cyclic_mask, sc.r, q)
+            t += time.perf_counter() - t0
+        return t
 
     def calibrate(self, seconds):
         m = max(64, self.threads * 32)   # the oracle hands out queries in chunks of 16
@@ -993,7 +1038,9 @@ class OracleRunner:
 
     def describe(self, m, total_s, steps):
         what = "query centers" if self.centers is not None else "query points"
-        return (f"{steps} x {m} random {what} of the {self.sc.n}-point workload, "
+        scenes = " + ".join(f"{sc.n}-point {sc.name}" for sc in self.scs)
+        ks = f", K = {' and '.join(str(k) for k in self.ks)}" if self.knn else ""
+        return (f"{steps} x {m} random {what} of the workload ({scenes}{ks}, split evenly), "
                 f"FP64 brute force over all points, {self.threads} threads, {total_s:.1f} s")
 
 
@@ -1086,7 +1133,8 @@ def main():
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": args.workload}, "cpu_baseline": cb,
+                "data": "synthetic", "config": workload_config(args.workload, args.gpus, r.queries_per_step()),
+                "cpu_baseline": cb,
                 "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -1206,9 +1254,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "description": desc, "l2": "flushed between steps",
-                       "step": "one CUDA graph replay of the library calls" if use_graph else "library calls",
-                       "queries_per_step": work.queries, "parallelism": f"replicas x{world}"},
+            "config": workload_config(args.workload, world, work.queries),
+            "step": "one CUDA graph replay of the library calls" if use_graph else "library calls",
             "step_algorithmic_gbs": step_gbs, "step_hbm_frac": step_gbs / peak,
             "roofline": roof, "gpu_launches": int(launches), "clocks": clk.summary(), "e2e": e2e,
             "rates": rates, "phases_ms_per_step": phases,
