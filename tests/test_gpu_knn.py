@@ -44,8 +44,12 @@ def test_tiny_config_k8_unbounded_exact():
 
 
 @pytest.mark.parametrize("mask", [7, 3, 0, 4])
-@pytest.mark.parametrize("k", [1, 5, 16, 64])
+@pytest.mark.parametrize("k", [1, 5, 16, 40, 64])
 def test_masks_and_k_within_r_max(mask, k):
+    # 0.92 points per cell, 245 expected within r_max: the warp kernel's
+    # first cut holds about K + 2 sqrt(K) + 4 candidates, so K = 40 sorts
+    # 33-64 keys (two register slots) and K = 64 around 84 (65-96 in three
+    # slots, 97-128 in four)
     pos = synth.uniform_points(30_000, 40 + mask)
     scene = synth.Scene(pos, (0, 0, 0), 1 / 32, (5, 5, 5), mask, 4 / 32)
     ids, d2, cnt = run_knn(scene, k, scene.r)
