@@ -15,14 +15,15 @@
 //     scatter, then insertion inside each small bucket) and the ordered ids
 //     are stored to the cell's record in a scratch buffer, reserved with one
 //     atomic as soon as the number of candidates is known;
-//  4. warps take (group of queries, 64 candidates) items: a lane holds two
-//     candidates, tests them against each query of the group (one ballot per
-//     32 candidates) and lane 0 stores the two hit masks to the record and
-//     adds their population counts to the query's count.
+//  4. the test phase (cell_test_phase, si_cell.cuh): a lane owns one query
+//     and builds its hit mask over each chunk of 32 candidates, which the
+//     lanes read as packed FP32 pairs; the masks go to the record and their
+//     population counts to the query's count.
 // Record of a cell in the scratch buffer: nc, the nc ordered ids, then one
 // 32-bit mask per (query, 32 candidates), query-major.  After the prefix sum,
-// k_cell_expand turns every query's masks into its ids at their place in the
-// output.
+// k_expand_items (a warp per few queries of one record) and k_cell_expand
+// (a block per split cell) turn every query's masks into its ids at their
+// place in the output.
 // Two configurations: most heavy cells fit a small block (8 warps, 1280
 // candidates, 128 queries, four blocks per SM); a cell that does not is
 // listed for the large one (16 warps, 2560 candidates, 512 queries), launched

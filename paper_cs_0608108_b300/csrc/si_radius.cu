@@ -5,8 +5,13 @@
 // order so that neighbouring threads walk neighbouring cells (their candidate
 // cells are shared through L1/L2); lists of up to 32 ids are sorted while
 // written, longer ones are queued for a warp (or block) bitonic sort.
-// Queries in heavy cells (heavy_cell): one block per cell (si_cell.cu), hit
-// masks over id-ordered candidates, expanded into sorted lists after the scan.
+// Queries in dense cells: one warp per query over the flattened class walk.
+// Queries in heavy cells (heavy_cell): one block per 2 x 2 x 2 group of heavy
+// cells (si_group.cu) or per cell (si_cell.cu), hit masks over id-ordered
+// candidates, expanded into sorted lists after the scan.  When heavy cells
+// exist, the per-query kernels run on a second stream of the grid beside the
+// heavy cells' kernels (forked and joined by events, so graph capture
+// follows them).
 #include <algorithm>
 #include <cmath>
 
