@@ -364,6 +364,27 @@ class RadiusWork:
         return float(tot)
 
 
+def host_link():
+    """Copy rate of the host link (page-locked host memory), each direction
+    on its own: best of three 512 MiB copies, GB/s."""
+    import torch
+    n = 1 << 27
+    d = torch.empty(n, dtype=torch.int32, device="cuda")
+    h = torch.empty(n, dtype=torch.int32).pin_memory()
+    out = {}
+    for name, dst, src in (("d2h_gbs", h, d), ("h2d_gbs", d, h)):
+        best = 0.0
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            best = max(best, 4 * n / (time.perf_counter() - t0) / 1e9)
+        out[name] = best
+    del d, h
+    return out
+
+
 def e2e_radius_host(work, steps, warmup):
     """The metric end to end through the C ABI with host buffers
     (si_query_radius_host): every step hands each scene's points in
@@ -1250,6 +1271,11 @@ def main():
                "pipelined": {"value": job_value(work.queries, world, p_ms), "ms_per_step": p_ms,
                              "how": "torch copies on a second stream, a step's lists copied out while the "
                                     "next step's points come in"}}
+        # the host link's own bound for these bytes (each direction alone)
+        link = host_link()
+        link["copy_bound_ms_per_step"] = (bi / link["h2d_gbs"] + bo / link["d2h_gbs"]) / 1e6
+        link["d2h_bound_ms_per_step"] = bo / link["d2h_gbs"] / 1e6
+        e2e["host_link"] = link
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
