@@ -616,13 +616,36 @@ class WalkWork:
         self.t += 1
         E = neighbor_energy(x, self.grid, self.scene.r)
         E.backward()
+        self.last = (E, x)
+
+    def check_graphs(self, rotation, outputs):
+        """The replayed graphs give what the eager step gives, frame by frame
+        (energy to 1e-12 relative, gradient to 1e-6 of its largest entry)."""
+        import torch
+        for f, gr in enumerate(rotation.graphs):
+            gr.replay()
+            torch.cuda.synchronize()
+            Eg, xg = outputs[f]
+            eg, gg = float(Eg.item()), xg.grad.detach().clone()
+            self.t = f
+            self.step()
+            torch.cuda.synchronize()
+            ee, ge = float(self.last[0].item()), self.last[1].grad
+            if abs(eg - ee) > 1e-12 * max(abs(ee), 1e-300) or \
+                    float((gg - ge).abs().max()) > 1e-6 * max(float(ge.abs().max()), 1e-30):
+                raise SystemExit(f"walk graph of frame {f} differs from the eager step: E {eg} vs {ee}")
+        self.t = 0
 
     def check(self):
         self.grid.sync()
 
     def algorithmic_bytes(self):
         n, C = self.scene.n, (1 << sum(self.scene.log2_cells)) + 1
-        return {"k_reduce": 16 * n + 4 * n + 4 * C + 16 * n, "k_bin_key": 24 * n + 8 * C,
+        # energy walk: the points, their indices and the cell starts read;
+        # adjoint walk: the same plus the gradient written (16 B a point)
+        walk = 16 * n + 4 * n + 4 * C
+        return {"k_reduce": walk, "k_reduce_eq2": walk, "k_reduce_grad": walk + 16 * n,
+                "k_reduce_grad_eq2": walk + 16 * n, "k_bin_key": 24 * n + 8 * C,
                 "k_bin_scatter": 48 * n + 4 * C}
 
     def step_bytes(self):
@@ -898,6 +921,47 @@ def capture_step(work):
         work.step()
     torch.cuda.synchronize()
     return graph, launch_count() - l0
+
+
+class _Rotation:
+    """Graphs replayed in turn (one per input frame of a rotating step)."""
+
+    def __init__(self, graphs):
+        self.graphs, self.k = graphs, 0
+
+    def replay(self):
+        self.graphs[self.k % len(self.graphs)].replay()
+        self.k += 1
+
+
+def capture_walk(work):
+    """The walk step (rebin, energy, adjoint through autograd) captured once
+    per input frame, the graphs replayed in the frames' order; returns the
+    rotation and the library kernels one step holds."""
+    import torch
+    from paper_cs_0608108_b300 import launch_count
+    graphs, outputs, per = [], [], 0
+    for f in range(len(work.frames)):
+        work.t = f
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            work.step()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        work.t = f
+        gr = torch.cuda.CUDAGraph()
+        l0 = launch_count()
+        with torch.cuda.graph(gr):
+            work.step()
+        torch.cuda.synchronize()
+        per = launch_count() - l0
+        graphs.append(gr)
+        outputs.append(work.last)
+    work.t = 0
+    rot = _Rotation(graphs)
+    work.check_graphs(rot, outputs)
+    return rot, per
 
 
 def _barrier():
@@ -1193,14 +1257,17 @@ def main():
     torch.cuda.synchronize()
     # the query workloads replay the step as one CUDA graph (the batched path
     # does the same inside the library); the plain-path loop stays eager
-    use_graph = (not args.no_graph and isinstance(work, (RadiusWork, CentersWork, KnnWork))
+    use_graph = (not args.no_graph and isinstance(work, (RadiusWork, CentersWork, KnnWork, WalkWork))
                  and not isinstance(work, LoopWork))
     graph, graph_launches = None, 0
     if use_graph:
         for _ in range(2):
             work.step()
         work.check()
-        graph, graph_launches = capture_step(work)
+        if isinstance(work, WalkWork):
+            graph, graph_launches = capture_walk(work)
+        else:
+            graph, graph_launches = capture_step(work)
     l0 = launch_count()
     with ClockSampler(local) as clk:
         ms = time_steps(work, args.steps, args.warmup, flush, graph)
@@ -1281,7 +1348,9 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": workload_config(args.workload, world, work.queries),
-            "step": "one CUDA graph replay of the library calls" if use_graph else "library calls",
+            "step": ("library calls" if not use_graph else
+                     "one CUDA graph replay of the autograd step (rebin, energy, adjoint), a graph per input frame"
+                     if isinstance(work, WalkWork) else "one CUDA graph replay of the library calls"),
             "step_algorithmic_gbs": step_gbs, "step_hbm_frac": step_gbs / peak,
             "roofline": roof, "gpu_launches": int(launches), "clocks": clk.summary(), "e2e": e2e,
             "rates": rates, "phases_ms_per_step": phases,
