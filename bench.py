@@ -1249,7 +1249,7 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     from paper_cs_0608108_b300 import _native, launch_count
     lib = _native.lib()
-    work, desc = make_work(args.workload)
+    work, _ = make_work(args.workload)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     # whole-step timing (no per-kernel events)
     if world > 1:
