@@ -611,12 +611,17 @@ si_status launch_cell_pass(const GridDev &g, const WalkParams &P, const Band &B,
 // k_cell_expand (a block per cell).  A warp goes through its item's
 // candidates a round of 32 chunks (1024 candidates) at a time: it stages
 // the round's ordered ids in its own shared rows (32 ids per row, rows
-// padded to 33 words), then expands that round's masks of each query as
-// k_cell_expand does, carrying each query's write position from round to
-// round in the register of lane t (query q0 + t).
+// padded to 36 words), then expands that round's masks of each query as
+// k_cell_expand does, but reading a lane's ids four at a time, carrying
+// each query's write position from round to round in the register of lane
+// t (query q0 + t).
 constexpr int kItemQ = 8;
 constexpr int kItemWarps = 8;
 constexpr int kItemRows = 32;
+// words per staged row: 32 ids and padding to a 16-byte multiple, so that a
+// lane reads four ids of its row at once (rows of 36 words: the eight lanes
+// of each quarter-warp phase hit distinct banks)
+constexpr int kRowW = 36;
 
 __global__ void __launch_bounds__(256) k_expand_plan(GridDev g, const int *__restrict__ heavy,
                                                      const long long *__restrict__ cell_rec,
@@ -644,13 +649,13 @@ __global__ void __launch_bounds__(kItemWarps * 32) k_expand_items(GridDev g, con
                                                                  const int *__restrict__ scratch,
                                                                  const long long *__restrict__ offsets,
                                                                  int *__restrict__ ids, long long cap) {
-  extern __shared__ int item_smem[];   // per warp: kItemRows * 33 id slots, then a 1024-id buffer
+  extern __shared__ __align__(16) int item_smem[];   // per warp: kItemRows * kRowW id slots, then a 1024-id buffer
   if (offsets[g.n] > cap) {
     if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(g.status, ST_CAPACITY);
     return;
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int *rows = item_smem + wid * (kItemRows * 33 + 1024), *buf = rows + kItemRows * 33;
+  int *rows = item_smem + wid * (kItemRows * kRowW + 1024), *buf = rows + kItemRows * kRowW;
   const int nitems = items[0].x;
   for (int it = blockIdx.x * kItemWarps + wid; it < nitems; it += gridDim.x * kItemWarps) {
     const int4 d = items[1 + it];
@@ -666,7 +671,7 @@ __global__ void __launch_bounds__(kItemWarps * 32) k_expand_items(GridDev g, con
     for (int c0 = 0; c0 < nchunk; c0 += 32) {
       __syncwarp();   // the previous round's (or item's) rows are no longer read
       const int kend = min(nc, (c0 + 32) * 32);
-      for (int k = c0 * 32 + lane; k < kend; k += 32) rows[((k >> 5) - c0) * 33 + (k & 31)] = __ldg(rec_ids + k);
+      for (int k = c0 * 32 + lane; k < kend; k += 32) rows[((k >> 5) - c0) * kRowW + (k & 31)] = __ldg(rec_ids + k);
       __syncwarp();
       for (int t = 0; t < cnt; ++t) {
         const unsigned mm = mnext;
@@ -683,12 +688,19 @@ __global__ void __launch_bounds__(kItemWarps * 32) k_expand_items(GridDev g, con
         const int c = __popc(mm);
         const int inc = warp_incl_scan_i(c);
         int o = inc - c;
-        const int *row = rows + lane * 33;   // read only where a bit is set
+        const int4 *row4 = reinterpret_cast<const int4 *>(rows + lane * kRowW);
 #pragma unroll
-        for (int b = 0; b < 32; ++b) {
-          const bool set = (mm >> b) & 1u;
-          if (set) buf[o] = row[b];
-          o += set ? 1 : 0;
+        for (int b4 = 0; b4 < 8; ++b4) {
+          const int4 v = row4[b4];   // ids 4 b4 .. 4 b4 + 3 of the lane's chunk
+          const unsigned nb = mm >> (4 * b4);
+          if (nb & 1u) buf[o] = v.x;
+          o += (int)(nb & 1u);
+          if (nb & 2u) buf[o] = v.y;
+          o += (int)((nb >> 1) & 1u);
+          if (nb & 4u) buf[o] = v.z;
+          o += (int)((nb >> 2) & 1u);
+          if (nb & 8u) buf[o] = v.w;
+          o += (int)((nb >> 3) & 1u);
         }
         __syncwarp();
         const int tot = __shfl_sync(0xffffffffu, inc, 31);
@@ -707,7 +719,7 @@ si_status launch_cell_expand(const GridDev &g, const int *heavy, const long long
   SI_CUDA_TRY(cudaMemsetAsync(blocks, 0, sizeof(int), st));
   SI_KLAUNCH("k_expand_plan", st,
              k_expand_plan<<<148 * 4, 256, 0, st>>>(g, heavy, cell_rec, scratch, items, blocks));
-  const size_t ism = (size_t)kItemWarps * (kItemRows * 33 + 1024) * sizeof(int);
+  const size_t ism = (size_t)kItemWarps * (kItemRows * kRowW + 1024) * sizeof(int);
   SI_CUDA_TRY(cudaFuncSetAttribute(k_expand_items, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
   SI_KLAUNCH("k_expand_items", st,
              k_expand_items<<<148 * 3, kItemWarps * 32, ism, st>>>(g, items, scratch, offsets, ids, cap));
