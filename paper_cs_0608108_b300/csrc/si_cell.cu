@@ -479,16 +479,20 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks) k_cell(GridDev g, 
 // After the prefix sum: every heavy query's masks expanded into its ids at
 // their place in the output.  A block per heavy cell, slab after slab (one
 // for an unsplit cell): the slab's ordered ids are staged in shared memory
-// (32 per row, rows padded to 33 words so that lanes reading the same
-// position of different rows fall in different banks); each warp takes every
+// (32 per row, rows padded to kRowW words); each warp takes every
 // kExpWarps-th query of the cell (a query's masks are row `slot - first slot`
 // of the slab record).  The warp keeps its queries' write positions in
 // registers (its t-th query in lane t % 32, slot t / 32), fetched at once and
 // carried from slab to slab.  For 32 masks at a time, lane j takes the j-th
-// and, over its 32 bit positions in turn, appends the ids of the set bits to
-// the warp's shared buffer after the hits of the masks before it; the warp
+// and, over its 32 bit positions in turn (reading its row's ids four at a
+// time), appends the ids of the set bits to the warp's shared buffer after
+// the hits of the masks before it; the warp
 // then stores the buffer contiguously.  The next masks are loaded while the
 // current ones are expanded.
+// words per staged row: 32 ids and padding to a 16-byte multiple, so that a
+// lane reads four ids of its row at once (rows of 36 words: the eight lanes
+// of each quarter-warp phase of a 16-byte read hit distinct banks)
+constexpr int kRowW = 36;
 constexpr int kExpWarps = 4;
 constexpr int kExpRows = (kCellCap + 31) / 32;
 constexpr int kExpSlots = (kCellMaxQ + 32 * kExpWarps - 1) / (32 * kExpWarps);   // positions per lane
@@ -498,7 +502,7 @@ __global__ void __launch_bounds__(kExpWarps * 32, 8) k_cell_expand(GridDev g, co
                                                                    const int *__restrict__ scratch,
                                                                    const long long *__restrict__ offsets,
                                                                    int *__restrict__ ids, long long cap) {
-  __shared__ int sids[kExpRows * 33];
+  __shared__ __align__(16) int sids[kExpRows * kRowW];
   __shared__ int sbuf[kExpWarps][1024];
   if (offsets[g.n] > cap) {
     if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(g.status, ST_CAPACITY);
@@ -533,7 +537,7 @@ __global__ void __launch_bounds__(kExpWarps * 32, 8) k_cell_expand(GridDev g, co
       const int *rec_ids = scratch + rec + 1;
       const unsigned *rec_masks = reinterpret_cast<const unsigned *>(rec_ids + nc);
       __syncthreads();   // the previous slab's (or cell's) ids are no longer read
-      for (int k = tid; k < nc; k += blockDim.x) sids[(k >> 5) * 33 + (k & 31)] = __ldg(rec_ids + k);
+      for (int k = tid; k < nc; k += blockDim.x) sids[(k >> 5) * kRowW + (k & 31)] = __ldg(rec_ids + k);
       __syncthreads();
       unsigned mnext = (nmine > 0 && lane < nchunk) ? __ldg(rec_masks + (long long)wid * nchunk + lane) : 0u;
       for (int t = 0; t < nmine; ++t) {
@@ -556,12 +560,19 @@ __global__ void __launch_bounds__(kExpWarps * 32, 8) k_cell_expand(GridDev g, co
           const int cnt = __popc(mm);
           const int inc = warp_incl_scan_i(cnt);
           int o = inc - cnt;
-          const int *row = sids + (c0 + lane) * 33;   // read only where a bit is set
+          const int4 *row4 = reinterpret_cast<const int4 *>(sids + (c0 + lane) * kRowW);
 #pragma unroll
-          for (int b = 0; b < 32; ++b) {
-            const bool set = (mm >> b) & 1u;
-            if (set) buf[o] = row[b];
-            o += set ? 1 : 0;
+          for (int b4 = 0; b4 < 8; ++b4) {
+            const int4 v = row4[b4];   // ids 4 b4 .. 4 b4 + 3 of the lane's chunk
+            const unsigned nb = mm >> (4 * b4);
+            if (nb & 1u) buf[o] = v.x;
+            o += (int)(nb & 1u);
+            if (nb & 2u) buf[o] = v.y;
+            o += (int)((nb >> 1) & 1u);
+            if (nb & 4u) buf[o] = v.z;
+            o += (int)((nb >> 2) & 1u);
+            if (nb & 8u) buf[o] = v.w;
+            o += (int)((nb >> 3) & 1u);
           }
           __syncwarp();
           const int tot = __shfl_sync(0xffffffffu, inc, 31);
@@ -618,10 +629,6 @@ si_status launch_cell_pass(const GridDev &g, const WalkParams &P, const Band &B,
 constexpr int kItemQ = 8;
 constexpr int kItemWarps = 8;
 constexpr int kItemRows = 32;
-// words per staged row: 32 ids and padding to a 16-byte multiple, so that a
-// lane reads four ids of its row at once (rows of 36 words: the eight lanes
-// of each quarter-warp phase hit distinct banks)
-constexpr int kRowW = 36;
 
 __global__ void __launch_bounds__(256) k_expand_plan(GridDev g, const int *__restrict__ heavy,
                                                      const long long *__restrict__ cell_rec,
