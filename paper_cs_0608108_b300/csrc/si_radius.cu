@@ -3,7 +3,7 @@
 //
 // Queries in lightly loaded cells: one thread per query point, queries in cell
 // order so that neighbouring threads walk neighbouring cells (their candidate
-// cells are shared through L1/L2); lists of up to 32 ids are sorted while
+// cells are shared through L1/L2); lists of up to 24 ids are sorted while
 // written, longer ones are queued for a warp (or block) bitonic sort.
 // Queries in dense cells: one warp per query over the flattened class walk.
 // Queries in heavy cells (heavy_cell): one block per 2 x 2 x 2 group of heavy
@@ -203,9 +203,12 @@ __global__ void __launch_bounds__(kQueryThreads) k_radius(GridDev g, WalkParams 
 // Per-query kernel with the class tables staged in shared memory: a
 // persistent grid, each block copies the tables once and then walks queries
 // in cell order (grid-stride), so the divergent per-lane table reads hit
-// shared memory instead of L2.
+// shared memory instead of L2.  Up to six blocks per SM (40 registers; at
+// d = 1.5 cells the tables and 24 staged ids a thread fit six blocks' shared
+// memory): the walk waits on dependent loads, and more resident warps hide
+// more of them.
 template <bool WRITE>
-__global__ void __launch_bounds__(kClassThreads) k_radius_cls(GridDev g, WalkParams P, Band B,
+__global__ void __launch_bounds__(kClassThreads, 6) k_radius_cls(GridDev g, WalkParams P, Band B,
                                                               unsigned flags, unsigned skip,
                                                               int n_entries, long long *counts,
                                                               const long long *offsets, int *ids,

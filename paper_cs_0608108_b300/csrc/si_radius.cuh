@@ -9,7 +9,7 @@ namespace si {
 
 constexpr int kQueryThreads = 128;   // per-query kernels
 constexpr int kClassThreads = 256;   // per-query kernel with shared-memory class tables
-constexpr int kInlineSort = 32;      // lists up to this length are sorted while written
+constexpr int kInlineSort = 24;      // lists up to this length are sorted while written
 constexpr int kDenseCap = 512;       // lists a warp of the dense path sorts in shared memory
 constexpr int kCellThreads = 512;
 constexpr int kCellCap = 2560;       // staged candidates per query cell
