@@ -419,8 +419,10 @@ struct WarpWriteVisitor {
   }
 };
 
+// Up to six blocks per SM (40 registers): more resident warps to wait on
+// the walk's dependent loads, and room beside the heavy cells' kernels.
 template <bool WRITE>
-__global__ void __launch_bounds__(kClassThreads, 4) k_radius_dense(GridDev g, WalkParams P, Band B,
+__global__ void __launch_bounds__(kClassThreads, 6) k_radius_dense(GridDev g, WalkParams P, Band B,
                                                                    unsigned flags, int n_entries,
                                                                    const int *__restrict__ denseq,
                                                                    long long *counts, const long long *offsets,
